@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""3DES-EDE3 benchmark on GB300: GB/s of the 1 GiB single-key ECB workload.
+
+Workload (one step): ECB encryption of a 1 GiB buffer (2^27 big-endian
+64-bit blocks) of seeded uniform-random bytes under one seeded key triple,
+input and output resident in HBM, one launch of the bitsliced ECB kernel
+through the C ABI (tdes_ecb_encrypt).  The input (1 GiB) is larger than the
+129 MB L2, so no flush is needed between steps.
+
+Reported beside it: the same pass decrypting and in CTR mode, the 1 MiB
+single-launch latency, the key-schedule time, an end-to-end number through
+the host-buffer entry point (tdes_ecb_crypt_host, pinned host memory, every
+byte copied host->device and back inside the timed region), the ALU
+roofline of the dominant kernel against a live LOP3-throughput probe, and
+the CPU oracle's throughput on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank encrypts its own 1 GiB
+(replicas: the cipher needs no exchange between GPUs); value = all bytes /
+the slowest rank's time.  --impl reference times the CPU oracle (the plain
+reference implementation of the paper's method) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3DES GB/s: 1 GiB ECB and batched serve (p50/p99 ms) vs plain ECB, bit-exact"
+WORKLOAD = ("3DES-EDE3 ECB encrypt of 1 GiB (2^27 big-endian 64-bit blocks) of seeded "
+            "uniform random bytes, one seeded key triple with odd-parity bytes")
+NBYTES = 1 << 30
+SEED = 2
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def start_clock_sampler(device_id: str | None):
+    cmd = ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+           "-lms", "100"]
+    if device_id:
+        cmd.insert(1, f"--id={device_id}")
+    try:
+        return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def stop_clock_sampler(p):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        out, _ = p.communicate(timeout=5)
+    except Exception:
+        p.kill()
+        out, _ = p.communicate()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
+def gpu_id_for_smi(torch, dev: int):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_baseline(keys: bytes, seconds: float = 12.0):
+    """The oracle as it stands, single-threaded and over all host cores."""
+    import oracle
+    from paper_2007_10752_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # calibrate on 64 KiB, then size each sample for about seconds/2
+    probe = synth.random_bytes(SEED, 1 << 16)
+    t = time.perf_counter()
+    oracle.tdes_parallel(keys, probe, "ecb_enc", threads=1)
+    rate1 = (1 << 16) / max(time.perf_counter() - t, 1e-6)
+    n1 = int(min(max(rate1 * seconds / 2, 1 << 16), 64 << 20)) // 8 * 8
+    n_mt = int(min(max(rate1 * cores * seconds / 2, 1 << 16), 512 << 20)) // 8 * 8
+    s1 = synth.random_bytes(SEED, n1)
+    t = time.perf_counter()
+    oracle.tdes_parallel(keys, s1, "ecb_enc", threads=1)
+    g1 = n1 / (time.perf_counter() - t) / 1e9
+    smt = synth.random_bytes(SEED, n_mt)
+    t = time.perf_counter()
+    oracle.tdes_parallel(keys, smt, "ecb_enc", threads=cores)
+    gmt = n_mt / (time.perf_counter() - t) / 1e9
+    return {"value": gmt, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": (f"ECB encrypt of the first {n_mt} bytes of the 1 GiB workload over "
+                       f"{cores} threads; single-thread: {g1:.6f} GB/s on the first {n1} bytes"),
+            "single_thread_gbs": g1}
+
+
+# ---------------------------------------------------------------- roofline
+def alg_ops_per_32_blocks() -> int:
+    """Logic-pipe operations the bitsliced ECB algorithm needs per 32 blocks.
+
+    48 rounds x (8 S-box circuits of G LOP3 in total + 32 fused XOR updates),
+    4 bit-matrix transposes x 256 operations, and 4 x 64 key-mask XORs
+    (prologue, two re-keyings, epilogue).  The 16 doubled expansion inputs
+    per round are XORed on the integer multiply-add pipe and not counted.
+    """
+    with open(os.path.join(ROOT, "paper_2007_10752_gb300", "gen", "sbox_lop3.json")) as f:
+        g = sum(len(s["gates"]) for s in json.load(f)["sboxes"])
+    return 48 * (g + 32) + 4 * 256 + 4 * 64
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2007_10752_gb300", "csrc")
+    for rel in ("tdes_kernels.cu", "tdes_bitslice.cuh", "generated/tdes_generated.cuh"):
+        with open(os.path.join(csrc, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per ECB launch from the committed ncu summary, if it is for this kernel."""
+    path = os.path.join(ROOT, "profiles", "tdes_ecb_kernel_1gib.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def probe_alu_peak():
+    import ctypes
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2007_10752_gb300", "libtdes_probe.so"))
+    lib.tdes_probe_lop3_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_float)]
+    best = 0.0
+    for ctas in (4, 8):
+        ops, ms = ctypes.c_double(), ctypes.c_float()
+        rc = lib.tdes_probe_lop3_rate(ctas, 256, 4000, ctypes.byref(ops), ctypes.byref(ms))
+        if rc == 0:
+            best = max(best, ops.value)
+    return best
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2007_10752_gb300 import build as b
+    from paper_2007_10752_gb300 import synth, tdes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    b.build()
+    tdes.load()
+    dev = torch.cuda.current_device()
+
+    keys = synth.key_triple(SEED)
+    host = synth.random_bytes(SEED, NBYTES)
+    x = torch.from_numpy(host).to(f"cuda:{dev}")
+    y = torch.empty_like(x)
+    t0 = time.perf_counter()
+    ks = tdes.KeySchedule.from_triple(keys)
+    keysched_ms = (time.perf_counter() - t0) * 1e3
+    stream = torch.cuda.current_stream()
+
+    def ecb_step():
+        tdes.tdes_ecb_encrypt(ks, x, y)
+
+    for _ in range(args.warmup):
+        ecb_step()
+    torch.cuda.synchronize()
+    alu_peak = probe_alu_peak() if rank == 0 else 0.0
+
+    # ---- timed region: K ECB launches, an event pair around each
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = start_clock_sampler(gpu_id_for_smi(torch, dev))
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for e0, e1 in evs:
+        e0.record(stream)
+        ecb_step()
+        e1.record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = stop_clock_sampler(sampler)
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    per_launch_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+    ms_per_step = total_ms / args.steps
+    value = world * NBYTES / (ms_per_step * 1e-3) / 1e9
+
+    # parity spot check of the timed output (a few windows against the oracle)
+    import oracle
+    yh = y[: 8 * 1024].cpu().numpy()
+    assert (yh == oracle.tdes_ecb(keys, host[: 8 * 1024])).all(), "bench output differs"
+
+    # ---- other modes of the same workload, and the 1 MiB single launch
+    def time_fn(fn, n):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    nonce = synth.nonce32(SEED)
+    dec_ms = time_fn(lambda: tdes.tdes_ecb_decrypt(ks, x, y), 50)
+    ctr_ms = time_fn(lambda: tdes.tdes_ctr_crypt(ks, nonce, 0, x, y), 50)
+    small_in, small_out = x[: 1 << 20], y[: 1 << 20]
+    small_us = time_fn(lambda: tdes.tdes_ecb_encrypt(ks, small_in, small_out), 200) * 1e3
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hbuf = torch.from_numpy(host.copy()).pin_memory()
+        dev_buf = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+        tdes.tdes_ecb_crypt_host(ks, False, hbuf, hbuf, dev_buf)  # warm-up
+        n_e2e = max(3, min(10, args.steps // 50))
+        if world > 1:
+            dist.barrier()
+        t = time.perf_counter()
+        for _ in range(n_e2e):
+            tdes.tdes_ecb_crypt_host(ks, False, hbuf, hbuf, dev_buf)
+        el = (time.perf_counter() - t) / n_e2e
+        if world > 1:
+            tt = torch.tensor([el], device=f"cuda:{dev}")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        e2e = {"value": world * NBYTES / el / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": NBYTES, "d2h_bytes_per_step": NBYTES,
+               "api": "tdes_ecb_crypt_host (pinned host buffer, 256 MiB device staging)"}
+        del hbuf, dev_buf
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    pk, pk_kind = peaks()
+    ops = alg_ops_per_32_blocks() * (NBYTES // 8 // 32)
+    achieved = ops / (per_launch_ms * 1e-3) / 1e12
+    peak = alu_peak / 1e12
+    hbm_gbs = 16 * (NBYTES // 8) / (per_launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mode": "ECB encrypt", "bytes_per_gpu": NBYTES,
+                   "l2": "input 1 GiB per step > 129 MB L2: no flush needed",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                     "unit": "Tops/s", "frac": round(achieved / peak, 4) if peak else None,
+                     "traffic": traffic,
+                     "peak_source": "live LOP3 probe (libtdes_probe.so) on this GPU",
+                     "alg_ops_per_32_blocks": alg_ops_per_32_blocks(),
+                     "hbm_achieved_gbs": round(hbm_gbs, 1),
+                     "hbm_peak_gbs": pk.get("hbm_gbs"),
+                     "hbm_frac": round(hbm_gbs / pk.get("hbm_gbs", HBM_FALLBACK_GBS), 4),
+                     "hbm_peak_source": pk_kind},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "extra": {"kernel_ms_per_launch": round(per_launch_ms, 4),
+                  "ecb_decrypt_gbs": round(NBYTES / (dec_ms * 1e-3) / 1e9, 3),
+                  "ctr_gbs": round(NBYTES / (ctr_ms * 1e-3) / 1e9, 3),
+                  "ecb_1mib_single_launch_us": round(small_us, 2),
+                  "key_schedule_ms": round(keysched_ms, 3),
+                  "sbox_lop3_per_round": tdes.tdes_sbox_gate_count()},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(keys)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args):
+    """The CPU oracle on the host cores: rank 0 only."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle
+    from paper_2007_10752_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    keys = synth.key_triple(SEED)
+    probe = synth.random_bytes(SEED, 1 << 16)
+    t = time.perf_counter()
+    oracle.tdes_parallel(keys, probe, "ecb_enc", threads=cores)
+    rate = (1 << 16) / max(time.perf_counter() - t, 1e-6)
+    # whole run about 60 s: size each step's sample from the calibration
+    per_step = int(min(max(rate * 60.0 / (args.steps + args.warmup), 1 << 16), NBYTES)) // 8 * 8
+    data = synth.random_bytes(SEED, per_step)
+    for _ in range(args.warmup):
+        oracle.tdes_parallel(keys, data, "ecb_enc", threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.tdes_parallel(keys, data, "ecb_enc", threads=cores)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step / (ms * 1e-3) / 1e9
+    sample = (f"ECB encrypt of the first {per_step} bytes of the 1 GiB workload per step, "
+              f"{cores} host threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "GB/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mode": "ECB encrypt", "sample_bytes": per_step},
+        "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

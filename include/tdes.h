@@ -1,0 +1,120 @@
+/*
+ * tdes.h -- C ABI of the GB300 (sm_103a) 3DES-EDE3 library libtdes_gb300.so.
+ *
+ * The operation is the one defined in "Bit-level Parallelization of 3DES
+ * Encryption on GPU" (Altinok, Peker, Temizel), Sec. III:
+ *   - key generation (Sec. III-A): PC-1, two 28-bit halves rotated left
+ *     cumulatively by shift_keys, PC-2 -> 16 round keys per base key, for
+ *     each of the three base keys;
+ *   - DES (Sec. III-B): initial_perm, 16 rounds of expansion, round-key XOR,
+ *     eight S-boxes, the per permutation and XOR into the left half, then the
+ *     halves combined and final_perm; decryption reverses the round keys;
+ *   - 3DES-EDE3 (Sec. III-B, the two equations):
+ *       C = E_K3(D_K2(E_K1(P))),   P = D_K1(E_K2(D_K3(C))).
+ * The paper encrypts files of independent 64-bit blocks in ECB mode (Sec. V);
+ * CTR and CBC are the usual block-cipher modes built on the same cipher.
+ *
+ * Conventions shared by every call:
+ *   - A block is 8 bytes, big-endian: bit 1 of the paper's numbering is the
+ *     most significant bit of the first byte.  Keys use the same order; the
+ *     parity bits (bit 8 of every byte) are ignored, as PC-1 drops them.
+ *   - Data pointers are DEVICE pointers owned by the caller, on the device
+ *     that was current when the key schedule was made.  They must be 8-byte
+ *     aligned; 16-byte aligned buffers take the fastest load path.
+ *     `nbytes` must be a multiple of 8 (the paper's input consists of whole
+ *     64-bit blocks); 0 is a valid empty call.  in == out (in place) is
+ *     allowed; any other overlap of the two ranges returns TDES_EINVAL.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream) unless stated otherwise; the caller synchronises.
+ *   - Every call returns TDES_OK (0) or a negative status and never aborts.
+ *     tdes_last_error() gives a message for the last failure of the calling
+ *     host thread.
+ */
+#ifndef TDES_GB300_H
+#define TDES_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tdes_stream_t; /* same type as cudaStream_t */
+typedef struct tdes_ks tdes_ks_t;          /* opaque, library-owned key schedule */
+
+#define TDES_OK 0
+#define TDES_EINVAL (-1)    /* bad argument: size, alignment, overlap, NULL, counter range */
+#define TDES_ENOMEM (-2)    /* device allocation failed */
+#define TDES_EBUSY (-3)     /* resource limit reached; retry later */
+#define TDES_ETIMEDOUT (-4) /* a bounded wait ran out */
+#define TDES_ECUDA (-5)     /* a CUDA runtime call failed; see tdes_last_error() */
+
+/* Key schedule (Sec. III-A) for the triple K1, K2, K3 (8 bytes each).
+ * Runs the key-schedule kernel on the current device and waits for it
+ * (synchronous).  *out receives a handle holding, in device memory, the
+ * round-constant tables of the bitsliced kernels for encryption and for
+ * decryption (the decryption table is the round keys in reverse order,
+ * Sec. III-B) and the six-bit round-key groups of the scalar path.  Weak
+ * keys and K1 = K2 = K3 (which reduces EDE3 to single DES, Sec. III-B) are
+ * accepted.  Free with tdes_key_free(). */
+int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3[8],
+                      tdes_ks_t **out);
+
+/* Releases a key schedule (NULL is ignored).  The caller must ensure no
+ * kernel that uses it is still running. */
+void tdes_key_free(tdes_ks_t *ks);
+
+/* ECB (the paper's mode, Sec. V): every 8-byte block of in[0, nbytes) is
+ * encrypted (resp. decrypted) independently with EDE3 into out. */
+int tdes_ecb_encrypt(const tdes_ks_t *ks, const void *in, void *out, size_t nbytes,
+                     tdes_stream_t stream);
+int tdes_ecb_decrypt(const tdes_ks_t *ks, const void *in, void *out, size_t nbytes,
+                     tdes_stream_t stream);
+
+/* CTR: out_i = in_i XOR E(nonce || ctr0 + i) for block i, where the counter
+ * block is the 32-bit nonce followed by the 32-bit counter, both big-endian.
+ * Encryption and decryption are the same call.  The counter never wraps:
+ * ctr0 + nbytes/8 > 2^32 returns TDES_EINVAL. */
+int tdes_ctr_crypt(const tdes_ks_t *ks, uint32_t nonce, uint32_t ctr0, const void *in,
+                   void *out, size_t nbytes, tdes_stream_t stream);
+
+/* CBC decryption: out_i = D(in_i) XOR in_{i-1}, with in_{-1} = iv (the
+ * 64-bit IV serialised big-endian).  Parallel over blocks.  In place
+ * (in == out) first snapshots the ciphertext block before every 8 KiB tile
+ * into a stream-ordered temporary of 8 bytes per tile (cudaMallocAsync on
+ * `stream`, freed on the same stream); TDES_ENOMEM if that fails. */
+int tdes_cbc_decrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out,
+                     size_t nbytes, tdes_stream_t stream);
+
+/* CBC encryption: out_i = E(in_i XOR out_{i-1}), out_{-1} = iv.  Each block
+ * depends on the previous one, so one GPU thread walks the whole message
+ * (latency about 48 dependent rounds per block); batch many messages to get
+ * throughput. */
+int tdes_cbc_encrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out,
+                     size_t nbytes, tdes_stream_t stream);
+
+/* Host-buffer ECB: encrypts (decrypt == 0) or decrypts host memory
+ * host_in[0, nbytes) into host_out, streaming it through the caller's device
+ * buffer dev_buf of dev_bytes bytes (at least 2 x 64 KiB, 16-byte aligned):
+ * host-to-device copies, the kernel and device-to-host copies of successive
+ * chunks overlap on internal streams.  Host buffers should be pinned
+ * (cudaHostAlloc / page-locked) for full copy speed.  Synchronous: returns
+ * when host_out is complete.  in == out is allowed. */
+int tdes_ecb_crypt_host(const tdes_ks_t *ks, int decrypt, const void *host_in, void *host_out,
+                        size_t nbytes, void *dev_buf, size_t dev_bytes);
+
+/* Number of LOP3 instructions the eight generated S-box circuits take per
+ * round, i.e. per 32 blocks per round (the circuit size fixed at build time). */
+int tdes_sbox_gate_count(void);
+
+/* Short English text of a status code. */
+const char *tdes_strerror(int status);
+
+/* Message of the last failure on the calling host thread ("" if none). */
+const char *tdes_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDES_GB300_H */

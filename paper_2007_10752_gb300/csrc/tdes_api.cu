@@ -1,0 +1,330 @@
+// tdes_api.cu -- the C ABI of include/tdes.h: argument checks, device-memory
+// ownership of key schedules, launch geometry, and the host-buffer pipeline.
+// All cipher arithmetic runs in the kernels of tdes_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/tdes.h"
+#include "tdes_internal.h"
+
+struct tdes_ks {
+    int device;
+    void* mem;              // one cudaMalloc holding everything below
+    uint32_t* tab[2];       // bitsliced round-constant tables: [0] encrypt, [1] decrypt
+    uint8_t* chunk[2];      // scalar-path round-key groups: [0] encrypt, [1] decrypt
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? TDES_ENOMEM : TDES_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+constexpr int kMaxDevices = 64;
+struct DeviceInfo {
+    bool ready = false;
+    int sms = 0;
+    int ctas_per_sm[tdes::kNumKernels] = {1, 1, 1};
+};
+DeviceInfo g_devices[kMaxDevices];
+std::mutex g_dev_mutex;
+
+const DeviceInfo* device_info(int device) {
+    if (device < 0 || device >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    DeviceInfo& d = g_devices[device];
+    if (!d.ready) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+            return nullptr;
+        for (int k = 0; k < tdes::kNumKernels; ++k) d.ctas_per_sm[k] = tdes::wide_ctas_per_sm(k);
+        d.ready = true;
+    }
+    return &d;
+}
+
+// Checks shared by every data call; sets *nblocks.
+int check_call(const tdes_ks_t* ks, const void* in, const void* out, size_t nbytes,
+               uint64_t* nblocks) {
+    if (ks == nullptr) return fail(TDES_EINVAL, "key schedule is NULL");
+    if (nbytes % 8 != 0) return fail(TDES_EINVAL, "nbytes = %zu is not a multiple of 8", nbytes);
+    *nblocks = nbytes / 8;
+    if (nbytes == 0) return TDES_OK;
+    if (in == nullptr || out == nullptr) return fail(TDES_EINVAL, "NULL data pointer");
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+    if ((a | b) & 7u) return fail(TDES_EINVAL, "data pointers must be 8-byte aligned");
+    if (a != b && a < b + nbytes && b < a + nbytes)
+        return fail(TDES_EINVAL, "input and output overlap without being the same buffer");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != ks->device)
+        return fail(TDES_EINVAL, "key schedule lives on device %d but device %d is current",
+                    ks->device, dev);
+    return TDES_OK;
+}
+
+bool aligned16(const void* in, const void* out) {
+    return ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+}
+
+}  // namespace
+
+namespace tdes {
+
+// Small inputs: one warp per CTA so the few tiles spread over many SMs.
+// Large inputs: kWideWarps warps per CTA, a grid of every resident CTA,
+// each warp striding over tiles.
+Geometry geometry_for(uint64_t ntiles, int kernel_id, int device) {
+    const DeviceInfo* d = device_info(device);
+    const int sms = d ? d->sms : 1;
+    const int per_sm = d ? d->ctas_per_sm[kernel_id] : 1;
+    if (ntiles <= (uint64_t)sms * kWideWarps) return {(int)(ntiles ? ntiles : 1), 32};
+    const uint64_t need = (ntiles + kWideWarps - 1) / kWideWarps;
+    const uint64_t full = (uint64_t)sms * per_sm;
+    return {(int)(need < full ? need : full), 32 * kWideWarps};
+}
+
+}  // namespace tdes
+
+extern "C" {
+
+int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3[8],
+                      tdes_ks_t** out) {
+    if (out == nullptr || k1 == nullptr || k2 == nullptr || k3 == nullptr)
+        return fail(TDES_EINVAL, "NULL argument to tdes_key_schedule");
+    *out = nullptr;
+    tdes::Keys24 keys;
+    memcpy(keys.b, k1, 8);
+    memcpy(keys.b + 8, k2, 8);
+    memcpy(keys.b + 16, k3, 8);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    const size_t tab_bytes = sizeof(uint32_t) * tdes::kTableWords;
+    const size_t total = 2 * tab_bytes + 2 * tdes::kChunkBytes;
+    void* mem = nullptr;
+    e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(key schedule)");
+    tdes_ks_t* ks = new (std::nothrow) tdes_ks_t;
+    if (ks == nullptr) {
+        cudaFree(mem);
+        return fail(TDES_ENOMEM, "host allocation failed");
+    }
+    ks->device = dev;
+    ks->mem = mem;
+    ks->tab[0] = static_cast<uint32_t*>(mem);
+    ks->tab[1] = ks->tab[0] + tdes::kTableWords;
+    ks->chunk[0] = reinterpret_cast<uint8_t*>(ks->tab[1] + tdes::kTableWords);
+    ks->chunk[1] = ks->chunk[0] + tdes::kChunkBytes;
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = tdes::launch_keysched(keys, ks->tab[0], ks->tab[1], ks->chunk[0], ks->chunk[1], s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(s);
+    }
+    memset(&keys, 0, sizeof keys);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        delete ks;
+        return cuda_fail(e, "key-schedule kernel");
+    }
+    *out = ks;
+    return TDES_OK;
+}
+
+void tdes_key_free(tdes_ks_t* ks) {
+    if (ks == nullptr) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != ks->device) cudaSetDevice(ks->device);
+    cudaFree(ks->mem);
+    if (cur >= 0 && cur != ks->device) cudaSetDevice(cur);
+    delete ks;
+}
+
+static int ecb(const tdes_ks_t* ks, int dir, const void* in, void* out, size_t nbytes,
+               tdes_stream_t stream) {
+    uint64_t nblocks = 0;
+    int rc = check_call(ks, in, out, nbytes, &nblocks);
+    if (rc != TDES_OK || nblocks == 0) return rc;
+    const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+    const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kEcb, ks->device);
+    cudaError_t e = tdes::launch_ecb(ks->tab[dir], in, out, nblocks, aligned16(in, out), g,
+                                     reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? TDES_OK : cuda_fail(e, "ECB kernel launch");
+}
+
+int tdes_ecb_encrypt(const tdes_ks_t* ks, const void* in, void* out, size_t nbytes,
+                     tdes_stream_t stream) {
+    return ecb(ks, 0, in, out, nbytes, stream);
+}
+
+int tdes_ecb_decrypt(const tdes_ks_t* ks, const void* in, void* out, size_t nbytes,
+                     tdes_stream_t stream) {
+    return ecb(ks, 1, in, out, nbytes, stream);
+}
+
+int tdes_ctr_crypt(const tdes_ks_t* ks, uint32_t nonce, uint32_t ctr0, const void* in, void* out,
+                   size_t nbytes, tdes_stream_t stream) {
+    uint64_t nblocks = 0;
+    int rc = check_call(ks, in, out, nbytes, &nblocks);
+    if (rc != TDES_OK || nblocks == 0) return rc;
+    if ((uint64_t)ctr0 + nblocks > (1ull << 32))
+        return fail(TDES_EINVAL, "CTR counter would wrap: ctr0 %u + %llu blocks > 2^32", ctr0,
+                    (unsigned long long)nblocks);
+    const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+    const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kCtr, ks->device);
+    cudaError_t e = tdes::launch_ctr(ks->tab[0], nonce, ctr0, in, out, nblocks,
+                                     aligned16(in, out), g,
+                                     reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CTR kernel launch");
+}
+
+int tdes_cbc_decrypt(const tdes_ks_t* ks, uint64_t iv, const void* in, void* out, size_t nbytes,
+                     tdes_stream_t stream) {
+    uint64_t nblocks = 0;
+    int rc = check_call(ks, in, out, nbytes, &nblocks);
+    if (rc != TDES_OK || nblocks == 0) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+    uint64_t* halo = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (in == out && ntiles > 1) {
+        e = cudaMallocAsync(reinterpret_cast<void**>(&halo), ntiles * sizeof(uint64_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(CBC halo)");
+        e = tdes::launch_cbc_halo(in, halo, nblocks, s);
+    }
+    if (e == cudaSuccess) {
+        const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kCbcDec, ks->device);
+        e = tdes::launch_cbc_dec(ks->tab[1], iv, in, out, nblocks, halo, aligned16(in, out), g, s);
+    }
+    if (halo != nullptr) {
+        cudaError_t e2 = cudaFreeAsync(halo, s);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CBC-decrypt kernel launch");
+}
+
+int tdes_cbc_encrypt(const tdes_ks_t* ks, uint64_t iv, const void* in, void* out, size_t nbytes,
+                     tdes_stream_t stream) {
+    uint64_t nblocks = 0;
+    int rc = check_call(ks, in, out, nbytes, &nblocks);
+    if (rc != TDES_OK || nblocks == 0) return rc;
+    cudaError_t e = tdes::launch_cbc_enc(ks->chunk[0], iv, in, out, nblocks,
+                                         reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CBC-encrypt kernel launch");
+}
+
+// Host-buffer ECB.  The device buffer is split into two halves; chunk k goes
+// host->device on the copy-in stream, through the kernel on the compute
+// stream, and device->host on the copy-out stream, with events ordering the
+// three and letting chunk k+1's copy-in overlap chunk k's kernel.
+int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, void* host_out,
+                        size_t nbytes, void* dev_buf, size_t dev_bytes) {
+    if (ks == nullptr) return fail(TDES_EINVAL, "key schedule is NULL");
+    if (nbytes % 8 != 0) return fail(TDES_EINVAL, "nbytes = %zu is not a multiple of 8", nbytes);
+    if (nbytes == 0) return TDES_OK;
+    if (host_in == nullptr || host_out == nullptr || dev_buf == nullptr)
+        return fail(TDES_EINVAL, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(dev_buf) & 15u)
+        return fail(TDES_EINVAL, "device buffer must be 16-byte aligned");
+    const size_t half = (dev_bytes / 2) & ~(size_t)(8 * tdes::kTileBlocks - 1);
+    if (half < 64 * 1024) return fail(TDES_EINVAL, "device buffer smaller than 2 x 64 KiB");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != ks->device) return fail(TDES_EINVAL, "key schedule lives on another device");
+
+    cudaStream_t sin = nullptr, scomp = nullptr, sout = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
+    e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_k[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming);
+    }
+    const char* what = "stream/event setup";
+    const uint8_t* src = static_cast<const uint8_t*>(host_in);
+    uint8_t* dst = static_cast<uint8_t*>(host_out);
+    uint8_t* buf[2] = {static_cast<uint8_t*>(dev_buf), static_cast<uint8_t*>(dev_buf) + half};
+    bool used[2] = {false, false};
+    for (size_t off = 0, k = 0; e == cudaSuccess && off < nbytes; off += half, ++k) {
+        const int b = (int)(k & 1);
+        const size_t n = (nbytes - off < half) ? nbytes - off : half;
+        const uint64_t nblocks = n / 8;
+        const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+        what = "host-to-device copy";
+        if (used[b]) e = cudaStreamWaitEvent(sin, ev_out[b], 0);  // buffer drained
+        if (e == cudaSuccess) e = cudaMemcpyAsync(buf[b], src + off, n, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[b], sin);
+        what = "ECB kernel";
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(scomp, ev_in[b], 0);
+        if (e == cudaSuccess) {
+            const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kEcb, ks->device);
+            e = tdes::launch_ecb(ks->tab[decrypt ? 1 : 0], buf[b], buf[b], nblocks, true, g, scomp);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_k[b], scomp);
+        what = "device-to-host copy";
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_k[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + off, buf[b], n, cudaMemcpyDeviceToHost, sout);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], sout);
+        used[b] = true;
+    }
+    cudaError_t es = sout ? cudaStreamSynchronize(sout) : cudaSuccess;
+    if (sin) cudaStreamSynchronize(sin);
+    if (scomp) cudaStreamSynchronize(scomp);
+    if (e == cudaSuccess && es != cudaSuccess) {
+        e = es;
+        what = "synchronise";
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+        if (ev_k[i]) cudaEventDestroy(ev_k[i]);
+        if (ev_out[i]) cudaEventDestroy(ev_out[i]);
+    }
+    if (sin) cudaStreamDestroy(sin);
+    if (scomp) cudaStreamDestroy(scomp);
+    if (sout) cudaStreamDestroy(sout);
+    return e == cudaSuccess ? TDES_OK : cuda_fail(e, what);
+}
+
+int tdes_sbox_gate_count(void) { return tdes::sbox_gate_count(); }
+
+const char* tdes_strerror(int status) {
+    switch (status) {
+        case TDES_OK: return "ok";
+        case TDES_EINVAL: return "invalid argument";
+        case TDES_ENOMEM: return "out of device memory";
+        case TDES_EBUSY: return "busy";
+        case TDES_ETIMEDOUT: return "timed out";
+        case TDES_ECUDA: return "CUDA error";
+        default: return "unknown status";
+    }
+}
+
+const char* tdes_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// tdes_bitslice.cuh -- bitsliced 3DES-EDE3 core shared by every kernel.
+//
+// A thread holds 32 independent 64-bit blocks.  After a 32x32 bit-matrix
+// transpose of their two 32-bit words, word A_w[c] holds one bit position of
+// all 32 blocks ("bit-plane"), so one 32-bit logic instruction advances 32
+// blocks at once.  The initial and final permutations and the expansion and
+// permutation inside the round are then only renames of planes, and the
+// S-boxes are circuits of LOP3 instructions (3-input lookup tables).
+//
+// What is computed is "Bit-level Parallelization of 3DES Encryption on GPU",
+// Sec. III-B: IP, 16 rounds per DES pass, FP, and the EDE3 composition
+// E_K3(D_K2(E_K1(P))) (decryption: D_K1(E_K2(D_K3(C)))).  Between the three
+// DES passes FP and IP cancel, so the 48 rounds run back to back on the
+// planes and only the half that takes the next XOR changes.
+//
+// Everything here is __host__ __device__ so that the same code can be run on
+// the host by the generator's self-check; the kernels are the product.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define TDES_HD __host__ __device__ __forceinline__
+
+template <int LUT>
+TDES_HD uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+#ifdef __CUDA_ARCH__
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+#else
+    uint32_t r = 0;
+    for (int i = 0; i < 8; ++i)
+        if ((LUT >> i) & 1) r |= ((i & 4) ? a : ~a) & ((i & 2) ? b : ~b) & ((i & 1) ? c : ~c);
+    return r;
+#endif
+}
+
+TDES_HD uint32_t byte_perm(uint32_t a, uint32_t b, uint32_t sel) {
+#ifdef __CUDA_ARCH__
+    return __byte_perm(a, b, sel);
+#else
+    uint64_t v = ((uint64_t)b << 32) | a;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; ++i) r |= (uint32_t)((v >> (8 * ((sel >> (4 * i)) & 7))) & 0xFF) << (8 * i);
+    return r;
+#endif
+}
+
+#include "generated/tdes_generated.cuh"
+
+// In-place 32x32 bit-matrix transpose: afterwards bit s of A[c] is the old
+// bit c of A[s].  Five stages each exchange one bit of the row index with
+// the same bit of the column index; the 16- and 8-bit stages are byte
+// permutes, the 4-, 2- and 1-bit stages a shift plus a LOP3 select per word.
+TDES_HD void transpose32(uint32_t (&A)[32]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t a = A[i], b = A[i + 16];
+        A[i] = byte_perm(a, b, 0x5410);
+        A[i + 16] = byte_perm(a, b, 0x7632);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i & 8) continue;
+        const uint32_t a = A[i], b = A[i + 8];
+        A[i] = byte_perm(a, b, 0x6240);
+        A[i + 8] = byte_perm(a, b, 0x7351);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i & 4) continue;
+        const uint32_t a = A[i], b = A[i + 4];
+        A[i] = lop3<0xe4>(a, b << 4, 0x0F0F0F0Fu);  // (a & m) | ((b << 4) & ~m)
+        A[i + 4] = lop3<0xe4>(a >> 4, b, 0x0F0F0F0Fu);  // ((a >> 4) & m) | (b & ~m)
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i & 2) continue;
+        const uint32_t a = A[i], b = A[i + 2];
+        A[i] = lop3<0xe4>(a, b << 2, 0x33333333u);
+        A[i + 2] = lop3<0xe4>(a >> 2, b, 0x33333333u);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+        const uint32_t a = A[i], b = A[i + 1];
+        A[i] = lop3<0xe4>(a, b << 1, 0x55555555u);
+        A[i + 1] = lop3<0xe4>(a >> 1, b, 0x55555555u);
+    }
+}
+// lop3<0xe4>(x, y, m) = m ? x : y  (0xE4 = (0xAA & 0xF0) | (~0xAA & 0xCC)).
+
+TDES_HD void xor_planes(uint32_t (&H)[32], const uint32_t* __restrict__ k) {
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(k + i);
+        H[i] ^= v.x;
+        H[i + 1] ^= v.y;
+        H[i + 2] ^= v.z;
+        H[i + 3] ^= v.w;
+    }
+}
+
+// The 48 rounds of EDE3 on keyed planes.  tab is the per-key round-constant
+// table (TDES_TABLE_WORDS words, encryption or decryption order) built by
+// the key-schedule kernel.
+TDES_HD void tdes_rounds(uint32_t (&Lh)[32], uint32_t (&Rh)[32], const uint32_t* __restrict__ tab) {
+    xor_planes(Lh, tab + TDES_TABLE_PRO);
+    xor_planes(Rh, tab + TDES_TABLE_PRO + 32);
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {  // first DES pass: rounds 0..15
+        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it));
+        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it + 1));
+    }
+    xor_planes(Lh, tab + TDES_TABLE_REKEY16);
+    xor_planes(Rh, tab + TDES_TABLE_REKEY16 + 32);
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {  // second pass: the XOR target repeats at its start
+        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (16 + 2 * it));
+        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (17 + 2 * it));
+    }
+    xor_planes(Lh, tab + TDES_TABLE_REKEY32);
+    xor_planes(Rh, tab + TDES_TABLE_REKEY32 + 32);
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {  // third pass
+        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (32 + 2 * it));
+        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (33 + 2 * it));
+    }
+    xor_planes(Lh, tab + TDES_TABLE_EPI);
+    xor_planes(Rh, tab + TDES_TABLE_EPI + 32);
+}
+
+// 32 blocks: A0[s], A1[s] are the first and second little-endian 32-bit
+// words of block s on entry and of its result on return.
+TDES_HD void tdes_process32(uint32_t (&A0)[32], uint32_t (&A1)[32], const uint32_t* __restrict__ tab) {
+    transpose32(A0);
+    transpose32(A1);
+    uint32_t Lh[32], Rh[32];
+    tdes_ip(A0, A1, Lh, Rh);
+    tdes_rounds(Lh, Rh, tab);
+    tdes_fp(Lh, Rh, A0, A1);
+    transpose32(A0);
+    transpose32(A1);
+}
+
+// ---------------------------------------------------------------- scalar path
+// One block at a time (serial CBC encryption).  A block is a 64-bit value
+// with bit 1 at position 63 (big-endian bytes); a half has bit 1 at 31.
+
+TDES_HD uint32_t rotr32(uint32_t x, int n) { return (x >> n) | (x << ((32 - n) & 31)); }
+
+TDES_HD uint64_t permute64(uint64_t v, const uint8_t* __restrict__ src) {
+    uint64_t r = 0;
+    for (int j = 0; j < 64; ++j) r |= ((v >> (63 - src[j])) & 1ull) << (63 - j);
+    return r;
+}
+
+// sp: 8 x 64 S-box/permutation words; chunks: 48 rounds x 8 six-bit round-key
+// groups; ip/fp: the permutations as 0-based source bits.
+TDES_HD uint64_t tdes_block_scalar(uint64_t v, const uint32_t* __restrict__ sp,
+                                   const uint8_t* __restrict__ chunks,
+                                   const uint8_t* __restrict__ ip, const uint8_t* __restrict__ fp) {
+    v = permute64(v, ip);
+    uint32_t L = (uint32_t)(v >> 32), R = (uint32_t)v;
+    for (int r = 0; r < 48; ++r) {
+        const uint8_t* k = chunks + 8 * r;
+        uint32_t f = 0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            // S-box g reads half bits 4g .. 4g+5 (cyclic), the first one most significant
+            const uint32_t x = (rotr32(R, (27 - 4 * g) & 31) & 63u) ^ k[g];
+            f ^= sp[64 * g + x];
+        }
+        const uint32_t t = L ^ f;
+        L = R;
+        R = t;
+        if ((r & 15) == 15) {  // end of a DES pass: undo the last swap (R16 || L16)
+            const uint32_t u = L;
+            L = R;
+            R = u;
+        }
+    }
+    return permute64(((uint64_t)L << 32) | R, fp);
+}
+
+TDES_HD uint64_t bswap64(uint64_t x) {
+    x = ((x & 0x00FF00FF00FF00FFull) << 8) | ((x >> 8) & 0x00FF00FF00FF00FFull);
+    x = ((x & 0x0000FFFF0000FFFFull) << 16) | ((x >> 16) & 0x0000FFFF0000FFFFull);
+    return (x << 32) | (x >> 32);
+}

@@ -1,0 +1,45 @@
+// tdes_internal.h -- launchers shared by the C ABI (tdes_api.cu) and the
+// kernels (tdes_kernels.cu).  Not part of the public interface.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tdes {
+
+constexpr int kTileBlocks = 1024;  // blocks per warp tile: 32 lanes x 32 blocks
+constexpr int kWideWarps = 8;      // warps per CTA for large inputs
+constexpr int kTableWords = 3328;  // words of one bitsliced round-constant table
+constexpr int kChunkBytes = 384;   // 48 rounds x 8 six-bit round-key groups
+
+struct Keys24 {
+    uint8_t b[24];
+};
+
+// Launch geometry for `ntiles` warp tiles on the current device.
+struct Geometry {
+    int grid;
+    int threads;
+};
+Geometry geometry_for(uint64_t ntiles, int kernel_id, int device);
+
+enum KernelId { kEcb = 0, kCtr = 1, kCbcDec = 2, kNumKernels = 3 };
+
+cudaError_t launch_keysched(const Keys24& keys, uint32_t* tab_enc, uint32_t* tab_dec,
+                            uint8_t* chunk_enc, uint8_t* chunk_dec, cudaStream_t s);
+cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t nblocks,
+                       bool vec16, Geometry g, cudaStream_t s);
+cudaError_t launch_ctr(const uint32_t* tab_enc, uint32_t nonce, uint32_t ctr0, const void* in,
+                       void* out, uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s);
+cudaError_t launch_cbc_halo(const void* in, uint64_t* halo, uint64_t nblocks, cudaStream_t s);
+cudaError_t launch_cbc_dec(const uint32_t* tab_dec, uint64_t iv, const void* in, void* out,
+                           uint64_t nblocks, const uint64_t* halo, bool vec16, Geometry g,
+                           cudaStream_t s);
+cudaError_t launch_cbc_enc(const uint8_t* chunk_enc, uint64_t iv, const void* in, void* out,
+                           uint64_t nblocks, cudaStream_t s);
+
+// Occupancy (CTAs per SM) of a bitsliced kernel at kWideWarps warps per CTA.
+int wide_ctas_per_sm(int kernel_id);
+int sbox_gate_count();
+
+}  // namespace tdes

@@ -1,0 +1,344 @@
+// tdes_kernels.cu -- sm_103a kernels of the 3DES-EDE3 library.
+//
+// Work unit: a warp tile of 1024 consecutive 64-bit blocks (8 KiB).  Lane l
+// of the warp owns the 32 blocks 2*(32*j + l) + h (j = 0..15, h = 0..1) of
+// the tile, so every 128-bit load or store instruction of the warp covers
+// 512 contiguous bytes.  The lane bitslices its 32 blocks in registers
+// (tdes_bitslice.cuh), runs the 48 rounds of EDE3 as LOP3 logic on 64
+// bit-planes, and un-bitslices.  The per-key round-constant table is staged
+// into shared memory once per CTA and read with broadcast 128-bit loads.
+#include <cuda_runtime.h>
+
+#include "tdes_internal.h"
+#include "tdes_keysched.cuh"
+
+namespace tdes {
+
+static_assert(kTableWords == TDES_TABLE_WORDS, "table size mismatch with the generator");
+static_assert(kChunkBytes == TDES_SUBKEY_WORDS, "chunk size mismatch");
+
+__device__ const uint8_t kRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
+__device__ const uint8_t kSubkeyBits[2][48][48] = TDES_SUBKEY_INIT;
+__device__ const uint32_t kSP[8][64] = TDES_SP_INIT;
+__device__ const uint8_t kIPsrc[64] = TDES_IP_INIT;
+__device__ const uint8_t kFPsrc[64] = TDES_FP_INIT;
+
+int sbox_gate_count() { return TDES_SBOX_GATES; }
+
+// ------------------------------------------------------------ key schedule
+// One thread per output word: 2 bitsliced tables then 2 chunk tables.
+__global__ void tdes_keysched_kernel(Keys24 keys, uint32_t* __restrict__ tab_enc,
+                                     uint32_t* __restrict__ tab_dec, uint8_t* __restrict__ ch_enc,
+                                     uint8_t* __restrict__ ch_dec) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < 2 * TDES_TABLE_WORDS) {
+        const int dir = e / TDES_TABLE_WORDS, w = e % TDES_TABLE_WORDS;
+        (dir ? tab_dec : tab_enc)[w] = tdes_table_word(keys.b, kRecipe[dir][w]);
+    } else if (e < 2 * TDES_TABLE_WORDS + 2 * TDES_SUBKEY_WORDS) {
+        const int f = e - 2 * TDES_TABLE_WORDS;
+        const int dir = f / TDES_SUBKEY_WORDS, c = f % TDES_SUBKEY_WORDS;
+        const int r = c / 8, g = c % 8;
+        (dir ? ch_dec : ch_enc)[c] = tdes_subkey_chunk(keys.b, &kSubkeyBits[dir][r][6 * g]);
+    }
+}
+
+cudaError_t launch_keysched(const Keys24& keys, uint32_t* tab_enc, uint32_t* tab_dec,
+                            uint8_t* chunk_enc, uint8_t* chunk_dec, cudaStream_t s) {
+    const int n = 2 * TDES_TABLE_WORDS + 2 * TDES_SUBKEY_WORDS;
+    tdes_keysched_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, tab_enc, tab_dec, chunk_enc,
+                                                          chunk_dec);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ tile helpers
+
+__device__ __forceinline__ void stage_table(uint32_t* __restrict__ dst,
+                                            const uint32_t* __restrict__ src) {
+    for (int i = 4 * threadIdx.x; i < TDES_TABLE_WORDS; i += 4 * blockDim.x)
+        *reinterpret_cast<uint4*>(dst + i) = __ldg(reinterpret_cast<const uint4*>(src + i));
+}
+
+// Slot s = 2j + h of a lane holds tile block 2*(32j + lane) + h.
+template <bool VEC>
+__device__ __forceinline__ void load_tile(const uint8_t* base, uint64_t b0, uint64_t nblocks,
+                                          uint32_t lane, uint32_t (&A0)[32], uint32_t (&A1)[32]) {
+    if (VEC && b0 + kTileBlocks <= nblocks) {
+        const uint4* p = reinterpret_cast<const uint4*>(base) + (b0 >> 1) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint4 v = __ldcs(p + 32 * j);
+            A0[2 * j] = v.x;
+            A1[2 * j] = v.y;
+            A0[2 * j + 1] = v.z;
+            A1[2 * j + 1] = v.w;
+        }
+    } else {
+        const uint2* p = reinterpret_cast<const uint2*>(base);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t b = b0 + 2 * (32 * j + lane) + h;
+                uint2 v = make_uint2(0u, 0u);
+                if (b < nblocks) v = __ldcs(p + b);
+                A0[2 * j + h] = v.x;
+                A1[2 * j + h] = v.y;
+            }
+    }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void store_tile(uint8_t* base, uint64_t b0, uint64_t nblocks,
+                                           uint32_t lane, const uint32_t (&A0)[32],
+                                           const uint32_t (&A1)[32]) {
+    if (VEC && b0 + kTileBlocks <= nblocks) {
+        uint4* p = reinterpret_cast<uint4*>(base) + (b0 >> 1) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            __stcs(p + 32 * j, make_uint4(A0[2 * j], A1[2 * j], A0[2 * j + 1], A1[2 * j + 1]));
+    } else {
+        uint2* p = reinterpret_cast<uint2*>(base);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t b = b0 + 2 * (32 * j + lane) + h;
+                if (b < nblocks) __stcs(p + b, make_uint2(A0[2 * j + h], A1[2 * j + h]));
+            }
+    }
+}
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0u, 0x0123); }
+
+// ------------------------------------------------------------------- ECB
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2)
+tdes_ecb_kernel(const uint32_t* __restrict__ table, const uint8_t* in, uint8_t* out,
+                uint64_t nblocks) {
+    __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
+    stage_table(tab, table);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = blockDim.x >> 5;
+    const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
+    for (uint64_t t = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles;
+         t += (uint64_t)gridDim.x * warps) {
+        uint32_t A0[32], A1[32];
+        load_tile<VEC>(in, t * kTileBlocks, nblocks, lane, A0, A1);
+        tdes_process32(A0, A1, tab);
+        store_tile<VEC>(out, t * kTileBlocks, nblocks, lane, A0, A1);
+    }
+}
+
+cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t nblocks,
+                       bool vec16, Geometry g, cudaStream_t s) {
+    if (vec16)
+        tdes_ecb_kernel<true><<<g.grid, g.threads, 0, s>>>(
+            tab, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks);
+    else
+        tdes_ecb_kernel<false><<<g.grid, g.threads, 0, s>>>(
+            tab, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- CTR
+// Keystream block i = E(nonce || ctr0 + i); the counter blocks are built in
+// registers, then the data tile is loaded and XORed on the way out.
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2)
+tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr0,
+                const uint8_t* in, uint8_t* out, uint64_t nblocks) {
+    __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
+    stage_table(tab, table);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = blockDim.x >> 5;
+    const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
+    const uint32_t nw = bswap32(nonce);
+    for (uint64_t t = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles;
+         t += (uint64_t)gridDim.x * warps) {
+        const uint64_t b0 = t * kTileBlocks;
+        uint32_t A0[32], A1[32];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t b = (uint32_t)b0 + 2u * (32u * j + lane) + h;
+                A0[2 * j + h] = nw;
+                A1[2 * j + h] = bswap32(ctr0 + b);
+            }
+        tdes_process32(A0, A1, tab);
+        if (VEC && b0 + kTileBlocks <= nblocks) {
+            const uint4* p = reinterpret_cast<const uint4*>(in) + (b0 >> 1) + lane;
+            uint4* q = reinterpret_cast<uint4*>(out) + (b0 >> 1) + lane;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint4 v = __ldcs(p + 32 * j);
+                __stcs(q + 32 * j, make_uint4(v.x ^ A0[2 * j], v.y ^ A1[2 * j],
+                                              v.z ^ A0[2 * j + 1], v.w ^ A1[2 * j + 1]));
+            }
+        } else {
+            const uint2* p = reinterpret_cast<const uint2*>(in);
+            uint2* q = reinterpret_cast<uint2*>(out);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t b = b0 + 2 * (32 * j + lane) + h;
+                    if (b < nblocks) {
+                        const uint2 v = __ldcs(p + b);
+                        __stcs(q + b, make_uint2(v.x ^ A0[2 * j + h], v.y ^ A1[2 * j + h]));
+                    }
+                }
+        }
+    }
+}
+
+cudaError_t launch_ctr(const uint32_t* tab_enc, uint32_t nonce, uint32_t ctr0, const void* in,
+                       void* out, uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s) {
+    if (vec16)
+        tdes_ctr_kernel<true><<<g.grid, g.threads, 0, s>>>(
+            tab_enc, nonce, ctr0, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out),
+            nblocks);
+    else
+        tdes_ctr_kernel<false><<<g.grid, g.threads, 0, s>>>(
+            tab_enc, nonce, ctr0, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out),
+            nblocks);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- CBC decrypt
+// halo[t] = ciphertext block just before tile t (t >= 1), taken before an
+// in-place decryption can overwrite it.
+__global__ void tdes_cbc_halo_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ halo,
+                                     uint64_t ntiles) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 1 && t < ntiles) halo[t] = in[t * kTileBlocks - 1];
+}
+
+cudaError_t launch_cbc_halo(const void* in, uint64_t* halo, uint64_t nblocks, cudaStream_t s) {
+    const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
+    if (ntiles <= 1) return cudaSuccess;
+    tdes_cbc_halo_kernel<<<(unsigned)((ntiles + 255) / 256), 256, 0, s>>>(
+        static_cast<const uint64_t*>(in), halo, ntiles);
+    return cudaGetLastError();
+}
+
+// P_i = D(C_i) XOR C_{i-1}.  The ciphertext the XOR needs is re-read after
+// the rounds: a lane's own blocks and its neighbours' in the same tile are
+// still intact (the warp stores only after __syncwarp); the block before the
+// tile comes from `halo` when decrypting in place, else from the input.
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2)
+tdes_cbc_dec_kernel(const uint32_t* __restrict__ table, uint64_t iv, const uint8_t* in,
+                    uint8_t* out, uint64_t nblocks, const uint64_t* __restrict__ halo) {
+    __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
+    stage_table(tab, table);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = blockDim.x >> 5;
+    const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
+    const uint2 ivw = make_uint2(bswap32((uint32_t)(iv >> 32)), bswap32((uint32_t)iv));
+    const uint2* c = reinterpret_cast<const uint2*>(in);
+    for (uint64_t t = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles;
+         t += (uint64_t)gridDim.x * warps) {
+        const uint64_t b0 = t * kTileBlocks;
+        uint32_t A0[32], A1[32];
+        load_tile<VEC>(in, b0, nblocks, lane, A0, A1);
+        tdes_process32(A0, A1, tab);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint64_t b = b0 + 2 * (32 * j + lane);  // slot 2j; slot 2j+1 is b + 1
+            uint2 prev0, prev1 = make_uint2(0u, 0u);
+            if (b == 0) {
+                prev0 = ivw;
+            } else if (j == 0 && lane == 0) {
+                if (halo != nullptr) {
+                    const uint64_t hv = halo[t];
+                    prev0 = make_uint2((uint32_t)hv, (uint32_t)(hv >> 32));
+                } else {
+                    prev0 = c[b - 1];
+                }
+            } else {
+                prev0 = (b - 1 < nblocks) ? c[b - 1] : make_uint2(0u, 0u);
+            }
+            if (b < nblocks) prev1 = c[b];
+            A0[2 * j] ^= prev0.x;
+            A1[2 * j] ^= prev0.y;
+            A0[2 * j + 1] ^= prev1.x;
+            A1[2 * j + 1] ^= prev1.y;
+        }
+        __syncwarp();
+        store_tile<VEC>(out, b0, nblocks, lane, A0, A1);
+    }
+}
+
+cudaError_t launch_cbc_dec(const uint32_t* tab_dec, uint64_t iv, const void* in, void* out,
+                           uint64_t nblocks, const uint64_t* halo, bool vec16, Geometry g,
+                           cudaStream_t s) {
+    if (vec16)
+        tdes_cbc_dec_kernel<true><<<g.grid, g.threads, 0, s>>>(
+            tab_dec, iv, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks,
+            halo);
+    else
+        tdes_cbc_dec_kernel<false><<<g.grid, g.threads, 0, s>>>(
+            tab_dec, iv, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks,
+            halo);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- CBC encrypt
+// C_i = E(P_i XOR C_{i-1}): serial, one thread walks the chain with the
+// scalar round (S-box/permutation words in shared memory).
+__global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64_t iv,
+                                    const uint8_t* in, uint8_t* out, uint64_t nblocks) {
+    __shared__ uint32_t sp[8 * 64];
+    __shared__ uint8_t ch[TDES_SUBKEY_WORDS];
+    __shared__ uint8_t ip[64], fp[64];
+    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) sp[i] = (&kSP[0][0])[i];
+    for (int i = threadIdx.x; i < TDES_SUBKEY_WORDS; i += blockDim.x) ch[i] = chunks_g[i];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        ip[i] = kIPsrc[i];
+        fp[i] = kFPsrc[i];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const uint64_t* p = reinterpret_cast<const uint64_t*>(in);
+    uint64_t* q = reinterpret_cast<uint64_t*>(out);
+    uint64_t prev = iv;
+    for (uint64_t i = 0; i < nblocks; ++i) {
+        const uint64_t x = bswap64(p[i]) ^ prev;
+        prev = tdes_block_scalar(x, sp, ch, ip, fp);
+        q[i] = bswap64(prev);
+    }
+}
+
+cudaError_t launch_cbc_enc(const uint8_t* chunk_enc, uint64_t iv, const void* in, void* out,
+                           uint64_t nblocks, cudaStream_t s) {
+    tdes_cbc_enc_kernel<<<1, 32, 0, s>>>(chunk_enc, iv, static_cast<const uint8_t*>(in),
+                                         static_cast<uint8_t*>(out), nblocks);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- occupancy
+int wide_ctas_per_sm(int kernel_id) {
+    int n = 0;
+    const int threads = 32 * kWideWarps;
+    cudaError_t e = cudaSuccess;
+    switch (kernel_id) {
+        case kEcb:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ecb_kernel<true>, threads, 0);
+            break;
+        case kCtr:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ctr_kernel<true>, threads, 0);
+            break;
+        default:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_cbc_dec_kernel<true>,
+                                                              threads, 0);
+            break;
+    }
+    if (e != cudaSuccess || n < 1) return 1;
+    return n;
+}
+
+}  // namespace tdes

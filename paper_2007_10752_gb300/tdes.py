@@ -1,0 +1,195 @@
+"""Thin ctypes binding of the C ABI in include/tdes.h (argument marshalling only).
+
+Every function takes the same arguments as its C counterpart, with torch
+tensors standing in for device pointers (uint8, contiguous, on the key
+schedule's device) and the current torch stream standing in for the
+cudaStream_t unless one is given.  All cipher work runs in the CUDA kernels
+of libtdes_gb300.so; if that library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdes_gb300.so")
+
+TDES_OK = 0
+TDES_EINVAL = -1
+TDES_ENOMEM = -2
+TDES_EBUSY = -3
+TDES_ETIMEDOUT = -4
+TDES_ECUDA = -5
+
+# every symbol include/tdes.h declares
+EXPORTED = (
+    "tdes_key_schedule", "tdes_key_free", "tdes_ecb_encrypt", "tdes_ecb_decrypt",
+    "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_ecb_crypt_host",
+    "tdes_sbox_gate_count", "tdes_strerror", "tdes_last_error",
+)
+
+_lib = None
+
+
+class TdesError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"tdes status {status}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (built by paper_2007_10752_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run python -m paper_2007_10752_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, sz, u32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.tdes_key_schedule.argtypes = [u8p, u8p, u8p, ctypes.POINTER(vp)]
+    lib.tdes_key_free.argtypes = [vp]
+    lib.tdes_key_free.restype = None
+    for name in ("tdes_ecb_encrypt", "tdes_ecb_decrypt"):
+        getattr(lib, name).argtypes = [vp, vp, vp, sz, vp]
+    lib.tdes_ctr_crypt.argtypes = [vp, u32, u32, vp, vp, sz, vp]
+    lib.tdes_cbc_decrypt.argtypes = [vp, u64, vp, vp, sz, vp]
+    lib.tdes_cbc_encrypt.argtypes = [vp, u64, vp, vp, sz, vp]
+    lib.tdes_ecb_crypt_host.argtypes = [vp, ctypes.c_int, vp, vp, sz, vp, sz]
+    lib.tdes_sbox_gate_count.argtypes = []
+    lib.tdes_strerror.argtypes = [ctypes.c_int]
+    lib.tdes_strerror.restype = ctypes.c_char_p
+    lib.tdes_last_error.argtypes = []
+    lib.tdes_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != TDES_OK:
+        msg = load().tdes_last_error().decode(errors="replace")
+        raise TdesError(status, msg)
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a tensor / ndarray / int."""
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _nbytes(t) -> int:
+    if isinstance(t, np.ndarray):
+        return t.nbytes
+    return t.numel() * t.element_size()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class KeySchedule:
+    """Owns a tdes_ks_t built by tdes_key_schedule on the current device."""
+
+    def __init__(self, k1: bytes, k2: bytes, k3: bytes):
+        lib = load()
+        if len(k1) != 8 or len(k2) != 8 or len(k3) != 8:
+            raise ValueError("each key is 8 bytes")
+        bufs = [(ctypes.c_uint8 * 8).from_buffer_copy(bytes(k)) for k in (k1, k2, k3)]
+        h = ctypes.c_void_p()
+        _check(lib.tdes_key_schedule(*[ctypes.cast(b, ctypes.POINTER(ctypes.c_uint8))
+                                       for b in bufs], ctypes.byref(h)))
+        self.handle = h.value
+
+    @classmethod
+    def from_triple(cls, keys24) -> "KeySchedule":
+        k = bytes(keys24)
+        if len(k) != 24:
+            raise ValueError("a key triple is 24 bytes")
+        return cls(k[:8], k[8:16], k[16:])
+
+    def free(self):
+        if self.handle:
+            load().tdes_key_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _io(inp, out):
+    n = _nbytes(inp)
+    if out is None:
+        out = inp.new_empty(inp.shape) if not isinstance(inp, np.ndarray) else np.empty_like(inp)
+    if _nbytes(out) < n:
+        raise ValueError("output smaller than input")
+    return out, n
+
+
+def tdes_ecb_encrypt(ks: KeySchedule, inp, out=None, stream=None, nbytes=None):
+    out, n = _io(inp, out)
+    _check(load().tdes_ecb_encrypt(ks.handle, _ptr(inp), _ptr(out),
+                                   n if nbytes is None else nbytes, _stream(stream)))
+    return out
+
+
+def tdes_ecb_decrypt(ks: KeySchedule, inp, out=None, stream=None, nbytes=None):
+    out, n = _io(inp, out)
+    _check(load().tdes_ecb_decrypt(ks.handle, _ptr(inp), _ptr(out),
+                                   n if nbytes is None else nbytes, _stream(stream)))
+    return out
+
+
+def tdes_ctr_crypt(ks: KeySchedule, nonce: int, ctr0: int, inp, out=None, stream=None,
+                   nbytes=None):
+    out, n = _io(inp, out)
+    _check(load().tdes_ctr_crypt(ks.handle, nonce & 0xFFFFFFFF, ctr0 & 0xFFFFFFFF, _ptr(inp),
+                                 _ptr(out), n if nbytes is None else nbytes, _stream(stream)))
+    return out
+
+
+def tdes_cbc_decrypt(ks: KeySchedule, iv: int, inp, out=None, stream=None, nbytes=None):
+    out, n = _io(inp, out)
+    _check(load().tdes_cbc_decrypt(ks.handle, iv & (2**64 - 1), _ptr(inp), _ptr(out),
+                                   n if nbytes is None else nbytes, _stream(stream)))
+    return out
+
+
+def tdes_cbc_encrypt(ks: KeySchedule, iv: int, inp, out=None, stream=None, nbytes=None):
+    out, n = _io(inp, out)
+    _check(load().tdes_cbc_encrypt(ks.handle, iv & (2**64 - 1), _ptr(inp), _ptr(out),
+                                   n if nbytes is None else nbytes, _stream(stream)))
+    return out
+
+
+def tdes_ecb_crypt_host(ks: KeySchedule, decrypt: bool, host_in, host_out, dev_buf,
+                        nbytes=None):
+    """Host buffers in and out (numpy arrays or CPU tensors, ideally pinned)."""
+    n = _nbytes(host_in) if nbytes is None else nbytes
+    _check(load().tdes_ecb_crypt_host(ks.handle, int(bool(decrypt)), _ptr(host_in),
+                                      _ptr(host_out), n, _ptr(dev_buf), _nbytes(dev_buf)))
+    return host_out
+
+
+def tdes_sbox_gate_count() -> int:
+    return int(load().tdes_sbox_gate_count())
+
+
+def tdes_strerror(status: int) -> str:
+    return load().tdes_strerror(status).decode()
