@@ -94,6 +94,30 @@ int tdes_cbc_decrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out
 int tdes_cbc_encrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out,
                      size_t nbytes, tdes_stream_t stream);
 
+/* Allocation-free CBC decryption.  The paper has no counterpart: this is a
+ * deployment variant of tdes_cbc_decrypt for callers that must not have the
+ * library allocate device memory -- for example a server that reserves the
+ * GPU's memory for its own pool at start-up and cannot let a request fail on
+ * an allocation, or a host framework that gives its plugins pre-sized
+ * buffers and forbids allocation on the hot path.  Same arguments and result
+ * as tdes_cbc_decrypt.  An in-place call (in == out) saves the ciphertext
+ * block before each 8 KiB tile in a fixed scratch array compiled into the
+ * library (8 bytes per tile, TDES_NOALLOC_MAX_TILES tiles = 1 MiB of device
+ * memory, held on every device that loads the library until the process
+ * exits); in-place calls larger than TDES_NOALLOC_MAX_BYTES return
+ * TDES_EINVAL.  Out-of-place calls use no scratch and have no size limit.
+ * The call never calls cudaMalloc, cudaFree or any allocating routine.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: two in-place
+ * calls that overlap in time on the GPU (different streams, no ordering
+ * between them) race on it and may return wrong plaintext.  Nothing in the
+ * array needs clearing: each call writes every entry it reads first. */
+#define TDES_NOALLOC_MAX_TILES 131072
+#define TDES_NOALLOC_MAX_BYTES ((uint64_t)TDES_NOALLOC_MAX_TILES * 8192u)
+int tdes_cbc_decrypt_noalloc(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out,
+                             size_t nbytes, tdes_stream_t stream);
+
 /* Host-buffer ECB: encrypts (decrypt == 0) or decrypts host memory
  * host_in[0, nbytes) into host_out, streaming it through the caller's device
  * buffer dev_buf of dev_bytes bytes (at least 2 x 64 KiB, 16-byte aligned):

@@ -12,13 +12,6 @@
 #include "../../include/tdes.h"
 #include "tdes_internal.h"
 
-struct tdes_ks {
-    int device;
-    void* mem;              // one cudaMalloc holding everything below
-    uint32_t* tab[2];       // bitsliced round-constant tables: [0] encrypt, [1] decrypt
-    uint8_t* chunk[2];      // scalar-path round-key groups: [0] encrypt, [1] decrypt
-};
-
 namespace {
 
 thread_local std::string g_last_error;
@@ -88,6 +81,8 @@ bool aligned16(const void* in, const void* out) {
 }  // namespace
 
 namespace tdes {
+
+void set_last_error(const char* msg) { g_last_error = msg; }
 
 // Small inputs: one warp per CTA so the few tiles spread over many SMs.
 // Large inputs: kWideWarps warps per CTA, a grid of every resident CTA,

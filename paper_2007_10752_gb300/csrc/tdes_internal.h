@@ -5,7 +5,18 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// The library's key-schedule object (opaque tdes_ks_t in include/tdes.h).
+struct tdes_ks {
+    int device;
+    void* mem;              // one cudaMalloc holding everything below
+    uint32_t* tab[2];       // bitsliced round-constant tables: [0] encrypt, [1] decrypt
+    uint8_t* chunk[2];      // scalar-path round-key groups: [0] encrypt, [1] decrypt
+};
+
 namespace tdes {
+
+// Records the message tdes_last_error() returns on this host thread.
+void set_last_error(const char* msg);
 
 constexpr int kTileBlocks = 1024;  // blocks per warp tile: 32 lanes x 32 blocks
 constexpr int kWideWarps = 8;      // warps per CTA for large inputs

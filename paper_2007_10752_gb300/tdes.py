@@ -26,7 +26,8 @@ TDES_ECUDA = -5
 # every symbol include/tdes.h declares
 EXPORTED = (
     "tdes_key_schedule", "tdes_key_free", "tdes_ecb_encrypt", "tdes_ecb_decrypt",
-    "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_ecb_crypt_host",
+    "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_cbc_decrypt_noalloc",
+    "tdes_ecb_crypt_host",
     "tdes_sbox_gate_count", "tdes_strerror", "tdes_last_error",
 )
 
@@ -57,6 +58,7 @@ def load(path: str = LIB_PATH):
     lib.tdes_ctr_crypt.argtypes = [vp, u32, u32, vp, vp, sz, vp]
     lib.tdes_cbc_decrypt.argtypes = [vp, u64, vp, vp, sz, vp]
     lib.tdes_cbc_encrypt.argtypes = [vp, u64, vp, vp, sz, vp]
+    lib.tdes_cbc_decrypt_noalloc.argtypes = [vp, u64, vp, vp, sz, vp]
     lib.tdes_ecb_crypt_host.argtypes = [vp, ctypes.c_int, vp, vp, sz, vp, sz]
     lib.tdes_sbox_gate_count.argtypes = []
     lib.tdes_strerror.argtypes = [ctypes.c_int]
@@ -176,6 +178,23 @@ def tdes_cbc_encrypt(ks: KeySchedule, iv: int, inp, out=None, stream=None, nbyte
     _check(load().tdes_cbc_encrypt(ks.handle, iv & (2**64 - 1), _ptr(inp), _ptr(out),
                                    n if nbytes is None else nbytes, _stream(stream)))
     return out
+
+
+def tdes_cbc_decrypt_noalloc(ks: KeySchedule, iv: int, inp, out=None, stream=None, nbytes=None):
+    """CBC decryption that makes the library allocate nothing (see include/tdes.h).
+
+    For callers that cannot let a library allocate device memory, e.g. a
+    server whose memory pool owns the GPU.  In-place calls keep their scratch
+    in a fixed 1 MiB array inside the library (limit TDES_NOALLOC_MAX_BYTES);
+    in-place calls that overlap in time on the GPU race on that array.
+    """
+    out, n = _io(inp, out)
+    _check(load().tdes_cbc_decrypt_noalloc(ks.handle, iv & (2**64 - 1), _ptr(inp), _ptr(out),
+                                           n if nbytes is None else nbytes, _stream(stream)))
+    return out
+
+
+TDES_NOALLOC_MAX_BYTES = 131072 * 8192
 
 
 def tdes_ecb_crypt_host(ks: KeySchedule, decrypt: bool, host_in, host_out, dev_buf,
