@@ -278,6 +278,9 @@ def run_ours(args):
     small_in, small_out = x[: 1 << 20], y[: 1 << 20]
     small_us = time_fn(lambda: tdes.tdes_ecb_encrypt(ks, small_in, small_out), 200) * 1e3
 
+    # ---- batched: 4096 messages with their own keys and modes, one launch
+    batched = None if args.no_batch else run_batched(torch, tdes, synth, stream, value)
+
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -339,6 +342,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
+        "batched": batched,
         "extra": {"kernel_ms_per_launch": round(per_launch_ms, 4),
                   "ecb_decrypt_gbs": round(NBYTES / (dec_ms * 1e-3) / 1e9, 3),
                   "ctr_gbs": round(NBYTES / (ctr_ms * 1e-3) / 1e9, 3),
@@ -351,6 +355,85 @@ def run_ours(args):
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- batched
+BATCH_WORKLOAD = ("4096 messages, lengths log-uniform 64 B..4 MiB (multiples of 8), uniform "
+                  "random payloads, own seeded key triple each, modes ECB 40% / CTR 30% / "
+                  "CBC-decrypt 20% / CBC-encrypt 10%, seeded IVs; one persistent launch "
+                  "replayed as a CUDA graph")
+
+
+def build_config3(torch, tdes, synth, seed=3, n=4096, modes_probs=(0.4, 0.3, 0.2, 0.1)):
+    lens = synth.log_uniform_lengths(seed, n, 64, 4 << 20)
+    modes = np.array([0, 2, 3, 4])[synth.categorical(seed, n, list(modes_probs),
+                                                     synth.STREAM_MODE)]
+    keys = synth.key_triples(seed, n)
+    ivs = synth.u64s(seed, n, synth.STREAM_IV)
+    offs = np.concatenate([[0], np.cumsum((lens + 15) // 16 * 16)])[:-1]
+    total = int(offs[-1] + lens[-1] + 16)
+    src = torch.from_numpy(synth.random_bytes(seed, (total + 7) // 8 * 8)).cuda()
+    dst = torch.empty_like(src)
+    kt = tdes.KeyTable(keys)
+    ents = []
+    for i in range(n):
+        iv = int(ivs[i]) & (0xFFFFFFFF00000000 if modes[i] == 2 else 0xFFFFFFFFFFFFFFFF)
+        ents.append((int(modes[i]), i, iv, src.data_ptr() + int(offs[i]),
+                     dst.data_ptr() + int(offs[i]), int(lens[i])))
+    return src, dst, kt, ents, lens, modes
+
+
+def time_graph(torch, batch, stream, reps):
+    batch.launch_graph(stream)  # capture + warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        batch.launch_graph(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_batched(torch, tdes, synth, stream, ecb_gbs):
+    """Config-3 batch: whole-batch makespan, and the parallel modes alone."""
+    src, dst, kt, ents, lens, modes = build_config3(torch, tdes, synth)
+    total = int(lens.sum())
+    par = [e for e in ents if e[0] != 4]
+    par_bytes = sum(e[5] for e in par)
+    # autotune the launch shape on the parallel-mode part (the throughput part)
+    bpar = tdes.Batch(kt, par)
+    best = None
+    for shape in ((8, 0), (8, 1), (6, 0), (4, 0)):
+        bpar.configure(*shape)
+        ms = time_graph(torch, bpar, stream, 5)
+        if best is None or ms < best[1]:
+            best = (shape, ms)
+    bpar.configure(*best[0])
+    par_ms = time_graph(torch, bpar, stream, 20)
+    ball = tdes.Batch(kt, ents)
+    ball.configure(*best[0])
+    all_ms = time_graph(torch, ball, stream, 2)
+    cbc = [e for e in ents if e[0] == 4]
+    longest = max((e[5] for e in cbc), default=0)
+    bc = tdes.Batch(kt, [max(cbc, key=lambda e: e[5])]) if cbc else None
+    chain_ms = time_graph(torch, bc, stream, 2) if bc else 0.0
+    par_gbs = par_bytes / (par_ms * 1e-3) / 1e9
+    info = ball.info()
+    return {
+        "workload": BATCH_WORKLOAD,
+        "messages": len(ents), "bytes": total,
+        "makespan_ms": round(all_ms, 3), "makespan_gbs": round(total / (all_ms * 1e-3) / 1e9, 3),
+        "parallel_modes_bytes": par_bytes, "parallel_modes_ms": round(par_ms, 3),
+        "parallel_modes_gbs": round(par_gbs, 3),
+        "parallel_modes_vs_plain_ecb": round(par_gbs / ecb_gbs, 4),
+        "cbc_encrypt_longest_bytes": longest,
+        "cbc_encrypt_longest_chain_ms": round(chain_ms, 3),
+        "cbc_encrypt_ns_per_block": round(chain_ms * 1e6 / max(1, longest // 8), 1),
+        "autotuned_shape": {"warps_per_cta": best[0][0], "ctas_per_sm": info["ctas_per_sm"]},
+        "tiles": info["n_tiles"], "small_items": info["n_small_items"],
+        "cbc_encrypt_messages": info["n_cbc_enc_messages"],
+    }
 
 
 # ------------------------------------------------------------- reference
@@ -402,6 +485,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -128,6 +128,80 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t *ks, uint64_t iv, const void *in, v
 int tdes_ecb_crypt_host(const tdes_ks_t *ks, int decrypt, const void *host_in, void *host_out,
                         size_t nbytes, void *dev_buf, size_t dev_bytes);
 
+/* ------------------------------------------------------------------------
+ * Batches: many messages, each with its own key triple and mode, in one
+ * persistent launch.  Not in the paper (which encrypts one file under one
+ * key triple in ECB, Sec. V); the cipher of every message is the same EDE3.
+ * ------------------------------------------------------------------------ */
+
+#define TDES_MODE_ECB_ENCRYPT 0u
+#define TDES_MODE_ECB_DECRYPT 1u
+#define TDES_MODE_CTR 2u          /* counter blocks: iv_or_ctr + i on the low 32 bits */
+#define TDES_MODE_CBC_DECRYPT 3u
+#define TDES_MODE_CBC_ENCRYPT 4u
+
+typedef struct tdes_keytable tdes_keytable_t; /* opaque: device-resident key schedules */
+typedef struct tdes_batch tdes_batch_t;       /* opaque: a planned batch */
+
+/* One message of a batch.  in/out: device pointers, 8-byte aligned, equal
+ * (in place) or disjoint; nbytes a multiple of 8 (0 = nothing to do).
+ * iv_or_ctr: the CBC IV, or for CTR the first counter block
+ * (nonce << 32 | ctr0; block i uses nonce || ctr0 + i, which must not pass
+ * 2^32).  Messages of one batch must not overlap each other. */
+typedef struct {
+    uint32_t mode;      /* TDES_MODE_* */
+    uint32_t key_index; /* key triple in the key table */
+    uint64_t iv_or_ctr;
+    const void *in;
+    void *out;
+    uint64_t nbytes;
+} tdes_desc_t;
+
+typedef struct {
+    uint32_t n_cbc_enc_messages; /* serial chains, one GPU lane each */
+    uint64_t n_tiles;            /* bitsliced 1024-block tiles of large messages */
+    uint32_t n_small_items;      /* warp items of small (<= 32-block) messages */
+    int warps_per_cta;
+    int ctas_per_sm;
+    uint64_t bytes_per_mode[5];  /* payload bytes, indexed by TDES_MODE_* */
+} tdes_batch_info_t;
+
+/* Key schedules (Sec. III-A) of `count` triples (keys: count x 24 bytes,
+ * K1||K2||K3 each) computed by one key-schedule kernel and kept in device
+ * memory (27392 bytes per triple) on the current device.  Synchronous.  The
+ * raw keys are not kept.  Free with tdes_keytable_free(). */
+int tdes_keytable_create(const uint8_t *keys, uint32_t count, tdes_keytable_t **out);
+void tdes_keytable_free(tdes_keytable_t *kt);
+
+/* Validates `count` descriptors and lays the batch out in device memory
+ * (synchronous; the plan can be launched many times).  per_desc_status
+ * (nullable, count entries) receives TDES_OK or TDES_EINVAL per descriptor:
+ * bad mode, key index, size, alignment, overlap or CTR counter range.
+ * Rejected descriptors are skipped; the call still returns TDES_OK with the
+ * plan of the valid ones (tdes_last_error() then counts the rejections).
+ * Messages are classified: CBC encryption (serial chains), large messages
+ * (more than 32 blocks: bitsliced tiles) and small ones (scalar blocks). */
+int tdes_batch_plan(const tdes_keytable_t *kt, const tdes_desc_t *descs, uint32_t count,
+                    int *per_desc_status, tdes_batch_t **out);
+
+/* Launch shape of the persistent kernel: warps per CTA (1..8; each warp owns
+ * a 13 KB shared-memory slice) and CTAs per SM (<= 0: as many as fit). */
+int tdes_batch_configure(tdes_batch_t *b, int warps_per_cta, int ctas_per_sm);
+
+/* Runs the whole batch on `stream`: one persistent launch whose warps claim
+ * work items from an atomic counter (preceded by a small snapshot launch
+ * when a large message is CBC-decrypted in place).  Asynchronous. */
+int tdes_batch_launch(tdes_batch_t *b, tdes_stream_t stream);
+
+/* The same work as one CUDA graph: captured on first use (and after
+ * tdes_batch_configure), replayed by later calls.  Asynchronous. */
+int tdes_batch_launch_graph(tdes_batch_t *b, tdes_stream_t stream);
+
+int tdes_batch_info(const tdes_batch_t *b, tdes_batch_info_t *info);
+
+/* Frees a plan; no launch of it may still be running. */
+void tdes_batch_free(tdes_batch_t *b);
+
 /* Number of LOP3 instructions the eight generated S-box circuits take per
  * round, i.e. per 32 blocks per round (the circuit size fixed at build time). */
 int tdes_sbox_gate_count(void);

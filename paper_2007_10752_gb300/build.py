@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtdes_gb300.so")
 PROBE_LIB = os.path.join(HERE, "libtdes_probe.so")  # benchmark's LOP3-rate probe, not the cipher
-SOURCES = ["tdes_api.cu", "tdes_kernels.cu", "tdes_noalloc.cu"]
+SOURCES = ["tdes_api.cu", "tdes_kernels.cu", "tdes_noalloc.cu", "tdes_batch.cu"]
 PROBE_SOURCES = ["tdes_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
@@ -37,6 +37,7 @@ def nvcc() -> str:
 def _inputs():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
     files += [os.path.join(CSRC, "generated", "tdes_generated.cuh"),
+              os.path.join(CSRC, "generated", "tdes_generated_scalar.cuh"),
               os.path.join(ROOT, "include", "tdes.h")]
     gen = os.path.join(HERE, "gen")
     files += [os.path.join(gen, f) for f in ("des_tables.py", "emit_cuda.py", "sbox_lop3.json")]

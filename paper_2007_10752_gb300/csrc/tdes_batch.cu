@@ -1,0 +1,706 @@
+// tdes_batch.cu -- many messages, each with its own key triple and mode, in
+// one persistent launch.
+//
+// A planned batch holds three kinds of work item, claimed by warps through
+// one global atomic counter (dynamic load balancing, no waiting between
+// warps):
+//   C  CBC-encryption chains: one lane per message, 32 messages per item,
+//      longest first (each block needs the previous ciphertext, so a chain
+//      is serial; these items are claimed first because they are the
+//      critical path);
+//   B  bitsliced warp tiles of 1024 blocks of one "large" message (more than
+//      32 blocks) in ECB, CTR or CBC-decrypt mode; the warp stages that
+//      message's 13 KB round-constant table in its own slice of shared
+//      memory and keeps it while consecutive tiles share the key;
+//   S  "small" messages (at most 32 blocks) packed whole, one block per lane,
+//      run with the scalar round (their bytes are a tiny share of any
+//      workload here, and a 1024-block tile would leave most lanes idle).
+// The per-key tables live in a device-resident key table built by the
+// key-schedule kernel for every triple at once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/tdes.h"
+#include "tdes_internal.h"
+#include "tdes_keysched.cuh"
+
+namespace tdes {
+
+constexpr int kSmallBlocks = 32;                          // S messages: nblocks <= this
+constexpr int kPerKeyWords = 2 * TDES_TABLE_WORDS;        // enc + dec bitsliced tables
+constexpr int kPerKeyChunks = 2 * TDES_SUBKEY_WORDS;      // enc + dec scalar groups
+constexpr int kWarpSmemBytes = TDES_TABLE_WORDS * 4;      // one table per warp (13 KB)
+static_assert(32 * TDES_SUBKEY_WORDS <= kWarpSmemBytes, "scalar groups must fit a warp slice");
+
+struct BatchMsg {
+    const uint8_t* in;
+    uint8_t* out;
+    uint64_t nblocks;
+    uint64_t iv;  // CBC: IV; CTR: first counter block
+    uint32_t key;
+    uint32_t mode;
+};
+
+struct BatchParams {
+    const BatchMsg* msgs;
+    const uint32_t* keytab;    // [key][dir][TDES_TABLE_WORDS]
+    const uint8_t* keychunks;  // [key][dir][TDES_SUBKEY_WORDS]
+    const uint32_t* c_list;    // CBC-enc message indices, longest first
+    uint32_t n_c, n_c_items;
+    const uint32_t* b_msg;     // large message index per B entry
+    const uint64_t* b_prefix;  // exclusive prefix of tiles, n_b + 1 entries
+    uint32_t n_b;
+    uint64_t n_b_tiles;
+    const uint32_t* s_list;    // small message indices
+    const uint2* s_items;      // (first, count) into s_list, whole messages, <= 32 blocks
+    uint32_t n_s_items;
+    uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
+    unsigned long long* counter;
+};
+
+__device__ const uint32_t kBatchSP[8][64] = TDES_SP_INIT;
+__device__ const uint64_t kBatchIPN[16][16] = TDES_IPN_INIT;
+__device__ const uint64_t kBatchFPN[16][16] = TDES_FPN_INIT;
+__device__ const uint8_t kBatchRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
+__device__ const uint8_t kBatchSubkeyBits[2][48][48] = TDES_SUBKEY_INIT;
+
+__device__ __forceinline__ uint32_t bswap32d(uint32_t x) { return __byte_perm(x, 0u, 0x0123); }
+
+// ---------------------------------------------------------------- key table
+// Thread per (key, word): bitsliced tables of both directions, then the
+// scalar groups of both directions.
+__global__ void tdes_keytable_kernel(const uint8_t* __restrict__ keys, uint32_t count,
+                                     uint32_t* __restrict__ tabs, uint8_t* __restrict__ chunks) {
+    const uint64_t per_key = (uint64_t)kPerKeyWords + kPerKeyChunks;
+    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= per_key * count) return;
+    const uint32_t key = (uint32_t)(e / per_key);
+    const uint32_t w = (uint32_t)(e % per_key);
+    const uint8_t* k = keys + 24ull * key;
+    if (w < kPerKeyWords) {
+        const int dir = w / TDES_TABLE_WORDS, i = w % TDES_TABLE_WORDS;
+        tabs[(uint64_t)key * kPerKeyWords + w] = tdes_table_word(k, kBatchRecipe[dir][i]);
+    } else {
+        const int f = w - kPerKeyWords;
+        const int dir = f / TDES_SUBKEY_WORDS, c = f % TDES_SUBKEY_WORDS;
+        chunks[(uint64_t)key * kPerKeyChunks + f] =
+            tdes_subkey_chunk(k, &kBatchSubkeyBits[dir][c / 8][6 * (c % 8)]);
+    }
+}
+
+// ------------------------------------------------------------ batch kernel
+
+struct SharedTables {
+    uint32_t sp[8 * 64];
+    uint64_t ipn[16 * 16];
+    uint64_t fpn[16 * 16];
+};
+
+__device__ __forceinline__ int dir_of(uint32_t mode) {
+    return (mode == TDES_MODE_ECB_DECRYPT || mode == TDES_MODE_CBC_DECRYPT) ? 1 : 0;
+}
+
+__device__ __forceinline__ uint64_t load_be(const uint8_t* p, uint64_t i) {
+    return bswap64(reinterpret_cast<const uint64_t*>(p)[i]);
+}
+__device__ __forceinline__ void store_be(uint8_t* p, uint64_t i, uint64_t v) {
+    reinterpret_cast<uint64_t*>(p)[i] = bswap64(v);
+}
+
+// One bitsliced tile: blocks [b0, b0 + 1024) of message m (ragged at the end).
+// The message record is read again after the rounds rather than kept in
+// registers across them (the 64 planes need the register file).
+__device__ __forceinline__ void batch_bs_tile(const BatchMsg* __restrict__ mp, uint64_t tile,
+                                              uint64_t gtile, const uint32_t* __restrict__ tab,
+                                              const uint64_t* __restrict__ halo, uint32_t lane) {
+    const uint64_t b0 = tile * kTileBlocks;
+    uint32_t A0[32], A1[32];
+    {
+    const BatchMsg m = *mp;
+    const uint64_t n = m.nblocks;
+    const bool full = b0 + kTileBlocks <= n;
+    const bool vec = full && (((reinterpret_cast<uintptr_t>(m.in) |
+                                reinterpret_cast<uintptr_t>(m.out)) & 15u) == 0);
+    if (m.mode == TDES_MODE_CTR) {
+        const uint32_t nw = bswap32d((uint32_t)(m.iv >> 32));
+        const uint32_t c0 = (uint32_t)m.iv;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                A0[2 * j + h] = nw;
+                A1[2 * j + h] = bswap32d(c0 + (uint32_t)(b0 + 2 * (32 * j + lane) + h));
+            }
+    } else if (vec) {
+        const uint4* p = reinterpret_cast<const uint4*>(m.in) + (b0 >> 1) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint4 v = __ldcs(p + 32 * j);
+            A0[2 * j] = v.x;
+            A1[2 * j] = v.y;
+            A0[2 * j + 1] = v.z;
+            A1[2 * j + 1] = v.w;
+        }
+    } else {
+        const uint2* p = reinterpret_cast<const uint2*>(m.in);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t b = b0 + 2 * (32 * j + lane) + h;
+                uint2 v = make_uint2(0u, 0u);
+                if (b < n) v = __ldcs(p + b);
+                A0[2 * j + h] = v.x;
+                A1[2 * j + h] = v.y;
+            }
+    }
+    }
+    tdes_process32(A0, A1, tab);
+    const BatchMsg m = *mp;
+    const uint64_t n = m.nblocks;
+    const bool full = b0 + kTileBlocks <= n;
+    const bool vec = full && (((reinterpret_cast<uintptr_t>(m.in) |
+                                reinterpret_cast<uintptr_t>(m.out)) & 15u) == 0);
+    const uint2* c = reinterpret_cast<const uint2*>(m.in);
+    if (m.mode == TDES_MODE_CTR) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t b = b0 + 2 * (32 * j + lane) + h;
+                if (b < n) {
+                    const uint2 v = __ldcs(c + b);
+                    A0[2 * j + h] ^= v.x;
+                    A1[2 * j + h] ^= v.y;
+                }
+            }
+        __syncwarp();  // in place: every lane has read its data before any lane writes
+    } else if (m.mode == TDES_MODE_CBC_DECRYPT) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint64_t b = b0 + 2 * (32 * j + lane);
+            uint2 prev0, prev1 = make_uint2(0u, 0u);
+            if (b == 0) {
+                prev0 = make_uint2(bswap32d((uint32_t)(m.iv >> 32)), bswap32d((uint32_t)m.iv));
+            } else if (j == 0 && lane == 0 && halo != nullptr && m.in == m.out) {
+                const uint64_t hv = halo[gtile];
+                prev0 = make_uint2((uint32_t)hv, (uint32_t)(hv >> 32));
+            } else {
+                prev0 = (b - 1 < n) ? c[b - 1] : make_uint2(0u, 0u);
+            }
+            if (b < n) prev1 = c[b];
+            A0[2 * j] ^= prev0.x;
+            A1[2 * j] ^= prev0.y;
+            A0[2 * j + 1] ^= prev1.x;
+            A1[2 * j + 1] ^= prev1.y;
+        }
+        __syncwarp();
+    }
+    if (vec) {
+        uint4* q = reinterpret_cast<uint4*>(m.out) + (b0 >> 1) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            __stcs(q + 32 * j, make_uint4(A0[2 * j], A1[2 * j], A0[2 * j + 1], A1[2 * j + 1]));
+    } else {
+        uint2* q = reinterpret_cast<uint2*>(m.out);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t b = b0 + 2 * (32 * j + lane) + h;
+                if (b < n) __stcs(q + b, make_uint2(A0[2 * j + h], A1[2 * j + h]));
+            }
+    }
+}
+
+__device__ __forceinline__ void stage_chunks(uint8_t* dst, const uint8_t* __restrict__ src) {
+    // 384 bytes = 24 x 16 bytes; src and dst are 16-byte aligned
+#pragma unroll 4
+    for (int i = 0; i < TDES_SUBKEY_WORDS / 16; ++i)
+        reinterpret_cast<uint4*>(dst)[i] = __ldg(reinterpret_cast<const uint4*>(src) + i);
+}
+
+// The scalar items are real calls (__noinline__): inlined, their register
+// needs would be allocated together with the bitsliced path's 64 planes and
+// force spills there; as calls they have their own allocation.
+
+// S item: whole small messages, one block per lane.
+__device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
+                                               uint8_t* warp_smem, const SharedTables& st,
+                                               uint32_t lane) {
+    // find this lane's (message, block): walk the item's messages in order
+    uint32_t msg = 0xFFFFFFFFu;
+    uint64_t blk = 0;
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < item.y; ++i) {
+        const uint32_t mi = p.s_list[item.x + i];
+        const uint32_t nb = (uint32_t)p.msgs[mi].nblocks;
+        if (lane >= acc && lane < acc + nb) {
+            msg = mi;
+            blk = lane - acc;
+        }
+        acc += nb;
+    }
+    uint64_t x = 0, prev = 0;
+    BatchMsg m;
+    if (msg != 0xFFFFFFFFu) {
+        m = p.msgs[msg];
+        stage_chunks(warp_smem + TDES_SUBKEY_WORDS * lane,
+                     p.keychunks + (uint64_t)m.key * kPerKeyChunks +
+                         TDES_SUBKEY_WORDS * dir_of(m.mode));
+        if (m.mode == TDES_MODE_CTR) {
+            x = (m.iv & 0xFFFFFFFF00000000ull) | (uint32_t)((uint32_t)m.iv + (uint32_t)blk);
+            prev = load_be(m.in, blk);  // the data to XOR
+        } else {
+            x = load_be(m.in, blk);
+            if (m.mode == TDES_MODE_CBC_DECRYPT) prev = blk ? load_be(m.in, blk - 1) : m.iv;
+        }
+    }
+    __syncwarp();  // every read of the item's messages precedes every write (in place)
+    if (msg != 0xFFFFFFFFu) {
+        uint64_t y = tdes_block_scalar_nib(x, st.sp, warp_smem + TDES_SUBKEY_WORDS * lane, st.ipn,
+                                           st.fpn);
+        if (m.mode == TDES_MODE_CTR || m.mode == TDES_MODE_CBC_DECRYPT) y ^= prev;
+        store_be(m.out, blk, y);
+    }
+    __syncwarp();
+}
+
+// C item: up to 32 CBC-encryption chains, one per lane.
+__device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t item,
+                                                uint8_t* warp_smem, const SharedTables& st,
+                                                uint32_t lane) {
+    const uint32_t idx = 32u * item + lane;
+    if (idx < p.n_c) {
+        const BatchMsg m = p.msgs[p.c_list[idx]];
+        uint8_t* ch = warp_smem + TDES_SUBKEY_WORDS * lane;
+        stage_chunks(ch, p.keychunks + (uint64_t)m.key * kPerKeyChunks);
+        uint64_t prev = m.iv;
+        for (uint64_t i = 0; i < m.nblocks; ++i) {
+            prev = tdes_block_scalar_nib(load_be(m.in, i) ^ prev, st.sp, ch, st.ipn, st.fpn);
+            store_be(m.out, i, prev);
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ __align__(16) SharedTables st;
+    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) st.sp[i] = (&kBatchSP[0][0])[i];
+    for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) {
+        st.ipn[i] = (&kBatchIPN[0][0])[i];
+        st.fpn[i] = (&kBatchFPN[0][0])[i];
+    }
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint8_t* wsm = dyn_smem + (size_t)warp * kWarpSmemBytes;
+    uint32_t* wtab = reinterpret_cast<uint32_t*>(wsm);
+    uint64_t staged = ~0ull;  // (key << 1 | dir) of the table in wtab
+    const uint64_t total = (uint64_t)p.n_c_items + p.n_b_tiles + p.n_s_items;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.counter, 1ull);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= total) break;
+        if (item < p.n_c_items) {
+            batch_cbc_enc_item(p, (uint32_t)item, wsm, st, lane);
+            staged = ~0ull;
+            continue;
+        }
+        item -= p.n_c_items;
+        if (item < p.n_b_tiles) {
+            // the large message holding global tile `item` (warp-uniform search)
+            uint32_t lo = 0, hi = p.n_b;  // b_prefix[lo] <= item < b_prefix[hi]
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (p.b_prefix[mid] <= item) lo = mid; else hi = mid;
+            }
+            const BatchMsg* mp = p.msgs + p.b_msg[lo];
+            const uint32_t key = mp->key, dir = (uint32_t)dir_of(mp->mode);
+            const uint64_t want = ((uint64_t)key << 1) | dir;
+            if (want != staged) {
+                __syncwarp();
+                const uint4* src = reinterpret_cast<const uint4*>(
+                    p.keytab + (uint64_t)key * kPerKeyWords + TDES_TABLE_WORDS * dir);
+                for (int i = lane; i < TDES_TABLE_WORDS / 4; i += 32)
+                    reinterpret_cast<uint4*>(wtab)[i] = __ldg(src + i);
+                __syncwarp();
+                staged = want;
+            }
+            batch_bs_tile(mp, item - p.b_prefix[lo], item, wtab, p.halo, lane);
+            continue;
+        }
+        item -= p.n_b_tiles;
+        batch_scalar_item(p, p.s_items[item], wsm, st, lane);
+        staged = ~0ull;
+    }
+}
+
+// In-place CBC decryption: save the ciphertext block before every B tile
+// (after the first of its message) before any tile is overwritten.
+__global__ void tdes_batch_halo_kernel(BatchParams p) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.n_b_tiles) return;
+    uint32_t lo = 0, hi = p.n_b;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (p.b_prefix[mid] <= t) lo = mid; else hi = mid;
+    }
+    const BatchMsg m = p.msgs[p.b_msg[lo]];
+    const uint64_t k = t - p.b_prefix[lo];
+    if (m.mode == TDES_MODE_CBC_DECRYPT && m.in == m.out && k >= 1)
+        p.halo[t] = reinterpret_cast<const uint64_t*>(m.in)[k * kTileBlocks - 1];
+}
+
+}  // namespace tdes
+
+// ===================================================================== host
+
+struct tdes_keytable {
+    int device;
+    uint32_t count;
+    void* mem;
+    uint32_t* tabs;
+    uint8_t* chunks;
+};
+
+struct tdes_batch {
+    int device;
+    const tdes_keytable* kt;
+    void* mem;
+    tdes::BatchParams params;
+    uint64_t total_items;
+    bool needs_halo;
+    int warps;         // warps per CTA
+    int ctas_per_sm;   // resident CTAs per SM used for the grid
+    int sms;
+    size_t dyn_smem;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaStream_t graph_stream;
+    uint64_t bytes[5];  // payload bytes per mode
+};
+
+namespace {
+
+int bfail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    tdes::set_last_error(buf);
+    return status;
+}
+
+int bcuda(cudaError_t e, const char* what) {
+    return bfail(e == cudaErrorMemoryAllocation ? TDES_ENOMEM : TDES_ECUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int max_ctas_per_sm(int warps, size_t dyn_smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes::tdes_batch_kernel, 32 * warps,
+                                                      dyn_smem) != cudaSuccess)
+        return 1;
+    return n < 1 ? 1 : n;
+}
+
+int set_launch_config(tdes_batch_t* b, int warps, int ctas_per_sm) {
+    const size_t dyn = (size_t)warps * tdes::kWarpSmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(tdes::tdes_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return bcuda(e, "cudaFuncSetAttribute(batch kernel smem)");
+    const int fit = max_ctas_per_sm(warps, dyn);
+    b->warps = warps;
+    b->dyn_smem = dyn;
+    b->ctas_per_sm = ctas_per_sm < 1 ? fit : std::min(ctas_per_sm, fit);
+    if (b->exec) {  // launch shape changed: recapture on next graph launch
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    return TDES_OK;
+}
+
+cudaError_t enqueue(tdes_batch_t* b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b->params.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (b->needs_halo && b->params.n_b_tiles) {
+        const unsigned grid = (unsigned)((b->params.n_b_tiles + 255) / 256);
+        tdes::tdes_batch_halo_kernel<<<grid, 256, 0, s>>>(b->params);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const uint64_t want_ctas = (b->total_items + b->warps - 1) / b->warps;
+    const uint64_t max_ctas = (uint64_t)b->sms * b->ctas_per_sm;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want_ctas, max_ctas));
+    tdes::tdes_batch_kernel<<<grid, 32 * b->warps, b->dyn_smem, s>>>(b->params);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** out) {
+    if (out == nullptr || (keys == nullptr && count > 0))
+        return bfail(TDES_EINVAL, "NULL argument to tdes_keytable_create");
+    *out = nullptr;
+    if (count == 0) return bfail(TDES_EINVAL, "empty key table");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
+    const size_t tab_bytes = (size_t)count * tdes::kPerKeyWords * 4;
+    const size_t chunk_bytes = align_up((size_t)count * tdes::kPerKeyChunks, 16);
+    const size_t key_bytes = align_up((size_t)count * 24, 16);
+    void* mem = nullptr;
+    e = cudaMalloc(&mem, tab_bytes + chunk_bytes + key_bytes);
+    if (e != cudaSuccess) return bcuda(e, "cudaMalloc(key table)");
+    tdes_keytable_t* kt = new (std::nothrow) tdes_keytable_t;
+    if (kt == nullptr) {
+        cudaFree(mem);
+        return bfail(TDES_ENOMEM, "host allocation failed");
+    }
+    kt->device = dev;
+    kt->count = count;
+    kt->mem = mem;
+    kt->tabs = static_cast<uint32_t*>(mem);
+    kt->chunks = static_cast<uint8_t*>(mem) + tab_bytes;
+    uint8_t* dkeys = kt->chunks + chunk_bytes;
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dkeys, keys, (size_t)count * 24, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const uint64_t n = (uint64_t)count * (tdes::kPerKeyWords + tdes::kPerKeyChunks);
+        tdes::tdes_keytable_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dkeys, count,
+                                                                              kt->tabs, kt->chunks);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(dkeys, 0, (size_t)count * 24, s);  // keys not kept
+    if (s) {
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(s);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        delete kt;
+        return bcuda(e, "key-table kernel");
+    }
+    *out = kt;
+    return TDES_OK;
+}
+
+void tdes_keytable_free(tdes_keytable_t* kt) {
+    if (kt == nullptr) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != kt->device) cudaSetDevice(kt->device);
+    cudaFree(kt->mem);
+    if (cur >= 0 && cur != kt->device) cudaSetDevice(cur);
+    delete kt;
+}
+
+int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_t count,
+                    int* per_desc_status, tdes_batch_t** out) {
+    if (out == nullptr || kt == nullptr || (descs == nullptr && count > 0))
+        return bfail(TDES_EINVAL, "NULL argument to tdes_batch_plan");
+    *out = nullptr;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
+    if (dev != kt->device) return bfail(TDES_EINVAL, "key table lives on another device");
+
+    std::vector<tdes::BatchMsg> msgs;
+    std::vector<uint32_t> c_list, b_msg, s_list;
+    std::vector<uint64_t> b_prefix(1, 0);
+    std::vector<uint2> s_items;
+    uint64_t bytes[5] = {0, 0, 0, 0, 0};
+    bool needs_halo = false;
+    int invalid = 0;
+    msgs.reserve(count);
+    for (uint32_t i = 0; i < count; ++i) {
+        const tdes_desc_t& d = descs[i];
+        const uintptr_t a = reinterpret_cast<uintptr_t>(d.in), o = reinterpret_cast<uintptr_t>(d.out);
+        int st = TDES_OK;
+        if (d.mode > TDES_MODE_CBC_ENCRYPT || d.key_index >= kt->count || d.nbytes % 8 != 0)
+            st = TDES_EINVAL;
+        else if (d.nbytes > 0 && (d.in == nullptr || d.out == nullptr || ((a | o) & 7u)))
+            st = TDES_EINVAL;
+        else if (a != o && a < o + d.nbytes && o < a + d.nbytes)
+            st = TDES_EINVAL;
+        else if (d.mode == TDES_MODE_CTR && (d.iv_or_ctr & 0xFFFFFFFFull) + d.nbytes / 8 > (1ull << 32))
+            st = TDES_EINVAL;
+        if (per_desc_status) per_desc_status[i] = st;
+        if (st != TDES_OK) {
+            ++invalid;
+            continue;
+        }
+        if (d.nbytes == 0) continue;
+        const uint32_t mi = (uint32_t)msgs.size();
+        msgs.push_back({static_cast<const uint8_t*>(d.in), static_cast<uint8_t*>(d.out),
+                        d.nbytes / 8, d.iv_or_ctr, d.key_index, d.mode});
+        bytes[d.mode] += d.nbytes;
+        const uint64_t nb = d.nbytes / 8;
+        if (d.mode == TDES_MODE_CBC_ENCRYPT) {
+            c_list.push_back(mi);
+        } else if (nb <= (uint64_t)tdes::kSmallBlocks) {
+            s_list.push_back(mi);
+        } else {
+            b_msg.push_back(mi);
+            b_prefix.push_back(b_prefix.back() + (nb + tdes::kTileBlocks - 1) / tdes::kTileBlocks);
+            if (d.mode == TDES_MODE_CBC_DECRYPT && d.in == d.out) needs_halo = true;
+        }
+    }
+    std::stable_sort(c_list.begin(), c_list.end(), [&](uint32_t x, uint32_t y) {
+        return msgs[x].nblocks > msgs[y].nblocks;
+    });
+    // pack small messages whole into items of at most 32 blocks
+    for (uint32_t i = 0; i < s_list.size();) {
+        uint32_t first = i, blocks = 0;
+        while (i < s_list.size() && blocks + msgs[s_list[i]].nblocks <= (uint64_t)tdes::kSmallBlocks)
+            blocks += (uint32_t)msgs[s_list[i++]].nblocks;
+        s_items.push_back(make_uint2(first, i - first));
+    }
+    const uint64_t n_b_tiles = b_prefix.back();
+
+    // one device allocation for everything the kernel reads
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t o2 = align_up(off, 16); off = o2 + n; return o2; };
+    const size_t o_msgs = take(msgs.size() * sizeof(tdes::BatchMsg));
+    const size_t o_c = take(c_list.size() * 4);
+    const size_t o_bm = take(b_msg.size() * 4);
+    const size_t o_bp = take(b_prefix.size() * 8);
+    const size_t o_sl = take(s_list.size() * 4);
+    const size_t o_si = take(s_items.size() * sizeof(uint2));
+    const size_t o_halo = take(needs_halo ? n_b_tiles * 8 : 0);
+    const size_t o_ctr = take(8);
+    std::vector<uint8_t> host(off, 0);
+    auto put = [&](size_t o, const void* src, size_t n) { if (n) memcpy(host.data() + o, src, n); };
+    put(o_msgs, msgs.data(), msgs.size() * sizeof(tdes::BatchMsg));
+    put(o_c, c_list.data(), c_list.size() * 4);
+    put(o_bm, b_msg.data(), b_msg.size() * 4);
+    put(o_bp, b_prefix.data(), b_prefix.size() * 8);
+    put(o_sl, s_list.data(), s_list.size() * 4);
+    put(o_si, s_items.data(), s_items.size() * sizeof(uint2));
+    void* mem = nullptr;
+    e = cudaMalloc(&mem, off);
+    if (e != cudaSuccess) return bcuda(e, "cudaMalloc(batch plan)");
+    e = cudaMemcpy(mem, host.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return bcuda(e, "cudaMemcpy(batch plan)");
+    }
+    tdes_batch_t* b = new (std::nothrow) tdes_batch_t();
+    if (b == nullptr) {
+        cudaFree(mem);
+        return bfail(TDES_ENOMEM, "host allocation failed");
+    }
+    uint8_t* base = static_cast<uint8_t*>(mem);
+    b->device = dev;
+    b->kt = kt;
+    b->mem = mem;
+    tdes::BatchParams& p = b->params;
+    p.msgs = reinterpret_cast<const tdes::BatchMsg*>(base + o_msgs);
+    p.keytab = kt->tabs;
+    p.keychunks = kt->chunks;
+    p.c_list = reinterpret_cast<const uint32_t*>(base + o_c);
+    p.n_c = (uint32_t)c_list.size();
+    p.n_c_items = (p.n_c + 31) / 32;
+    p.b_msg = reinterpret_cast<const uint32_t*>(base + o_bm);
+    p.b_prefix = reinterpret_cast<const uint64_t*>(base + o_bp);
+    p.n_b = (uint32_t)b_msg.size();
+    p.n_b_tiles = n_b_tiles;
+    p.s_list = reinterpret_cast<const uint32_t*>(base + o_sl);
+    p.s_items = reinterpret_cast<const uint2*>(base + o_si);
+    p.n_s_items = (uint32_t)s_items.size();
+    p.halo = needs_halo ? reinterpret_cast<uint64_t*>(base + o_halo) : nullptr;
+    p.counter = reinterpret_cast<unsigned long long*>(base + o_ctr);
+    b->total_items = (uint64_t)p.n_c_items + p.n_b_tiles + p.n_s_items;
+    b->needs_halo = needs_halo;
+    memcpy(b->bytes, bytes, sizeof bytes);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    int rc = set_launch_config(b, tdes::kWideWarps, 0);
+    if (rc != TDES_OK) {
+        cudaFree(mem);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    if (invalid) bfail(TDES_EINVAL, "%d descriptor(s) rejected; see per_desc_status", invalid);
+    return TDES_OK;
+}
+
+int tdes_batch_configure(tdes_batch_t* b, int warps_per_cta, int ctas_per_sm) {
+    if (b == nullptr || warps_per_cta < 1 || warps_per_cta > 8)
+        return bfail(TDES_EINVAL, "tdes_batch_configure: 1..8 warps per CTA");
+    return set_launch_config(b, warps_per_cta, ctas_per_sm);
+}
+
+int tdes_batch_launch(tdes_batch_t* b, tdes_stream_t stream) {
+    if (b == nullptr) return bfail(TDES_EINVAL, "batch is NULL");
+    if (b->total_items == 0) return TDES_OK;
+    cudaError_t e = enqueue(b, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? TDES_OK : bcuda(e, "batch launch");
+}
+
+int tdes_batch_launch_graph(tdes_batch_t* b, tdes_stream_t stream) {
+    if (b == nullptr) return bfail(TDES_EINVAL, "batch is NULL");
+    if (b->total_items == 0) return TDES_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (b->exec == nullptr) {
+        // capture on a private stream so that the caller's stream need not be capturable
+        cudaStream_t cap = nullptr;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bcuda(e, "cudaStreamCreate");
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = enqueue(b, cap);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(cap, &g);
+            if (e == cudaSuccess) e = e1;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+            if (e == cudaSuccess) b->graph = g;
+            else if (g) cudaGraphDestroy(g);
+        }
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return bcuda(e, "batch graph capture");
+        }
+    }
+    e = cudaGraphLaunch(b->exec, s);
+    return e == cudaSuccess ? TDES_OK : bcuda(e, "cudaGraphLaunch");
+}
+
+int tdes_batch_info(const tdes_batch_t* b, tdes_batch_info_t* info) {
+    if (b == nullptr || info == nullptr) return bfail(TDES_EINVAL, "NULL argument");
+    info->n_cbc_enc_messages = b->params.n_c;
+    info->n_tiles = b->params.n_b_tiles;
+    info->n_small_items = b->params.n_s_items;
+    info->warps_per_cta = b->warps;
+    info->ctas_per_sm = b->ctas_per_sm;
+    for (int i = 0; i < 5; ++i) info->bytes_per_mode[i] = b->bytes[i];
+    return TDES_OK;
+}
+
+void tdes_batch_free(tdes_batch_t* b) {
+    if (b == nullptr) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->mem);
+    delete b;
+}
+
+}  // extern "C"

@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "tdes_bitslice.cuh"
+#include "generated/tdes_generated_scalar.cuh"
 
 #define TDES_SUBKEY_WORDS (48 * 8)  // 48 rounds x 8 six-bit groups (bytes)
 

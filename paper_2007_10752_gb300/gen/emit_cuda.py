@@ -1,7 +1,8 @@
 """Emit the generated CUDA headers of the bitsliced 3DES kernels.
 
-Writes ``paper_2007_10752_gb300/csrc/generated/tdes_generated.cuh`` from
-``des_tables.py`` and ``sbox_lop3.json``:
+Writes ``paper_2007_10752_gb300/csrc/generated/tdes_generated.cuh`` (the
+bitsliced path) and ``tdes_generated_scalar.cuh`` (tables of the scalar
+one-block-per-thread path) from ``des_tables.py`` and ``sbox_lop3.json``:
 
 * ``tdes_round``: one Feistel round over 32 blocks held as bit-planes
   (Sec. III-B: expansion, round-key XOR, the eight S-boxes, the
@@ -265,6 +266,13 @@ def emit(path: str = OUT) -> str:
             L.append(f"    {chunk}, \\")
         L.append("  }, \\")
     L.append("}")
+    text = "\n".join(L) + "\n"
+    _write(path, text)
+    L = []
+    L.append("// GENERATED by paper_2007_10752_gb300/gen/emit_cuda.py -- do not edit.")
+    L.append("// Tables of the scalar (one block per thread) 3DES path, from Appendix A.")
+    L.append("#pragma once")
+    L.append("#include <cstdint>")
     L.append("")
     L.append("// Scalar path (serial CBC encryption).  Round-key bit j of EDE3 round r:")
     L.append("// 64*key + (key bit - 1), [0] encrypt, [1] decrypt.")
@@ -295,16 +303,36 @@ def emit(path: str = OUT) -> str:
         L.append("  {" + ",".join(vals) + "}, \\")
     L.append("}")
     L.append("")
+    L.append("// Initial / final permutation by nibbles: entry [n][v] is the output word")
+    L.append("// contribution of value v in input nibble n (input bits 4n+1..4n+4).")
+    for name, perm in (("IPN", T.IP), ("FPN", T.FP)):
+        dest = {src: j for j, src in enumerate(perm, start=1)}  # input bit -> output bit
+        L.append(f"#define TDES_{name}_INIT {{ \\")
+        for n in range(16):
+            vals = []
+            for v in range(16):
+                w = 0
+                for t in range(4):
+                    if (v >> (3 - t)) & 1:
+                        w |= 1 << (64 - dest[4 * n + t + 1])
+                vals.append(f"0x{w:016x}ull")
+            L.append("  {" + ",".join(vals) + "}, \\")
+        L.append("}")
+    L.append("")
     L.append("// Initial and final permutation as 0-based source bit (bit 1 = index 0).")
     L.append("#define TDES_IP_INIT {" + ",".join(str(x - 1) for x in T.IP) + "}")
     L.append("#define TDES_FP_INIT {" + ",".join(str(x - 1) for x in T.FP) + "}")
     text = "\n".join(L) + "\n"
+    _write(os.path.join(os.path.dirname(path), "tdes_generated_scalar.cuh"), text)
+    return path
+
+
+def _write(path, text):
     os.makedirs(os.path.dirname(path), exist_ok=True)
     old = open(path).read() if os.path.exists(path) else None
     if old != text:
         with open(path, "w") as f:
             f.write(text)
-    return path
 
 
 if __name__ == "__main__":

@@ -1,0 +1,52 @@
+"""A small, self-contained launch sequence for profiler captures.
+
+Runs `--launches` back-to-back launches of one kernel of the library on a
+seeded buffer of `--mib` MiB (default 256 MiB: larger than the 129 MB L2, a
+few hundred MB on the device) and exits.  Used as the target of ncu
+captures, whose commands are recorded beside their summaries in profiles/.
+
+  python -m paper_2007_10752_gb300.profile_case --kernel ecb --mib 256 --launches 3
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec"], default="ecb")
+    ap.add_argument("--mib", type=int, default=256)
+    ap.add_argument("--launches", type=int, default=3)
+    args = ap.parse_args()
+
+    import torch
+
+    from paper_2007_10752_gb300 import build, synth, tdes
+    build.build()
+    torch.cuda.set_device(0)
+    n = args.mib << 20
+    keys = synth.key_triple(2)
+    x = torch.from_numpy(synth.random_bytes(2, n)).cuda()
+    y = torch.empty_like(x)
+    ks = tdes.KeySchedule.from_triple(keys)
+    for _ in range(args.launches):
+        if args.kernel == "ecb":
+            tdes.tdes_ecb_encrypt(ks, x, y)
+        elif args.kernel == "ecb_dec":
+            tdes.tdes_ecb_decrypt(ks, x, y)
+        elif args.kernel == "ctr":
+            tdes.tdes_ctr_crypt(ks, 1, 0, x, y)
+        else:
+            tdes.tdes_cbc_decrypt(ks, 1, x, y)
+    torch.cuda.synchronize()
+    print(f"{args.kernel}: {args.launches} launches on {args.mib} MiB done")
+
+
+if __name__ == "__main__":
+    main()

@@ -27,9 +27,31 @@ TDES_ECUDA = -5
 EXPORTED = (
     "tdes_key_schedule", "tdes_key_free", "tdes_ecb_encrypt", "tdes_ecb_decrypt",
     "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_cbc_decrypt_noalloc",
-    "tdes_ecb_crypt_host",
+    "tdes_ecb_crypt_host", "tdes_keytable_create", "tdes_keytable_free", "tdes_batch_plan",
+    "tdes_batch_configure", "tdes_batch_launch", "tdes_batch_launch_graph", "tdes_batch_info",
+    "tdes_batch_free",
     "tdes_sbox_gate_count", "tdes_strerror", "tdes_last_error",
 )
+
+MODE_ECB_ENCRYPT = 0
+MODE_ECB_DECRYPT = 1
+MODE_CTR = 2
+MODE_CBC_DECRYPT = 3
+MODE_CBC_ENCRYPT = 4
+
+
+class Desc(ctypes.Structure):
+    """tdes_desc_t"""
+    _fields_ = [("mode", ctypes.c_uint32), ("key_index", ctypes.c_uint32),
+                ("iv_or_ctr", ctypes.c_uint64), ("in_ptr", ctypes.c_void_p),
+                ("out_ptr", ctypes.c_void_p), ("nbytes", ctypes.c_uint64)]
+
+
+class BatchInfo(ctypes.Structure):
+    """tdes_batch_info_t"""
+    _fields_ = [("n_cbc_enc_messages", ctypes.c_uint32), ("n_tiles", ctypes.c_uint64),
+                ("n_small_items", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("bytes_per_mode", ctypes.c_uint64 * 5)]
 
 _lib = None
 
@@ -60,6 +82,16 @@ def load(path: str = LIB_PATH):
     lib.tdes_cbc_encrypt.argtypes = [vp, u64, vp, vp, sz, vp]
     lib.tdes_cbc_decrypt_noalloc.argtypes = [vp, u64, vp, vp, sz, vp]
     lib.tdes_ecb_crypt_host.argtypes = [vp, ctypes.c_int, vp, vp, sz, vp, sz]
+    lib.tdes_keytable_create.argtypes = [vp, u32, ctypes.POINTER(vp)]
+    lib.tdes_keytable_free.argtypes = [vp]
+    lib.tdes_keytable_free.restype = None
+    lib.tdes_batch_plan.argtypes = [vp, vp, u32, vp, ctypes.POINTER(vp)]
+    lib.tdes_batch_configure.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.tdes_batch_launch.argtypes = [vp, vp]
+    lib.tdes_batch_launch_graph.argtypes = [vp, vp]
+    lib.tdes_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    lib.tdes_batch_free.argtypes = [vp]
+    lib.tdes_batch_free.restype = None
     lib.tdes_sbox_gate_count.argtypes = []
     lib.tdes_strerror.argtypes = [ctypes.c_int]
     lib.tdes_strerror.restype = ctypes.c_char_p
@@ -204,6 +236,79 @@ def tdes_ecb_crypt_host(ks: KeySchedule, decrypt: bool, host_in, host_out, dev_b
     _check(load().tdes_ecb_crypt_host(ks.handle, int(bool(decrypt)), _ptr(host_in),
                                       _ptr(host_out), n, _ptr(dev_buf), _nbytes(dev_buf)))
     return host_out
+
+
+class KeyTable:
+    """Owns a tdes_keytable_t: device-resident schedules of many key triples."""
+
+    def __init__(self, keys):
+        k = np.ascontiguousarray(np.asarray(keys, dtype=np.uint8).reshape(-1, 24))
+        h = ctypes.c_void_p()
+        _check(load().tdes_keytable_create(k.ctypes.data, k.shape[0], ctypes.byref(h)))
+        self.handle = h.value
+        self.count = k.shape[0]
+
+    def free(self):
+        if self.handle:
+            load().tdes_keytable_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_descs(entries):
+    """entries: iterable of (mode, key_index, iv_or_ctr, in_ptr, out_ptr, nbytes)."""
+    entries = list(entries)
+    arr = (Desc * max(1, len(entries)))()
+    for i, (mode, key, iv, ip, op, n) in enumerate(entries):
+        arr[i] = Desc(mode, key, iv & (2**64 - 1), _ptr(ip), _ptr(op), n)
+    return arr, len(entries)
+
+
+class Batch:
+    """Owns a tdes_batch_t planned from descriptors (see include/tdes.h)."""
+
+    def __init__(self, kt: KeyTable, entries):
+        descs, n = make_descs(entries)
+        self._descs = descs
+        self.status = np.zeros(max(1, n), dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(load().tdes_batch_plan(kt.handle, ctypes.addressof(descs), n,
+                                      self.status.ctypes.data, ctypes.byref(h)))
+        self.status = self.status[:n]
+        self.handle = h.value
+        self.kt = kt
+
+    def configure(self, warps_per_cta: int, ctas_per_sm: int = 0):
+        _check(load().tdes_batch_configure(self.handle, warps_per_cta, ctas_per_sm))
+
+    def launch(self, stream=None):
+        _check(load().tdes_batch_launch(self.handle, _stream(stream)))
+
+    def launch_graph(self, stream=None):
+        _check(load().tdes_batch_launch_graph(self.handle, _stream(stream)))
+
+    def info(self) -> dict:
+        bi = BatchInfo()
+        _check(load().tdes_batch_info(self.handle, ctypes.byref(bi)))
+        return {"n_cbc_enc_messages": bi.n_cbc_enc_messages, "n_tiles": bi.n_tiles,
+                "n_small_items": bi.n_small_items, "warps_per_cta": bi.warps_per_cta,
+                "ctas_per_sm": bi.ctas_per_sm, "bytes_per_mode": list(bi.bytes_per_mode)}
+
+    def free(self):
+        if self.handle:
+            load().tdes_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def tdes_sbox_gate_count() -> int:

@@ -4,7 +4,7 @@
 // key-table recipes and plane renames can be checked against the CPU oracle
 // without a GPU.
 //
-// Usage: tdes_host_check <bs_enc|bs_dec|sc_enc|sc_dec> <48 hex digits K1||K2||K3>
+// Usage: tdes_host_check <bs_enc|bs_dec|sc_enc|sc_dec|sn_enc|sn_dec> <48 hex K1||K2||K3>
 //   reads whole 8-byte blocks on stdin, writes the results on stdout.
 #include <cstdio>
 #include <cstdlib>
@@ -18,6 +18,8 @@ static const uint8_t kSub[2][48][48] = TDES_SUBKEY_INIT;
 static const uint32_t kSP[8][64] = TDES_SP_INIT;
 static const uint8_t kIP[64] = TDES_IP_INIT;
 static const uint8_t kFP[64] = TDES_FP_INIT;
+static const uint64_t kIPN[16][16] = TDES_IPN_INIT;
+static const uint64_t kFPN[16][16] = TDES_FPN_INIT;
 
 int main(int argc, char** argv) {
     if (argc != 3 || strlen(argv[2]) != 48) return 2;
@@ -61,7 +63,10 @@ int main(int argc, char** argv) {
             uint64_t v;
             memcpy(&v, &data[8 * i], 8);
             v = bswap64(v);
-            v = tdes_block_scalar(v, &kSP[0][0], chunks, kIP, kFP);
+            if (argv[1][1] == 'n')
+                v = tdes_block_scalar_nib(v, &kSP[0][0], chunks, &kIPN[0][0], &kFPN[0][0]);
+            else
+                v = tdes_block_scalar(v, &kSP[0][0], chunks, kIP, kFP);
             v = bswap64(v);
             memcpy(&out[8 * i], &v, 8);
         }

@@ -39,11 +39,11 @@ def test_sbox_circuits_match_oracle_exhaustively():
                 assert (v >> x) & 1 == want, (g, t, x)
 
 
-def test_generated_header_is_current(tmp_path):
-    fresh = emit_cuda.emit(str(tmp_path / "gen.cuh"))
-    committed = os.path.join(ROOT, "paper_2007_10752_gb300", "csrc", "generated",
-                             "tdes_generated.cuh")
-    assert open(fresh).read() == open(committed).read()
+def test_generated_headers_are_current(tmp_path):
+    emit_cuda.emit(str(tmp_path / "tdes_generated.cuh"))
+    gen_dir = os.path.join(ROOT, "paper_2007_10752_gb300", "csrc", "generated")
+    for name in ("tdes_generated.cuh", "tdes_generated_scalar.cuh"):
+        assert open(tmp_path / name).read() == open(os.path.join(gen_dir, name)).read(), name
 
 
 def test_round_schedule_and_recipe_shape():
@@ -89,7 +89,7 @@ KEYSETS = [
 
 
 @pytest.mark.parametrize("name,mk", KEYSETS, ids=[k[0] for k in KEYSETS])
-@pytest.mark.parametrize("mode", ["bs_enc", "bs_dec", "sc_enc", "sc_dec"])
+@pytest.mark.parametrize("mode", ["bs_enc", "bs_dec", "sc_enc", "sc_dec", "sn_enc", "sn_dec"])
 def test_generated_code_matches_oracle(host_check, name, mk, mode):
     keys = mk()
     data = synth.random_bytes(len(name) * 31 + 5, 8 * 75)  # 2 full groups of 32 + a ragged one

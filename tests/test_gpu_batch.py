@@ -1,0 +1,230 @@
+"""Batches through the C ABI: every message of a mixed batch (own key triple,
+own mode, uneven length, some in place, some only 8-byte aligned) equals the
+CPU oracle on that message alone, bit for bit, and equals the same message
+run alone on the GPU (alone vs in the mix); graph replay and every launch
+shape give identical bytes; invalid descriptors are rejected and skipped."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_10752_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NCPU = max(1, min(16, os.cpu_count() or 1))
+MODES = ["ecb_enc", "ecb_dec", "ctr", "cbc_dec", "cbc_enc"]
+
+
+def oracle_msg(mode, keys, iv, data):
+    if mode == 0:
+        return oracle.tdes_ecb(keys, data)
+    if mode == 1:
+        return oracle.tdes_ecb(keys, data, decrypt=True)
+    if mode == 2:
+        return oracle.tdes_ctr(keys, iv >> 32, iv & 0xFFFFFFFF, data)
+    if mode == 3:
+        return oracle.tdes_cbc_decrypt(keys, iv, data)
+    return oracle.tdes_cbc_encrypt(keys, iv, data)
+
+
+def build_mix(seed, n_msgs, n_keys, max_blocks, in_place_frac=0.3):
+    """Messages laid out in one device arena; returns (arena, msgs, keys)."""
+    rng = np.random.default_rng(seed)
+    keys = synth.key_triples(seed, n_keys)
+    sizes = []
+    for i in range(n_msgs):
+        r = rng.random()
+        if r < 0.35:
+            nb = int(rng.integers(0, 33))          # small: scalar path (0 = empty)
+        elif r < 0.8:
+            nb = int(rng.integers(33, 3000))       # one to three tiles, ragged
+        else:
+            nb = int(rng.integers(3000, max_blocks))
+        sizes.append(nb)
+    msgs, off = [], 0
+    for i, nb in enumerate(sizes):
+        mode = int(rng.integers(0, 5))
+        key = int(rng.integers(0, n_keys))
+        iv = int(synth.words(seed, i, 1, synth.STREAM_IV)[0])
+        if mode == 2:
+            iv = (iv & 0xFFFFFFFF00000000) | int(rng.integers(0, 1 << 20))
+        in_place = rng.random() < in_place_frac
+        align = 8 if rng.random() < 0.3 else 16
+        off = (off + 15) // 16 * 16 + (8 if align == 8 else 0)
+        in_off = off
+        off += 8 * nb + 16
+        out_off = in_off if in_place else (off + 15) // 16 * 16 + (8 if align == 8 else 0)
+        if not in_place:
+            off = out_off + 8 * nb + 16
+        data = synth.random_bytes(seed * 1000 + i, 8 * nb)
+        msgs.append(dict(mode=mode, key=key, iv=iv, nb=nb, in_off=in_off, out_off=out_off,
+                         data=data))
+    arena = torch.zeros(off + 64, dtype=torch.uint8, device="cuda")
+    for m in msgs:
+        if m["nb"]:
+            arena[m["in_off"]:m["in_off"] + 8 * m["nb"]].copy_(torch.from_numpy(m["data"]))
+    return arena, msgs, keys
+
+
+def entries_for(arena, msgs):
+    base = arena.data_ptr()
+    return [(m["mode"], m["key"], m["iv"], base + m["in_off"], base + m["out_off"], 8 * m["nb"])
+            for m in msgs]
+
+
+def outputs(arena, msgs):
+    torch.cuda.synchronize()
+    h = arena.cpu().numpy()
+    return [h[m["out_off"]:m["out_off"] + 8 * m["nb"]] for m in msgs]
+
+
+def restage(arena, msgs):
+    for m in msgs:
+        if m["nb"]:
+            arena[m["in_off"]:m["in_off"] + 8 * m["nb"]].copy_(torch.from_numpy(m["data"]))
+
+
+@pytest.fixture(scope="module")
+def mix(cuda_lib):
+    arena, msgs, keys = build_mix(11, 180, 23, 20000)
+    kt = cuda_lib.KeyTable(keys)
+    want = [oracle_msg(m["mode"], keys[m["key"]].tobytes(), m["iv"], m["data"]) for m in msgs]
+    return cuda_lib, arena, msgs, keys, kt, want
+
+
+def test_mixed_batch_matches_oracle(mix):
+    T, arena, msgs, keys, kt, want = mix
+    b = T.Batch(kt, entries_for(arena, msgs))
+    assert (b.status == 0).all()
+    info = b.info()
+    assert info["n_cbc_enc_messages"] > 0 and info["n_tiles"] > 0 and info["n_small_items"] > 0
+    b.launch()
+    for i, (got, w) in enumerate(zip(outputs(arena, msgs), want)):
+        m = msgs[i]
+        assert (got == w).all(), f"message {i}: mode {m['mode']} {m['nb']} blocks"
+
+
+def test_graph_and_launch_shapes_identical(mix):
+    T, arena, msgs, keys, kt, want = mix
+    b = T.Batch(kt, entries_for(arena, msgs))
+    for shape in [(8, 0), (4, 1), (8, 1), (2, 0)]:
+        restage(arena, msgs)
+        b.configure(*shape)
+        b.launch_graph()
+        for i, (got, w) in enumerate(zip(outputs(arena, msgs), want)):
+            assert (got == w).all(), f"shape {shape}, message {i}"
+    # a second replay of the same graph on restaged inputs gives the same bytes
+    restage(arena, msgs)
+    b.launch_graph()
+    for got, w in zip(outputs(arena, msgs), want):
+        assert (got == w).all()
+
+
+def test_alone_equals_in_the_mix(mix):
+    T, arena, msgs, keys, kt, want = mix
+    restage(arena, msgs)
+    T.Batch(kt, entries_for(arena, msgs)).launch()
+    mixed = [o.copy() for o in outputs(arena, msgs)]
+    base = arena.data_ptr()
+    for i in range(0, len(msgs), 7):
+        m = msgs[i]
+        restage(arena, [m])
+        T.Batch(kt, [(m["mode"], m["key"], m["iv"], base + m["in_off"], base + m["out_off"],
+                      8 * m["nb"])]).launch()
+        alone = outputs(arena, [m])[0]
+        assert (alone == mixed[i]).all(), f"message {i} differs alone vs in the mix"
+        # and equals the single-message entry points
+        if m["nb"] and m["mode"] in (0, 1, 2, 3):
+            ks = T.KeySchedule.from_triple(keys[m["key"]].tobytes())
+            x = torch.from_numpy(m["data"]).cuda()
+            if m["mode"] == 0:
+                y = T.tdes_ecb_encrypt(ks, x)
+            elif m["mode"] == 1:
+                y = T.tdes_ecb_decrypt(ks, x)
+            elif m["mode"] == 2:
+                y = T.tdes_ctr_crypt(ks, m["iv"] >> 32, m["iv"] & 0xFFFFFFFF, x)
+            else:
+                y = T.tdes_cbc_decrypt(ks, m["iv"], x)
+            torch.cuda.synchronize()
+            assert (y.cpu().numpy() == alone).all()
+
+
+def test_invalid_descriptors_are_skipped(cuda_lib):
+    T = cuda_lib
+    keys = synth.key_triples(5, 3)
+    kt = T.KeyTable(keys)
+    buf = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    data = synth.random_bytes(5, 4096)
+    buf[:4096].copy_(torch.from_numpy(data))
+    base = buf.data_ptr()
+    entries = [
+        (0, 0, 0, base, base + 8192, 4096),          # valid
+        (7, 0, 0, base, base + 16384, 4096),         # bad mode
+        (0, 3, 0, base, base + 16384, 4096),         # bad key index
+        (0, 0, 0, base, base + 16384, 4095),         # not whole blocks
+        (0, 0, 0, base + 4, base + 16384, 4096),     # 4-byte aligned
+        (0, 0, 0, base, base + 8, 4096),             # partial overlap
+        (2, 0, 0xFFFFFFF0, base, base + 16384, 4096),  # CTR counter would wrap
+        (1, 1, 0, base, base + 24576, 0),            # empty: fine, nothing done
+    ]
+    b = T.Batch(kt, entries)
+    assert list(b.status) == [0, -1, -1, -1, -1, -1, -1, 0]
+    b.launch()
+    torch.cuda.synchronize()
+    got = buf[8192:8192 + 4096].cpu().numpy()
+    assert (got == oracle.tdes_ecb(keys[0].tobytes(), data)).all()
+    assert (buf[16384:16384 + 4096] == 0).all()
+
+
+def test_config3_shape_sampled(cuda_lib):
+    """4096 messages, log-uniform 64 B .. 4 MiB, modes 40/30/20/10, own keys:
+    sampled windows of every message against the oracle."""
+    T = cuda_lib
+    seed = 3
+    n = 4096
+    lens = synth.log_uniform_lengths(seed, n, 64, 4 << 20)
+    modes = np.array([0, 2, 3, 4])[synth.categorical(seed, n, [0.4, 0.3, 0.2, 0.1],
+                                                     synth.STREAM_MODE)]
+    keys = synth.key_triples(seed, n)
+    ivs = synth.u64s(seed, n, synth.STREAM_IV)
+    total = int(lens.sum())
+    offs = np.concatenate([[0], np.cumsum((lens + 15) // 16 * 16)])[:-1]
+    src = torch.from_numpy(synth.random_bytes(seed, (total + 15) // 16 * 16 + 16 * n)).cuda()
+    dst = torch.zeros_like(src)
+    kt = T.KeyTable(keys)
+    ents = []
+    for i in range(n):
+        iv = int(ivs[i])
+        if modes[i] == 2:
+            iv &= 0xFFFFFFFF00000000
+        ents.append((int(modes[i]), i, iv, src.data_ptr() + int(offs[i]),
+                     dst.data_ptr() + int(offs[i]), int(lens[i])))
+    b = T.Batch(kt, ents)
+    assert (b.status == 0).all()
+    b.launch()
+    torch.cuda.synchronize()
+    hs, hd = src.cpu().numpy(), dst.cpu().numpy()
+    rng = np.random.default_rng(seed)
+    for i in range(n):
+        mode, _, iv, _, _, nb = ents[i]
+        o = int(offs[i])
+        nblk = nb // 8
+        k = keys[i].tobytes()
+        w = min(nblk, 64)
+        for s in sorted({0, nblk - w, int(rng.integers(0, nblk - w + 1))}):
+            x = hs[o + 8 * s:o + 8 * (s + w)]
+            y = hd[o + 8 * s:o + 8 * (s + w)]
+            if mode == 0:
+                ref = oracle.tdes_ecb(k, x)
+            elif mode == 2:
+                ref = oracle.tdes_ctr(k, iv >> 32, (iv & 0xFFFFFFFF) + s, x)
+            elif mode == 3:
+                prev = iv if s == 0 else int.from_bytes(hs[o + 8 * s - 8:o + 8 * s].tobytes(), "big")
+                ref = oracle.tdes_cbc_decrypt(k, prev, x)
+            else:  # the chain recurrence, from the GPU's own previous ciphertext
+                prev = iv if s == 0 else int.from_bytes(hd[o + 8 * s - 8:o + 8 * s].tobytes(), "big")
+                ref = oracle.tdes_cbc_encrypt(k, prev, x)
+            assert (y == ref).all(), f"message {i} mode {mode} window {s}"
