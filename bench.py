@@ -161,7 +161,7 @@ def kernel_source_hash() -> str:
 
 def profiled_traffic():
     """DRAM bytes per ECB launch from the committed ncu summary, if it is for this kernel."""
-    path = os.path.join(ROOT, "profiles", "tdes_ecb_kernel_1gib.md")
+    path = os.path.join(ROOT, "profiles", "tdes_ecb_kernel_256mib.md")
     try:
         text = open(path).read()
     except OSError:

@@ -33,6 +33,7 @@
 namespace tdes {
 
 constexpr int kSmallBlocks = 32;                          // S messages: nblocks <= this
+constexpr uint64_t kSoloChainBlocks = 512;                // longer CBC-enc chains: one per warp
 constexpr int kPerKeyWords = 2 * TDES_TABLE_WORDS;        // enc + dec bitsliced tables
 constexpr int kPerKeyChunks = 2 * TDES_SUBKEY_WORDS;      // enc + dec scalar groups
 constexpr int kWarpSmemBytes = TDES_TABLE_WORDS * 4;      // one table per warp (13 KB)
@@ -53,6 +54,7 @@ struct BatchParams {
     const uint8_t* keychunks;  // [key][dir][TDES_SUBKEY_WORDS]
     const uint32_t* c_list;    // CBC-enc message indices, longest first
     uint32_t n_c, n_c_items;
+    uint32_t n_c_solo;         // the first n_c_solo chains run one per warp
     const uint32_t* b_msg;     // large message index per B entry
     const uint64_t* b_prefix;  // exclusive prefix of tiles, n_b + 1 entries
     uint32_t n_b;
@@ -264,26 +266,36 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
     }
     __syncwarp();  // every read of the item's messages precedes every write (in place)
     if (msg != 0xFFFFFFFFu) {
-        uint64_t y = tdes_block_scalar_nib(x, st.sp, warp_smem + TDES_SUBKEY_WORDS * lane, st.ipn,
-                                           st.fpn);
+        uint64_t y = tdes_block_scalar_nib(
+            x, st.sp, reinterpret_cast<const uint32_t*>(warp_smem + TDES_SUBKEY_WORDS * lane),
+            st.ipn, st.fpn);
         if (m.mode == TDES_MODE_CTR || m.mode == TDES_MODE_CBC_DECRYPT) y ^= prev;
         store_be(m.out, blk, y);
     }
     __syncwarp();
 }
 
-// C item: up to 32 CBC-encryption chains, one per lane.
+// C item: CBC-encryption chains, one per lane.  The first n_c_solo items
+// (the longest chains) hold one chain each; the rest hold up to 32.
 __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t item,
                                                 uint8_t* warp_smem, const SharedTables& st,
                                                 uint32_t lane) {
-    const uint32_t idx = 32u * item + lane;
-    if (idx < p.n_c) {
+    uint32_t idx, end;
+    if (item < p.n_c_solo) {
+        idx = lane == 0 ? item : p.n_c;
+        end = p.n_c_solo;
+    } else {
+        idx = p.n_c_solo + 32u * (item - p.n_c_solo) + lane;
+        end = p.n_c;
+    }
+    if (idx < end) {
         const BatchMsg m = p.msgs[p.c_list[idx]];
         uint8_t* ch = warp_smem + TDES_SUBKEY_WORDS * lane;
         stage_chunks(ch, p.keychunks + (uint64_t)m.key * kPerKeyChunks);
         uint64_t prev = m.iv;
         for (uint64_t i = 0; i < m.nblocks; ++i) {
-            prev = tdes_block_scalar_nib(load_be(m.in, i) ^ prev, st.sp, ch, st.ipn, st.fpn);
+            prev = tdes_block_scalar_nib(load_be(m.in, i) ^ prev, st.sp,
+                                         reinterpret_cast<const uint32_t*>(ch), st.ipn, st.fpn);
             store_be(m.out, i, prev);
         }
     }
@@ -616,7 +628,11 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     p.keychunks = kt->chunks;
     p.c_list = reinterpret_cast<const uint32_t*>(base + o_c);
     p.n_c = (uint32_t)c_list.size();
-    p.n_c_items = (p.n_c + 31) / 32;
+    // chains longer than kSoloChainBlocks get a warp of their own
+    p.n_c_solo = 0;
+    while (p.n_c_solo < p.n_c && msgs[c_list[p.n_c_solo]].nblocks > tdes::kSoloChainBlocks)
+        ++p.n_c_solo;
+    p.n_c_items = p.n_c_solo + (p.n_c - p.n_c_solo + 31) / 32;
     p.b_msg = reinterpret_cast<const uint32_t*>(base + o_bm);
     p.b_prefix = reinterpret_cast<const uint64_t*>(base + o_bp);
     p.n_b = (uint32_t)b_msg.size();

@@ -154,23 +154,33 @@ TDES_HD uint64_t permute64(uint64_t v, const uint8_t* __restrict__ src) {
     return r;
 }
 
-// sp: 8 x 64 S-box/permutation words; chunks: 48 rounds x 8 six-bit round-key
-// groups; ip/fp: the permutations as 0-based source bits.
+// One Feistel round of the scalar path.  The expansion windows of S-boxes
+// 1, 7, 5, 3 are the four bytes of rotr(R, 27) and those of S-boxes 2, 8, 6, 4
+// the four bytes of rotr(R, 23) (six bits each, first bit most significant),
+// so two rotates and two XORs with the round's key words ke/ko form all eight
+// S-box inputs; sp[64g + x] is S-box g followed by the permutation.
+TDES_HD uint32_t tdes_f_scalar(uint32_t R, uint32_t ke, uint32_t ko,
+                               const uint32_t* __restrict__ sp) {
+    const uint32_t we = rotr32(R, 27) ^ ke;
+    const uint32_t wo = rotr32(R, 23) ^ ko;
+    const uint32_t a = sp[0 * 64 + (we & 63u)] ^ sp[6 * 64 + ((we >> 8) & 63u)] ^
+                       sp[4 * 64 + ((we >> 16) & 63u)];
+    const uint32_t b = sp[2 * 64 + ((we >> 24) & 63u)] ^ sp[1 * 64 + (wo & 63u)] ^
+                       sp[7 * 64 + ((wo >> 8) & 63u)];
+    const uint32_t c = sp[5 * 64 + ((wo >> 16) & 63u)] ^ sp[3 * 64 + ((wo >> 24) & 63u)];
+    return a ^ b ^ c;
+}
+
+// sp: 8 x 64 S-box/permutation words; keys: 48 rounds x (ke, ko) words (the
+// round-key groups in the byte order of the expansion windows); ip/fp: the
+// permutations as 0-based source bits.
 TDES_HD uint64_t tdes_block_scalar(uint64_t v, const uint32_t* __restrict__ sp,
-                                   const uint8_t* __restrict__ chunks,
+                                   const uint32_t* __restrict__ keys,
                                    const uint8_t* __restrict__ ip, const uint8_t* __restrict__ fp) {
     v = permute64(v, ip);
     uint32_t L = (uint32_t)(v >> 32), R = (uint32_t)v;
     for (int r = 0; r < 48; ++r) {
-        const uint8_t* k = chunks + 8 * r;
-        uint32_t f = 0;
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            // S-box g reads half bits 4g .. 4g+5 (cyclic), the first one most significant
-            const uint32_t x = (rotr32(R, (27 - 4 * g) & 31) & 63u) ^ k[g];
-            f ^= sp[64 * g + x];
-        }
-        const uint32_t t = L ^ f;
+        const uint32_t t = L ^ tdes_f_scalar(R, keys[2 * r], keys[2 * r + 1], sp);
         L = R;
         R = t;
         if ((r & 15) == 15) {  // end of a DES pass: undo the last swap (R16 || L16)
@@ -192,29 +202,26 @@ TDES_HD uint64_t permute64_nib(uint64_t v, const uint64_t* __restrict__ tab) {
 }
 
 // The same EDE3 block as tdes_block_scalar with the permutations by nibble
-// tables (ipn/fpn: 16 x 16 words each) instead of bit loops.
+// tables (ipn/fpn: 16 x 16 words each) instead of bit loops.  The 16 rounds
+// of a DES pass are unrolled by two so that the halves alternate in place.
 TDES_HD uint64_t tdes_block_scalar_nib(uint64_t v, const uint32_t* __restrict__ sp,
-                                       const uint8_t* __restrict__ chunks,
+                                       const uint32_t* __restrict__ keys,
                                        const uint64_t* __restrict__ ipn,
                                        const uint64_t* __restrict__ fpn) {
     v = permute64_nib(v, ipn);
     uint32_t L = (uint32_t)(v >> 32), R = (uint32_t)v;
-    for (int r = 0; r < 48; ++r) {
-        const uint8_t* k = chunks + 8 * r;
-        uint32_t f = 0;
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const uint32_t x = (rotr32(R, (27 - 4 * g) & 31) & 63u) ^ k[g];
-            f ^= sp[64 * g + x];
+    for (int pass = 0; pass < 3; ++pass) {
+        const uint32_t* k = keys + 32 * pass;
+#pragma unroll 2
+        for (int r = 0; r < 16; r += 2) {
+            L ^= tdes_f_scalar(R, k[2 * r], k[2 * r + 1], sp);
+            R ^= tdes_f_scalar(L, k[2 * r + 2], k[2 * r + 3], sp);
         }
-        const uint32_t t = L ^ f;
+        // after 16 in-place rounds L = L16, R = R16; the next pass (or the
+        // output R16 || L16) starts from the swapped halves
+        const uint32_t u = L;
         L = R;
-        R = t;
-        if ((r & 15) == 15) {
-            const uint32_t u = L;
-            L = R;
-            R = u;
-        }
+        R = u;
     }
     return permute64_nib(((uint64_t)L << 32) | R, fpn);
 }

@@ -20,8 +20,8 @@ static_assert(kChunkBytes == TDES_SUBKEY_WORDS, "chunk size mismatch");
 __device__ const uint8_t kRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
 __device__ const uint8_t kSubkeyBits[2][48][48] = TDES_SUBKEY_INIT;
 __device__ const uint32_t kSP[8][64] = TDES_SP_INIT;
-__device__ const uint8_t kIPsrc[64] = TDES_IP_INIT;
-__device__ const uint8_t kFPsrc[64] = TDES_FP_INIT;
+__device__ const uint64_t kIPN[16][16] = TDES_IPN_INIT;
+__device__ const uint64_t kFPN[16][16] = TDES_FPN_INIT;
 
 int sbox_gate_count() { return TDES_SBOX_GATES; }
 
@@ -289,17 +289,19 @@ cudaError_t launch_cbc_dec(const uint32_t* tab_dec, uint64_t iv, const void* in,
 
 // --------------------------------------------------------------- CBC encrypt
 // C_i = E(P_i XOR C_{i-1}): serial, one thread walks the chain with the
-// scalar round (S-box/permutation words in shared memory).
+// scalar round (S-box/permutation words and nibble permutation tables in
+// shared memory).
 __global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64_t iv,
                                     const uint8_t* in, uint8_t* out, uint64_t nblocks) {
-    __shared__ uint32_t sp[8 * 64];
-    __shared__ uint8_t ch[TDES_SUBKEY_WORDS];
-    __shared__ uint8_t ip[64], fp[64];
+    __shared__ __align__(16) uint32_t sp[8 * 64];
+    __shared__ __align__(16) uint32_t keys[TDES_SUBKEY_WORDS / 4];
+    __shared__ __align__(16) uint64_t ipn[16 * 16], fpn[16 * 16];
     for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) sp[i] = (&kSP[0][0])[i];
-    for (int i = threadIdx.x; i < TDES_SUBKEY_WORDS; i += blockDim.x) ch[i] = chunks_g[i];
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-        ip[i] = kIPsrc[i];
-        fp[i] = kFPsrc[i];
+    for (int i = threadIdx.x; i < TDES_SUBKEY_WORDS / 4; i += blockDim.x)
+        keys[i] = reinterpret_cast<const uint32_t*>(chunks_g)[i];
+    for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) {
+        ipn[i] = (&kIPN[0][0])[i];
+        fpn[i] = (&kFPN[0][0])[i];
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -308,7 +310,7 @@ __global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64
     uint64_t prev = iv;
     for (uint64_t i = 0; i < nblocks; ++i) {
         const uint64_t x = bswap64(p[i]) ^ prev;
-        prev = tdes_block_scalar(x, sp, ch, ip, fp);
+        prev = tdes_block_scalar_nib(x, sp, keys, ipn, fpn);
         q[i] = bswap64(prev);
     }
 }

@@ -137,6 +137,12 @@ def recipe():
     return words
 
 
+# S-box whose six-bit round-key group sits in byte p of a scalar round-key word
+# pair: rotr(R, 27) puts the expansion windows of S-boxes 1, 7, 5, 3 (0-based
+# 0, 6, 4, 2) at bits 0, 8, 16, 24, and rotr(R, 23) those of S-boxes 2, 8, 6, 4.
+SCALAR_GROUP_ORDER = (0, 6, 4, 2, 1, 7, 5, 3)
+
+
 def subkey_source(direction, r):
     """(key index 0..2, DES round-key index 0..15) of EDE3 round r."""
     stage, k = divmod(r, 16)
@@ -274,15 +280,23 @@ def emit(path: str = OUT) -> str:
     L.append("#pragma once")
     L.append("#include <cstdint>")
     L.append("")
-    L.append("// Scalar path (serial CBC encryption).  Round-key bit j of EDE3 round r:")
+    L.append("// Scalar path.  Per EDE3 round r: 8 six-bit round-key groups, byte p holding")
+    L.append("// the group of S-box SCALAR_GROUP_ORDER[p] (so the 8 bytes read as two")
+    L.append("// little-endian words line up with the expansion windows of rotr(R, 27) and")
+    L.append("// rotr(R, 23)); entry [dir][r][6p + u] = key bit of bit u of byte p:")
     L.append("// 64*key + (key bit - 1), [0] encrypt, [1] decrypt.")
+    L.append("#define TDES_SCALAR_GROUP_ORDER {" + ",".join(map(str, SCALAR_GROUP_ORDER)) + "}")
     L.append("#define TDES_SUBKEY_INIT { \\")
     rkb = T.round_key_bits()
     for direction in ("enc", "dec"):
         L.append("  { \\")
         for r in range(48):
             key, sub = subkey_source(direction, r)
-            L.append("    {" + ",".join(str(64 * key + rkb[sub][j] - 1) for j in range(48)) + "}, \\")
+            bits = []
+            for pos in range(8):
+                g = SCALAR_GROUP_ORDER[pos]
+                bits += [64 * key + rkb[sub][6 * g + u] - 1 for u in range(6)]
+            L.append("    {" + ",".join(map(str, bits)) + "}, \\")
         L.append("  }, \\")
     L.append("}")
     L.append("")

@@ -56,7 +56,7 @@ int main(int argc, char** argv) {
             }
         }
     } else {
-        uint8_t chunks[TDES_SUBKEY_WORDS];
+        alignas(16) uint8_t chunks[TDES_SUBKEY_WORDS];
         for (int r = 0; r < 48; ++r)
             for (int g = 0; g < 8; ++g) chunks[8 * r + g] = tdes_subkey_chunk(keys, &kSub[dec][r][6 * g]);
         for (size_t i = 0; i < n; ++i) {
@@ -64,9 +64,11 @@ int main(int argc, char** argv) {
             memcpy(&v, &data[8 * i], 8);
             v = bswap64(v);
             if (argv[1][1] == 'n')
-                v = tdes_block_scalar_nib(v, &kSP[0][0], chunks, &kIPN[0][0], &kFPN[0][0]);
+                v = tdes_block_scalar_nib(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks),
+                                          &kIPN[0][0], &kFPN[0][0]);
             else
-                v = tdes_block_scalar(v, &kSP[0][0], chunks, kIP, kFP);
+                v = tdes_block_scalar(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks), kIP,
+                                      kFP);
             v = bswap64(v);
             memcpy(&out[8 * i], &v, 8);
         }
