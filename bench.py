@@ -281,6 +281,9 @@ def run_ours(args):
     # ---- batched: 4096 messages with their own keys and modes, one launch
     batched = None if args.no_batch else run_batched(torch, tdes, synth, stream, value)
 
+    # ---- serving: Poisson arrivals at fractions of the measured peak
+    serving = None if args.no_serve else run_serving(torch, tdes, synth, x)
+
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -343,6 +346,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
         "batched": batched,
+        "serving": serving,
         "extra": {"kernel_ms_per_launch": round(per_launch_ms, 4),
                   "ecb_decrypt_gbs": round(NBYTES / (dec_ms * 1e-3) / 1e9, 3),
                   "ctr_gbs": round(NBYTES / (ctr_ms * 1e-3) / 1e9, 3),
@@ -436,6 +440,39 @@ def run_batched(torch, tdes, synth, stream, ecb_gbs):
     }
 
 
+# ---------------------------------------------------------------- serving
+SERVE_WORKLOAD = ("open-loop Poisson arrivals; sizes 80% uniform 64 B..4 KiB, 20% log-uniform "
+                  "64 KiB..16 MiB; key drawn per request from 16384 resident triples; modes "
+                  "ECB/CTR/CBC-decrypt 1/3 each; 8 GiB admission budget; payloads resident "
+                  "in HBM; latency = completion - scheduled arrival")
+
+
+def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
+    kt = tdes.KeyTable(synth.key_triples(4, 16384))
+    srv = tdes.Server(kt, budget_bytes=8 << 30, slots=4, warps_per_cta=4)
+    out_pool = torch.empty(8 << 30, dtype=torch.uint8, device=in_pool.device)
+    srv.loadtest(in_pool, out_pool, 2000, 0.0, seed=99)  # warm-up
+    peak = srv.loadtest(in_pool, out_pool, n_peak, 0.0, seed=5)
+    points = []
+    for frac in (0.25, 0.5, 0.75, 0.95):
+        r = srv.loadtest(in_pool, out_pool, n_points, frac * peak["gbps"], seed=int(frac * 100))
+        points.append({"load": frac, "offered_gbs": round(r["offered_gbps"], 2),
+                       "achieved_gbs": round(r["gbps"], 2),
+                       "p50_ms": round(r["p50_ms"], 4), "p99_ms": round(r["p99_ms"], 4),
+                       "p999_ms": round(r["p999_ms"], 4),
+                       "small_p50_ms": round(r["small_p50_ms"], 4),
+                       "small_p99_ms": round(r["small_p99_ms"], 4),
+                       "large_p50_ms": round(r["large_p50_ms"], 4),
+                       "large_p99_ms": round(r["large_p99_ms"], 4),
+                       "requests": r["requests"], "batches": r["batches"],
+                       "duration_s": round(r["duration_s"], 3)})
+    srv.close()
+    del out_pool
+    return {"workload": SERVE_WORKLOAD, "peak_closed_loop_gbs": round(peak["gbps"], 2),
+            "peak_p50_ms": round(peak["p50_ms"], 3), "points": points,
+            "server": srv.config}
+
+
 # ------------------------------------------------------------- reference
 def run_reference(args):
     """The CPU oracle on the host cores: rank 0 only."""
@@ -486,6 +523,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -202,6 +202,84 @@ int tdes_batch_info(const tdes_batch_t *b, tdes_batch_info_t *info);
 /* Frees a plan; no launch of it may still be running. */
 void tdes_batch_free(tdes_batch_t *b);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of individual requests.  Not in the paper.
+ * ------------------------------------------------------------------------ */
+
+typedef struct tdes_server tdes_server_t; /* opaque */
+
+typedef struct {
+    uint64_t budget_bytes;   /* HBM admission budget: input + output bytes of the requests
+                                admitted and not yet complete (in place counts once) */
+    uint32_t slots;          /* batches in flight at once, each on its own stream */
+    uint32_t max_batch;      /* requests per batch at most */
+    int warps_per_cta;       /* persistent-kernel shape, 1..8 */
+    int reserve_ctas_per_sm; /* with slots > 1: CTAs per SM a batch leaves for the next one */
+    uint32_t ring_entries;   /* completion records kept; older tickets read as complete */
+} tdes_server_config_t;
+
+/* Defaults: 8 GiB budget, 4 slots, 16384 requests per batch, 4 warps per CTA,
+ * 1 CTA per SM reserved, 2^21 completion records. */
+void tdes_server_config_default(tdes_server_config_t *cfg);
+
+/* Starts a server on the current device over a key table (which must
+ * outlive it).  A dispatcher thread admits queued requests in arrival order
+ * while the admitted bytes stay within the budget, plans each admitted group
+ * into one persistent batch launch on a free slot, and records completions;
+ * requests arriving while batches run go into the next free slot. */
+int tdes_server_create(const tdes_keytable_t *kt, const tdes_server_config_t *cfg,
+                       tdes_server_t **out);
+
+/* Queues one request (same rules as a batch descriptor; device buffers must
+ * stay valid until it completes).  Never blocks: *ticket identifies it.
+ * TDES_EINVAL for a bad descriptor or one larger than the whole budget. */
+int tdes_server_submit(tdes_server_t *s, const tdes_desc_t *req, uint64_t *ticket);
+
+/* 0 complete, 1 pending, < 0 the request failed. */
+int tdes_server_poll(tdes_server_t *s, uint64_t ticket);
+
+/* Waits (bounded) for a ticket: its status, or TDES_ETIMEDOUT; never hangs. */
+int tdes_server_wait(tdes_server_t *s, uint64_t ticket, uint64_t timeout_ns);
+
+/* Finishes every queued and running request, then stops the server. */
+void tdes_server_destroy(tdes_server_t *s);
+
+/* Open-loop load generator for a server.  Draws n_requests requests from a
+ * seeded SplitMix64 stream: with probability small_frac a size uniform in
+ * [small_min, small_max], else log-uniform in [large_min, large_max] (both
+ * rounded down to multiples of 8); mode ECB-encrypt / CTR / CBC-decrypt with
+ * mode_probs; key index uniform below n_keys; input at a random 16-byte
+ * aligned offset of in_pool; output in a ring over out_pool whose regions
+ * are reused only after their previous request completed.  Arrivals are
+ * Poisson at offered_gbps of payload (<= 0: all at once, i.e. saturation).
+ * Latency = completion time seen by the dispatcher - scheduled arrival. */
+typedef struct {
+    uint64_t n_requests;
+    double offered_gbps;
+    uint64_t seed;
+    double small_frac;
+    uint32_t small_min, small_max;
+    uint64_t large_min, large_max;
+    double mode_probs[3];
+    uint32_t n_keys;
+    const void *in_pool;
+    uint64_t in_pool_bytes;
+    void *out_pool;
+    uint64_t out_pool_bytes;
+} tdes_loadtest_config_t;
+
+typedef struct {
+    double p50_ms, p90_ms, p99_ms, p999_ms, mean_ms, max_ms;
+    double small_p50_ms, small_p99_ms, large_p50_ms, large_p99_ms;
+    double gbps;          /* payload bytes / (last completion - start) */
+    double offered_gbps;
+    double duration_s;
+    uint64_t requests, bytes, batches;
+} tdes_loadtest_result_t;
+
+int tdes_serve_loadtest(tdes_server_t *s, const tdes_loadtest_config_t *cfg,
+                        tdes_loadtest_result_t *res);
+
 /* Number of LOP3 instructions the eight generated S-box circuits take per
  * round, i.e. per 32 blocks per round (the circuit size fixed at build time). */
 int tdes_sbox_gate_count(void);

@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtdes_gb300.so")
 PROBE_LIB = os.path.join(HERE, "libtdes_probe.so")  # benchmark's LOP3-rate probe, not the cipher
-SOURCES = ["tdes_api.cu", "tdes_kernels.cu", "tdes_noalloc.cu", "tdes_batch.cu"]
+SOURCES = ["tdes_api.cu", "tdes_kernels.cu", "tdes_noalloc.cu", "tdes_batch.cu", "tdes_serve.cu"]
 PROBE_SOURCES = ["tdes_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

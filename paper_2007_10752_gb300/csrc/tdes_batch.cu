@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/tdes.h"
+#include "tdes_batch_internal.h"
 #include "tdes_internal.h"
 #include "tdes_keysched.cuh"
 
@@ -38,33 +39,6 @@ constexpr int kPerKeyWords = 2 * TDES_TABLE_WORDS;        // enc + dec bitsliced
 constexpr int kPerKeyChunks = 2 * TDES_SUBKEY_WORDS;      // enc + dec scalar groups
 constexpr int kWarpSmemBytes = TDES_TABLE_WORDS * 4;      // one table per warp (13 KB)
 static_assert(32 * TDES_SUBKEY_WORDS <= kWarpSmemBytes, "scalar groups must fit a warp slice");
-
-struct BatchMsg {
-    const uint8_t* in;
-    uint8_t* out;
-    uint64_t nblocks;
-    uint64_t iv;  // CBC: IV; CTR: first counter block
-    uint32_t key;
-    uint32_t mode;
-};
-
-struct BatchParams {
-    const BatchMsg* msgs;
-    const uint32_t* keytab;    // [key][dir][TDES_TABLE_WORDS]
-    const uint8_t* keychunks;  // [key][dir][TDES_SUBKEY_WORDS]
-    const uint32_t* c_list;    // CBC-enc message indices, longest first
-    uint32_t n_c, n_c_items;
-    uint32_t n_c_solo;         // the first n_c_solo chains run one per warp
-    const uint32_t* b_msg;     // large message index per B entry
-    const uint64_t* b_prefix;  // exclusive prefix of tiles, n_b + 1 entries
-    uint32_t n_b;
-    uint64_t n_b_tiles;
-    const uint32_t* s_list;    // small message indices
-    const uint2* s_items;      // (first, count) into s_list, whole messages, <= 32 blocks
-    uint32_t n_s_items;
-    uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
-    unsigned long long* counter;
-};
 
 __device__ const uint32_t kBatchSP[8][64] = TDES_SP_INIT;
 __device__ const uint64_t kBatchIPN[16][16] = TDES_IPN_INIT;
@@ -375,13 +349,143 @@ __global__ void tdes_batch_halo_kernel(BatchParams p) {
 
 // ===================================================================== host
 
-struct tdes_keytable {
-    int device;
-    uint32_t count;
-    void* mem;
-    uint32_t* tabs;
-    uint8_t* chunks;
-};
+namespace tdes {
+
+int validate_desc(const tdes_desc_t& d, uint32_t key_count) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(d.in), o = reinterpret_cast<uintptr_t>(d.out);
+    if (d.mode > TDES_MODE_CBC_ENCRYPT || d.key_index >= key_count || d.nbytes % 8 != 0)
+        return TDES_EINVAL;
+    if (d.nbytes > 0 && (d.in == nullptr || d.out == nullptr || ((a | o) & 7u))) return TDES_EINVAL;
+    if (a != o && a < o + d.nbytes && o < a + d.nbytes) return TDES_EINVAL;
+    if (d.mode == TDES_MODE_CTR && (d.iv_or_ctr & 0xFFFFFFFFull) + d.nbytes / 8 > (1ull << 32))
+        return TDES_EINVAL;
+    return TDES_OK;
+}
+
+static size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, int* status,
+                PlanHost* h) {
+    std::vector<BatchMsg> msgs;
+    std::vector<uint32_t> c_list, b_msg, s_list;
+    std::vector<uint64_t> b_prefix(1, 0);
+    std::vector<uint2> s_items;
+    *h = PlanHost();
+    msgs.reserve(count);
+    for (uint32_t i = 0; i < count; ++i) {
+        const tdes_desc_t& d = descs[i];
+        const int st = validate_desc(d, key_count);
+        if (status) status[i] = st;
+        if (st != TDES_OK) {
+            ++h->invalid;
+            continue;
+        }
+        if (d.nbytes == 0) continue;
+        const uint32_t mi = (uint32_t)msgs.size();
+        const uint64_t nb = d.nbytes / 8;
+        msgs.push_back({static_cast<const uint8_t*>(d.in), static_cast<uint8_t*>(d.out), nb,
+                        d.iv_or_ctr, d.key_index, d.mode});
+        h->bytes_per_mode[d.mode] += d.nbytes;
+        if (d.mode == TDES_MODE_CBC_ENCRYPT) {
+            c_list.push_back(mi);
+        } else if (nb <= (uint64_t)kSmallBlocks) {
+            s_list.push_back(mi);
+        } else {
+            b_msg.push_back(mi);
+            b_prefix.push_back(b_prefix.back() + (nb + kTileBlocks - 1) / kTileBlocks);
+            if (d.mode == TDES_MODE_CBC_DECRYPT && d.in == d.out) h->needs_halo = true;
+        }
+    }
+    std::stable_sort(c_list.begin(), c_list.end(),
+                     [&](uint32_t x, uint32_t y) { return msgs[x].nblocks > msgs[y].nblocks; });
+    for (uint32_t i = 0; i < s_list.size();) {  // small messages packed whole, <= 32 blocks
+        const uint32_t first = i;
+        uint32_t blocks = 0;
+        while (i < s_list.size() && blocks + msgs[s_list[i]].nblocks <= (uint64_t)kSmallBlocks)
+            blocks += (uint32_t)msgs[s_list[i++]].nblocks;
+        s_items.push_back(make_uint2(first, i - first));
+    }
+    h->n_c = (uint32_t)c_list.size();
+    while (h->n_c_solo < h->n_c && msgs[c_list[h->n_c_solo]].nblocks > kSoloChainBlocks)
+        ++h->n_c_solo;
+    h->n_c_items = h->n_c_solo + (h->n_c - h->n_c_solo + 31) / 32;
+    h->n_b = (uint32_t)b_msg.size();
+    h->n_b_tiles = b_prefix.back();
+    h->n_s_items = (uint32_t)s_items.size();
+    h->total_items = (uint64_t)h->n_c_items + h->n_b_tiles + h->n_s_items;
+    size_t off = 0;
+    auto take = [&](size_t n) { const size_t o = align16(off); off = o + n; return o; };
+    h->o_msgs = take(msgs.size() * sizeof(BatchMsg));
+    h->o_c = take(c_list.size() * 4);
+    h->o_bm = take(b_msg.size() * 4);
+    h->o_bp = take(b_prefix.size() * 8);
+    h->o_sl = take(s_list.size() * 4);
+    h->o_si = take(s_items.size() * sizeof(uint2));
+    h->o_halo = take(h->needs_halo ? h->n_b_tiles * 8 : 0);
+    h->o_ctr = take(8);
+    h->image.assign(align16(off), 0);
+    auto put = [&](size_t o, const void* src, size_t n) {
+        if (n) memcpy(h->image.data() + o, src, n);
+    };
+    put(h->o_msgs, msgs.data(), msgs.size() * sizeof(BatchMsg));
+    put(h->o_c, c_list.data(), c_list.size() * 4);
+    put(h->o_bm, b_msg.data(), b_msg.size() * 4);
+    put(h->o_bp, b_prefix.data(), b_prefix.size() * 8);
+    put(h->o_sl, s_list.data(), s_list.size() * 4);
+    put(h->o_si, s_items.data(), s_items.size() * sizeof(uint2));
+}
+
+BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt) {
+    uint8_t* base = static_cast<uint8_t*>(dev_base);
+    BatchParams p;
+    p.msgs = reinterpret_cast<const BatchMsg*>(base + h.o_msgs);
+    p.keytab = kt->tabs;
+    p.keychunks = kt->chunks;
+    p.c_list = reinterpret_cast<const uint32_t*>(base + h.o_c);
+    p.n_c = h.n_c;
+    p.n_c_items = h.n_c_items;
+    p.n_c_solo = h.n_c_solo;
+    p.b_msg = reinterpret_cast<const uint32_t*>(base + h.o_bm);
+    p.b_prefix = reinterpret_cast<const uint64_t*>(base + h.o_bp);
+    p.n_b = h.n_b;
+    p.n_b_tiles = h.n_b_tiles;
+    p.s_list = reinterpret_cast<const uint32_t*>(base + h.o_sl);
+    p.s_items = reinterpret_cast<const uint2*>(base + h.o_si);
+    p.n_s_items = h.n_s_items;
+    p.halo = h.needs_halo ? reinterpret_cast<uint64_t*>(base + h.o_halo) : nullptr;
+    p.counter = reinterpret_cast<unsigned long long*>(base + h.o_ctr);
+    return p;
+}
+
+cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
+    const size_t dyn = (size_t)warps * kWarpSmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(tdes_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_batch_kernel, 32 * warps, dyn);
+    if (e != cudaSuccess) return e;
+    *dyn_smem = dyn;
+    *ctas_fit = n < 1 ? 1 : n;
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo, int warps,
+                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s) {
+    if (total_items == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (needs_halo && p.n_b_tiles) {
+        tdes_batch_halo_kernel<<<(unsigned)((p.n_b_tiles + 255) / 256), 256, 0, s>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const uint64_t want = (total_items + warps - 1) / warps;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
+    tdes_batch_kernel<<<grid, 32 * warps, dyn_smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace tdes
 
 struct tdes_batch {
     int device;
@@ -396,7 +500,6 @@ struct tdes_batch {
     size_t dyn_smem;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    cudaStream_t graph_stream;
     uint64_t bytes[5];  // payload bytes per mode
 };
 
@@ -417,22 +520,11 @@ int bcuda(cudaError_t e, const char* what) {
                  cudaGetErrorString(e));
 }
 
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-int max_ctas_per_sm(int warps, size_t dyn_smem) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes::tdes_batch_kernel, 32 * warps,
-                                                      dyn_smem) != cudaSuccess)
-        return 1;
-    return n < 1 ? 1 : n;
-}
-
 int set_launch_config(tdes_batch_t* b, int warps, int ctas_per_sm) {
-    const size_t dyn = (size_t)warps * tdes::kWarpSmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(tdes::tdes_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return bcuda(e, "cudaFuncSetAttribute(batch kernel smem)");
-    const int fit = max_ctas_per_sm(warps, dyn);
+    size_t dyn = 0;
+    int fit = 1;
+    cudaError_t e = tdes::prepare_batch_kernel(warps, &dyn, &fit);
+    if (e != cudaSuccess) return bcuda(e, "batch kernel set-up");
     b->warps = warps;
     b->dyn_smem = dyn;
     b->ctas_per_sm = ctas_per_sm < 1 ? fit : std::min(ctas_per_sm, fit);
@@ -446,18 +538,8 @@ int set_launch_config(tdes_batch_t* b, int warps, int ctas_per_sm) {
 }
 
 cudaError_t enqueue(tdes_batch_t* b, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b->params.counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
-    if (b->needs_halo && b->params.n_b_tiles) {
-        const unsigned grid = (unsigned)((b->params.n_b_tiles + 255) / 256);
-        tdes::tdes_batch_halo_kernel<<<grid, 256, 0, s>>>(b->params);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const uint64_t want_ctas = (b->total_items + b->warps - 1) / b->warps;
-    const uint64_t max_ctas = (uint64_t)b->sms * b->ctas_per_sm;
-    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want_ctas, max_ctas));
-    tdes::tdes_batch_kernel<<<grid, 32 * b->warps, b->dyn_smem, s>>>(b->params);
-    return cudaGetLastError();
+    return tdes::enqueue_batch(b->params, b->total_items, b->needs_halo, b->warps, b->dyn_smem,
+                               (uint64_t)b->sms * b->ctas_per_sm, s);
 }
 
 }  // namespace
@@ -473,8 +555,8 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
     const size_t tab_bytes = (size_t)count * tdes::kPerKeyWords * 4;
-    const size_t chunk_bytes = align_up((size_t)count * tdes::kPerKeyChunks, 16);
-    const size_t key_bytes = align_up((size_t)count * 24, 16);
+    const size_t chunk_bytes = tdes::align16((size_t)count * tdes::kPerKeyChunks);
+    const size_t key_bytes = tdes::align16((size_t)count * 24);
     void* mem = nullptr;
     e = cudaMalloc(&mem, tab_bytes + chunk_bytes + key_bytes);
     if (e != cudaSuccess) return bcuda(e, "cudaMalloc(key table)");
@@ -491,7 +573,8 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
     uint8_t* dkeys = kt->chunks + chunk_bytes;
     cudaStream_t s = nullptr;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dkeys, keys, (size_t)count * 24, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dkeys, keys, (size_t)count * 24, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const uint64_t n = (uint64_t)count * (tdes::kPerKeyWords + tdes::kPerKeyChunks);
         tdes::tdes_keytable_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dkeys, count,
@@ -532,83 +615,12 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
     if (dev != kt->device) return bfail(TDES_EINVAL, "key table lives on another device");
-
-    std::vector<tdes::BatchMsg> msgs;
-    std::vector<uint32_t> c_list, b_msg, s_list;
-    std::vector<uint64_t> b_prefix(1, 0);
-    std::vector<uint2> s_items;
-    uint64_t bytes[5] = {0, 0, 0, 0, 0};
-    bool needs_halo = false;
-    int invalid = 0;
-    msgs.reserve(count);
-    for (uint32_t i = 0; i < count; ++i) {
-        const tdes_desc_t& d = descs[i];
-        const uintptr_t a = reinterpret_cast<uintptr_t>(d.in), o = reinterpret_cast<uintptr_t>(d.out);
-        int st = TDES_OK;
-        if (d.mode > TDES_MODE_CBC_ENCRYPT || d.key_index >= kt->count || d.nbytes % 8 != 0)
-            st = TDES_EINVAL;
-        else if (d.nbytes > 0 && (d.in == nullptr || d.out == nullptr || ((a | o) & 7u)))
-            st = TDES_EINVAL;
-        else if (a != o && a < o + d.nbytes && o < a + d.nbytes)
-            st = TDES_EINVAL;
-        else if (d.mode == TDES_MODE_CTR && (d.iv_or_ctr & 0xFFFFFFFFull) + d.nbytes / 8 > (1ull << 32))
-            st = TDES_EINVAL;
-        if (per_desc_status) per_desc_status[i] = st;
-        if (st != TDES_OK) {
-            ++invalid;
-            continue;
-        }
-        if (d.nbytes == 0) continue;
-        const uint32_t mi = (uint32_t)msgs.size();
-        msgs.push_back({static_cast<const uint8_t*>(d.in), static_cast<uint8_t*>(d.out),
-                        d.nbytes / 8, d.iv_or_ctr, d.key_index, d.mode});
-        bytes[d.mode] += d.nbytes;
-        const uint64_t nb = d.nbytes / 8;
-        if (d.mode == TDES_MODE_CBC_ENCRYPT) {
-            c_list.push_back(mi);
-        } else if (nb <= (uint64_t)tdes::kSmallBlocks) {
-            s_list.push_back(mi);
-        } else {
-            b_msg.push_back(mi);
-            b_prefix.push_back(b_prefix.back() + (nb + tdes::kTileBlocks - 1) / tdes::kTileBlocks);
-            if (d.mode == TDES_MODE_CBC_DECRYPT && d.in == d.out) needs_halo = true;
-        }
-    }
-    std::stable_sort(c_list.begin(), c_list.end(), [&](uint32_t x, uint32_t y) {
-        return msgs[x].nblocks > msgs[y].nblocks;
-    });
-    // pack small messages whole into items of at most 32 blocks
-    for (uint32_t i = 0; i < s_list.size();) {
-        uint32_t first = i, blocks = 0;
-        while (i < s_list.size() && blocks + msgs[s_list[i]].nblocks <= (uint64_t)tdes::kSmallBlocks)
-            blocks += (uint32_t)msgs[s_list[i++]].nblocks;
-        s_items.push_back(make_uint2(first, i - first));
-    }
-    const uint64_t n_b_tiles = b_prefix.back();
-
-    // one device allocation for everything the kernel reads
-    size_t off = 0;
-    auto take = [&](size_t n) { size_t o2 = align_up(off, 16); off = o2 + n; return o2; };
-    const size_t o_msgs = take(msgs.size() * sizeof(tdes::BatchMsg));
-    const size_t o_c = take(c_list.size() * 4);
-    const size_t o_bm = take(b_msg.size() * 4);
-    const size_t o_bp = take(b_prefix.size() * 8);
-    const size_t o_sl = take(s_list.size() * 4);
-    const size_t o_si = take(s_items.size() * sizeof(uint2));
-    const size_t o_halo = take(needs_halo ? n_b_tiles * 8 : 0);
-    const size_t o_ctr = take(8);
-    std::vector<uint8_t> host(off, 0);
-    auto put = [&](size_t o, const void* src, size_t n) { if (n) memcpy(host.data() + o, src, n); };
-    put(o_msgs, msgs.data(), msgs.size() * sizeof(tdes::BatchMsg));
-    put(o_c, c_list.data(), c_list.size() * 4);
-    put(o_bm, b_msg.data(), b_msg.size() * 4);
-    put(o_bp, b_prefix.data(), b_prefix.size() * 8);
-    put(o_sl, s_list.data(), s_list.size() * 4);
-    put(o_si, s_items.data(), s_items.size() * sizeof(uint2));
+    tdes::PlanHost h;
+    tdes::build_plan(descs, count, kt->count, per_desc_status, &h);
     void* mem = nullptr;
-    e = cudaMalloc(&mem, off);
+    e = cudaMalloc(&mem, h.image.size());
     if (e != cudaSuccess) return bcuda(e, "cudaMalloc(batch plan)");
-    e = cudaMemcpy(mem, host.data(), off, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(mem, h.image.data(), h.image.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(mem);
         return bcuda(e, "cudaMemcpy(batch plan)");
@@ -618,33 +630,13 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
         cudaFree(mem);
         return bfail(TDES_ENOMEM, "host allocation failed");
     }
-    uint8_t* base = static_cast<uint8_t*>(mem);
     b->device = dev;
     b->kt = kt;
     b->mem = mem;
-    tdes::BatchParams& p = b->params;
-    p.msgs = reinterpret_cast<const tdes::BatchMsg*>(base + o_msgs);
-    p.keytab = kt->tabs;
-    p.keychunks = kt->chunks;
-    p.c_list = reinterpret_cast<const uint32_t*>(base + o_c);
-    p.n_c = (uint32_t)c_list.size();
-    // chains longer than kSoloChainBlocks get a warp of their own
-    p.n_c_solo = 0;
-    while (p.n_c_solo < p.n_c && msgs[c_list[p.n_c_solo]].nblocks > tdes::kSoloChainBlocks)
-        ++p.n_c_solo;
-    p.n_c_items = p.n_c_solo + (p.n_c - p.n_c_solo + 31) / 32;
-    p.b_msg = reinterpret_cast<const uint32_t*>(base + o_bm);
-    p.b_prefix = reinterpret_cast<const uint64_t*>(base + o_bp);
-    p.n_b = (uint32_t)b_msg.size();
-    p.n_b_tiles = n_b_tiles;
-    p.s_list = reinterpret_cast<const uint32_t*>(base + o_sl);
-    p.s_items = reinterpret_cast<const uint2*>(base + o_si);
-    p.n_s_items = (uint32_t)s_items.size();
-    p.halo = needs_halo ? reinterpret_cast<uint64_t*>(base + o_halo) : nullptr;
-    p.counter = reinterpret_cast<unsigned long long*>(base + o_ctr);
-    b->total_items = (uint64_t)p.n_c_items + p.n_b_tiles + p.n_s_items;
-    b->needs_halo = needs_halo;
-    memcpy(b->bytes, bytes, sizeof bytes);
+    b->params = tdes::bind_plan(h, mem, kt);
+    b->total_items = h.total_items;
+    b->needs_halo = h.needs_halo;
+    memcpy(b->bytes, h.bytes_per_mode, sizeof b->bytes);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     int rc = set_launch_config(b, tdes::kWideWarps, 0);
     if (rc != TDES_OK) {
@@ -653,7 +645,7 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
         return rc;
     }
     *out = b;
-    if (invalid) bfail(TDES_EINVAL, "%d descriptor(s) rejected; see per_desc_status", invalid);
+    if (h.invalid) bfail(TDES_EINVAL, "%d descriptor(s) rejected; see per_desc_status", h.invalid);
     return TDES_OK;
 }
 

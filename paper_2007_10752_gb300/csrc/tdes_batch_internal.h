@@ -1,0 +1,73 @@
+// tdes_batch_internal.h -- batch plans shared by the batch API (tdes_batch.cu)
+// and the serving loop (tdes_serve.cu).  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tdes.h"
+
+struct tdes_keytable {
+    int device;
+    uint32_t count;
+    void* mem;
+    uint32_t* tabs;   // [key][dir][3328] bitsliced round-constant tables
+    uint8_t* chunks;  // [key][dir][384] scalar round-key words
+};
+
+namespace tdes {
+
+struct BatchMsg {
+    const uint8_t* in;
+    uint8_t* out;
+    uint64_t nblocks;
+    uint64_t iv;  // CBC: IV; CTR: first counter block
+    uint32_t key;
+    uint32_t mode;
+};
+
+struct BatchParams {
+    const BatchMsg* msgs;
+    const uint32_t* keytab;    // [key][dir][TDES_TABLE_WORDS]
+    const uint8_t* keychunks;  // [key][dir][TDES_SUBKEY_WORDS]
+    const uint32_t* c_list;    // CBC-enc message indices, longest first
+    uint32_t n_c, n_c_items;
+    uint32_t n_c_solo;         // the first n_c_solo chains run one per warp
+    const uint32_t* b_msg;     // large message index per B entry
+    const uint64_t* b_prefix;  // exclusive prefix of tiles, n_b + 1 entries
+    uint32_t n_b;
+    uint64_t n_b_tiles;
+    const uint32_t* s_list;    // small message indices
+    const uint2* s_items;      // (first, count) into s_list, whole messages, <= 32 blocks
+    uint32_t n_s_items;
+    uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
+    unsigned long long* counter;
+};
+
+
+// A batch laid out on the host as the byte image of its device buffer.
+struct PlanHost {
+    std::vector<uint8_t> image;
+    size_t o_msgs = 0, o_c = 0, o_bm = 0, o_bp = 0, o_sl = 0, o_si = 0, o_halo = 0, o_ctr = 0;
+    uint32_t n_c = 0, n_c_solo = 0, n_c_items = 0, n_b = 0, n_s_items = 0;
+    uint64_t n_b_tiles = 0, total_items = 0;
+    bool needs_halo = false;
+    uint64_t bytes_per_mode[5] = {0, 0, 0, 0, 0};
+    int invalid = 0;
+};
+
+// TDES_OK or TDES_EINVAL for one descriptor against a key table of key_count.
+int validate_desc(const tdes_desc_t& d, uint32_t key_count);
+// Validates and classifies n descriptors into `out` (status: nullable, n entries).
+void build_plan(const tdes_desc_t* d, uint32_t n, uint32_t key_count, int* status, PlanHost* out);
+// Kernel parameters of a plan whose image was copied to dev_base.
+BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt);
+// Sets the batch kernel's shared-memory limit for `warps` warps per CTA and
+// returns how many CTAs of that shape fit on an SM.
+cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit);
+// Counter reset, halo snapshot (if needed) and the persistent kernel on s.
+cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo, int warps,
+                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s);
+
+}  // namespace tdes

@@ -1,0 +1,455 @@
+// tdes_serve.cu -- continuous-batching request server over the batch kernel,
+// and an open-loop load generator that measures its latency.
+//
+// Requests (device buffers, one key index and mode each) are queued by
+// tdes_server_submit without blocking.  A dispatcher thread owns the GPU
+// side.  It admits queued requests in arrival order while the bytes in
+// flight (input + output) stay within the HBM budget, and plans every
+// admitted group into one persistent batch launch on one of several streams
+// ("slots").  Requests that arrive while earlier batches run are dispatched
+// into the next free slot at once, so their work overlaps on the device.
+// Each batch's grid leaves room on every SM for the next batch.  Key
+// schedules stay resident in the key table; the plan of each batch is
+// copied from pinned staging owned by its slot.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/tdes.h"
+#include "tdes_batch_internal.h"
+#include "tdes_internal.h"
+
+namespace {
+
+int sfail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    tdes::set_last_error(buf);
+    return status;
+}
+
+int scuda(cudaError_t e, const char* what) {
+    return sfail(e == cudaErrorMemoryAllocation ? TDES_ENOMEM : TDES_ECUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void* dmem = nullptr;
+    size_t dcap = 0;
+    uint8_t* pinned = nullptr;
+    size_t pcap = 0;
+    std::vector<uint64_t> tickets;
+    uint64_t cost = 0;
+    bool busy = false;
+};
+
+struct Pending {
+    tdes_desc_t d;
+    uint64_t ticket;
+    uint64_t cost;
+};
+
+struct Completion {
+    std::atomic<uint64_t> ticket{0};  // published last (release)
+    int status = 0;
+    int64_t t_done_ns = 0;
+};
+
+uint64_t cost_of(const tdes_desc_t& d) { return d.in == d.out ? d.nbytes : 2 * d.nbytes; }
+
+}  // namespace
+
+struct tdes_server {
+    int device = 0;
+    const tdes_keytable* kt = nullptr;
+    tdes_server_config_t cfg{};
+    int sms = 0, ctas_fit = 1;
+    size_t dyn_smem = 0;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::deque<Pending> queue;
+    uint64_t next_ticket = 1;
+    std::vector<Completion> ring;
+    std::thread thread;
+    std::atomic<bool> stop{false};
+    std::atomic<uint64_t> batches{0}, completed{0};
+    std::atomic<int> sticky_error{0};
+    uint64_t admitted = 0;  // dispatcher thread only
+
+    void complete(uint64_t ticket, int status, int64_t t) {
+        Completion& c = ring[ticket % ring.size()];
+        c.status = status;
+        c.t_done_ns = t;
+        c.ticket.store(ticket, std::memory_order_release);
+        completed.fetch_add(1, std::memory_order_relaxed);
+    }
+
+    bool ensure_capacity(Slot& sl, size_t n) {
+        if (sl.dcap < n) {
+            if (sl.dmem) cudaFree(sl.dmem);
+            sl.dmem = nullptr;
+            sl.dcap = 0;
+            const size_t want = std::max(n, (size_t)1 << 20) * 2;
+            if (cudaMalloc(&sl.dmem, want) != cudaSuccess) return false;
+            sl.dcap = want;
+        }
+        if (sl.pcap < n) {
+            if (sl.pinned) cudaFreeHost(sl.pinned);
+            sl.pinned = nullptr;
+            sl.pcap = 0;
+            const size_t want = std::max(n, (size_t)1 << 20) * 2;
+            if (cudaHostAlloc(reinterpret_cast<void**>(&sl.pinned), want, cudaHostAllocDefault) !=
+                cudaSuccess)
+                return false;
+            sl.pcap = want;
+        }
+        return true;
+    }
+
+    void dispatch_loop() {
+        cudaSetDevice(device);
+        std::vector<Pending> take;
+        std::vector<tdes_desc_t> descs;
+        tdes::PlanHost plan;
+        const uint64_t reserve = cfg.slots > 1 ? (uint64_t)std::max(0, cfg.reserve_ctas_per_sm) : 0;
+        const uint64_t per_sm = std::max<uint64_t>(1, (uint64_t)ctas_fit > reserve
+                                                          ? (uint64_t)ctas_fit - reserve : 1);
+        const uint64_t max_ctas = (uint64_t)sms * per_sm;
+        for (;;) {
+            bool worked = false;
+            bool any_busy = false;
+            for (Slot& sl : slots) {
+                if (!sl.busy) continue;
+                const cudaError_t q = cudaEventQuery(sl.done);
+                if (q == cudaErrorNotReady) {
+                    any_busy = true;
+                    continue;
+                }
+                const int st = q == cudaSuccess ? TDES_OK : TDES_ECUDA;
+                if (st != TDES_OK) sticky_error.store(st);
+                const int64_t t = now_ns();
+                for (uint64_t tk : sl.tickets) complete(tk, st, t);
+                admitted -= sl.cost;
+                sl.busy = false;
+                worked = true;
+            }
+            for (Slot& sl : slots) {
+                if (sl.busy) continue;
+                take.clear();
+                uint64_t cost = 0;
+                {
+                    std::lock_guard<std::mutex> lock(mu);
+                    while (!queue.empty() && take.size() < cfg.max_batch &&
+                           admitted + cost + queue.front().cost <= cfg.budget_bytes) {
+                        cost += queue.front().cost;
+                        take.push_back(queue.front());
+                        queue.pop_front();
+                    }
+                }
+                if (take.empty()) break;
+                descs.resize(take.size());
+                for (size_t i = 0; i < take.size(); ++i) descs[i] = take[i].d;
+                tdes::build_plan(descs.data(), (uint32_t)descs.size(), kt->count, nullptr, &plan);
+                cudaError_t e = cudaSuccess;
+                if (!ensure_capacity(sl, plan.image.size())) e = cudaErrorMemoryAllocation;
+                if (e == cudaSuccess) {
+                    memcpy(sl.pinned, plan.image.data(), plan.image.size());
+                    e = cudaMemcpyAsync(sl.dmem, sl.pinned, plan.image.size(),
+                                        cudaMemcpyHostToDevice, sl.stream);
+                }
+                if (e == cudaSuccess) {
+                    const tdes::BatchParams p = tdes::bind_plan(plan, sl.dmem, kt);
+                    e = tdes::enqueue_batch(p, plan.total_items, plan.needs_halo,
+                                            cfg.warps_per_cta, dyn_smem, max_ctas, sl.stream);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+                if (e != cudaSuccess) {
+                    sticky_error.store(TDES_ECUDA);
+                    const int64_t t = now_ns();
+                    for (const Pending& pd : take) complete(pd.ticket, TDES_ECUDA, t);
+                    continue;
+                }
+                sl.tickets.clear();
+                for (const Pending& pd : take) sl.tickets.push_back(pd.ticket);
+                sl.cost = cost;
+                sl.busy = true;
+                admitted += cost;
+                any_busy = true;
+                worked = true;
+                batches.fetch_add(1, std::memory_order_relaxed);
+            }
+            if (stop.load(std::memory_order_acquire) && !any_busy) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (queue.empty()) break;
+            }
+            if (!worked) std::this_thread::yield();
+        }
+    }
+};
+
+extern "C" {
+
+void tdes_server_config_default(tdes_server_config_t* cfg) {
+    if (cfg == nullptr) return;
+    cfg->budget_bytes = 8ull << 30;
+    cfg->slots = 4;
+    cfg->max_batch = 16384;
+    cfg->warps_per_cta = 4;
+    cfg->reserve_ctas_per_sm = 1;
+    cfg->ring_entries = 1u << 21;
+}
+
+int tdes_server_create(const tdes_keytable_t* kt, const tdes_server_config_t* cfg_in,
+                       tdes_server_t** out) {
+    if (kt == nullptr || out == nullptr) return sfail(TDES_EINVAL, "NULL argument");
+    *out = nullptr;
+    tdes_server_config_t cfg;
+    tdes_server_config_default(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.slots < 1 || cfg.slots > 64 || cfg.max_batch < 1 || cfg.warps_per_cta < 1 ||
+        cfg.warps_per_cta > 8 || cfg.ring_entries < 1024 || cfg.budget_bytes < 16)
+        return sfail(TDES_EINVAL, "bad server configuration");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return scuda(e, "cudaGetDevice");
+    if (dev != kt->device) return sfail(TDES_EINVAL, "key table lives on another device");
+    tdes_server* s = new (std::nothrow) tdes_server();
+    if (s == nullptr) return sfail(TDES_ENOMEM, "host allocation failed");
+    s->device = dev;
+    s->kt = kt;
+    s->cfg = cfg;
+    s->ring = std::vector<Completion>(cfg.ring_entries);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    e = tdes::prepare_batch_kernel(cfg.warps_per_cta, &s->dyn_smem, &s->ctas_fit);
+    s->slots.resize(cfg.slots);
+    for (Slot& sl : s->slots) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        int rc = scuda(e, "server set-up");
+        tdes_server_destroy(s);
+        return rc;
+    }
+    s->thread = std::thread([s] { s->dispatch_loop(); });
+    *out = s;
+    return TDES_OK;
+}
+
+int tdes_server_submit(tdes_server_t* s, const tdes_desc_t* req, uint64_t* ticket) {
+    if (s == nullptr || req == nullptr || ticket == nullptr)
+        return sfail(TDES_EINVAL, "NULL argument");
+    if (tdes::validate_desc(*req, s->kt->count) != TDES_OK)
+        return sfail(TDES_EINVAL, "invalid request descriptor");
+    const uint64_t cost = cost_of(*req);
+    if (cost > s->cfg.budget_bytes)
+        return sfail(TDES_EINVAL, "request of %llu bytes exceeds the admission budget",
+                     (unsigned long long)req->nbytes);
+    if (s->sticky_error.load()) return sfail(s->sticky_error.load(), "server stopped by an error");
+    std::lock_guard<std::mutex> lock(s->mu);
+    const uint64_t t = s->next_ticket++;
+    *ticket = t;
+    if (req->nbytes == 0) {
+        s->complete(t, TDES_OK, now_ns());
+        return TDES_OK;
+    }
+    s->queue.push_back({*req, t, cost});
+    return TDES_OK;
+}
+
+int tdes_server_poll(tdes_server_t* s, uint64_t ticket) {
+    if (s == nullptr || ticket == 0) return sfail(TDES_EINVAL, "bad ticket");
+    const Completion& c = s->ring[ticket % s->ring.size()];
+    const uint64_t seen = c.ticket.load(std::memory_order_acquire);
+    if (seen == ticket) return c.status;
+    if (seen > ticket) return TDES_OK;  // completed long ago; its record was reused
+    return 1;
+}
+
+int tdes_server_wait(tdes_server_t* s, uint64_t ticket, uint64_t timeout_ns) {
+    const int64_t until = now_ns() + (int64_t)std::min<uint64_t>(timeout_ns, INT64_MAX / 2);
+    for (;;) {
+        const int r = tdes_server_poll(s, ticket);
+        if (r != 1) return r;
+        if (now_ns() > until) return sfail(TDES_ETIMEDOUT, "ticket %llu still pending",
+                                           (unsigned long long)ticket);
+        std::this_thread::yield();
+    }
+}
+
+void tdes_server_destroy(tdes_server_t* s) {
+    if (s == nullptr) return;
+    s->stop.store(true, std::memory_order_release);
+    if (s->thread.joinable()) s->thread.join();
+    for (Slot& sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.dmem) cudaFree(sl.dmem);
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+    }
+    delete s;
+}
+
+// --------------------------------------------------------------- load test
+
+static uint64_t mix64(uint64_t z) {  // SplitMix64 finaliser (Steele, Lea, Flood 2014)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct Rng {
+    uint64_t state;
+    uint64_t next() { return mix64(state += 0x9E3779B97F4A7C15ull); }
+    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+static double percentile(std::vector<double>& v, double q) {
+    if (v.empty()) return 0.0;
+    const size_t k = std::min(v.size() - 1, (size_t)std::floor(q * (double)(v.size() - 1) + 0.5));
+    std::nth_element(v.begin(), v.begin() + k, v.end());
+    return v[k];
+}
+
+int tdes_serve_loadtest(tdes_server_t* s, const tdes_loadtest_config_t* c,
+                        tdes_loadtest_result_t* res) {
+    if (s == nullptr || c == nullptr || res == nullptr) return sfail(TDES_EINVAL, "NULL argument");
+    if (c->n_requests == 0 || c->n_keys == 0 || c->n_keys > s->kt->count ||
+        c->small_min < 8 || c->small_max < c->small_min || c->large_min < 8 ||
+        c->large_max < c->large_min || c->in_pool == nullptr || c->out_pool == nullptr ||
+        c->in_pool_bytes < c->large_max || c->out_pool_bytes < 2 * c->large_max)
+        return sfail(TDES_EINVAL, "bad load-test configuration");
+    const uint64_t n = c->n_requests;
+    Rng rng{c->seed};
+    std::vector<tdes_desc_t> reqs(n);
+    std::vector<uint8_t> small(n);
+    double total = 0.0;
+    const double lmin = std::log((double)c->large_min), lmax = std::log((double)c->large_max);
+    double psum = c->mode_probs[0] + c->mode_probs[1] + c->mode_probs[2];
+    if (!(psum > 0)) psum = 1.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t nb;
+        small[i] = rng.uniform() < c->small_frac;
+        if (small[i])
+            nb = c->small_min + (rng.next() % (c->small_max - c->small_min + 1));
+        else
+            nb = (uint64_t)std::exp(lmin + rng.uniform() * (lmax - lmin));
+        nb = std::max<uint64_t>(8, nb / 8 * 8);
+        const double u = rng.uniform() * psum;
+        const uint32_t mode = u < c->mode_probs[0] ? TDES_MODE_ECB_ENCRYPT
+                              : u < c->mode_probs[0] + c->mode_probs[1] ? TDES_MODE_CTR
+                                                                        : TDES_MODE_CBC_DECRYPT;
+        const uint64_t in_off = (rng.next() % (c->in_pool_bytes - nb + 1)) / 16 * 16;
+        tdes_desc_t& d = reqs[i];
+        d.mode = mode;
+        d.key_index = (uint32_t)(rng.next() % c->n_keys);
+        d.iv_or_ctr = mode == TDES_MODE_CTR ? (rng.next() & 0xFFFFFFFF00000000ull) : rng.next();
+        d.in = static_cast<const uint8_t*>(c->in_pool) + in_off;
+        d.out = nullptr;
+        d.nbytes = nb;
+        total += (double)nb;
+    }
+    // arrival times: Poisson at the offered byte rate, or all at once
+    std::vector<int64_t> arrive(n, 0);
+    const double rate = c->offered_gbps > 0 ? c->offered_gbps * 1e9 / (total / (double)n) : 0.0;
+    double t = 0.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (rate > 0) t += -std::log(1.0 - rng.uniform()) / rate;
+        arrive[i] = (int64_t)(t * 1e9);
+    }
+    // output regions: a ring over out_pool; a region is reused only after the
+    // request that held it has completed (waiting counts toward latency)
+    struct Held {
+        uint64_t ticket, lo, hi;
+    };
+    std::deque<Held> held;
+    uint64_t head = 0;
+    std::vector<uint64_t> tickets(n);
+    const int64_t t0 = now_ns() + 1000000;
+    const uint64_t batches0 = s->batches.load();
+    for (uint64_t i = 0; i < n; ++i) {
+        tdes_desc_t& d = reqs[i];
+        if (head + d.nbytes > c->out_pool_bytes) head = 0;
+        const uint64_t lo = head, hi = head + d.nbytes;
+        head = (hi + 15) / 16 * 16;
+        for (;;) {
+            // Regions are handed out in ring order, so a new one can only lap
+            // the oldest held regions: check those at the front.
+            while (!held.empty() && tdes_server_poll(s, held.front().ticket) != 1) held.pop_front();
+            bool overlap = false;
+            const size_t scan = std::min<size_t>(held.size(), 64);
+            for (size_t k = 0; k < scan && !overlap; ++k)
+                overlap = held[k].lo < hi && lo < held[k].hi &&
+                          tdes_server_poll(s, held[k].ticket) == 1;
+            if (!overlap) break;
+            std::this_thread::yield();
+        }
+        d.out = static_cast<uint8_t*>(c->out_pool) + lo;
+        while (now_ns() < t0 + arrive[i]) std::this_thread::yield();
+        const int rc = tdes_server_submit(s, &d, &tickets[i]);
+        if (rc != TDES_OK) return rc;
+        held.push_back({tickets[i], lo, hi});
+    }
+    for (uint64_t i = 0; i < n; ++i) {
+        const int rc = tdes_server_wait(s, tickets[i], 120ull * 1000000000ull);
+        if (rc != TDES_OK) return rc;
+    }
+    std::vector<double> lat(n), lat_s, lat_l;
+    int64_t last = t0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const Completion& cp = s->ring[tickets[i] % s->ring.size()];
+        if (cp.ticket.load(std::memory_order_acquire) != tickets[i])
+            return sfail(TDES_EINVAL, "completion ring too small for %llu requests",
+                         (unsigned long long)n);
+        lat[i] = (double)(cp.t_done_ns - (t0 + arrive[i])) * 1e-6;
+        last = std::max(last, cp.t_done_ns);
+        (small[i] ? lat_s : lat_l).push_back(lat[i]);
+    }
+    double sum = 0.0, mx = 0.0;
+    for (double v : lat) {
+        sum += v;
+        mx = std::max(mx, v);
+    }
+    res->requests = n;
+    res->bytes = (uint64_t)total;
+    res->duration_s = (double)(last - t0) * 1e-9;
+    res->gbps = total / std::max(1e-9, (double)(last - t0)) ;
+    res->offered_gbps = c->offered_gbps;
+    res->batches = s->batches.load() - batches0;
+    res->mean_ms = sum / (double)n;
+    res->max_ms = mx;
+    res->p50_ms = percentile(lat, 0.50);
+    res->p90_ms = percentile(lat, 0.90);
+    res->p99_ms = percentile(lat, 0.99);
+    res->p999_ms = percentile(lat, 0.999);
+    res->small_p50_ms = percentile(lat_s, 0.50);
+    res->small_p99_ms = percentile(lat_s, 0.99);
+    res->large_p50_ms = percentile(lat_l, 0.50);
+    res->large_p99_ms = percentile(lat_l, 0.99);
+    return TDES_OK;
+}
+
+}  // extern "C"

@@ -29,7 +29,8 @@ EXPORTED = (
     "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_cbc_decrypt_noalloc",
     "tdes_ecb_crypt_host", "tdes_keytable_create", "tdes_keytable_free", "tdes_batch_plan",
     "tdes_batch_configure", "tdes_batch_launch", "tdes_batch_launch_graph", "tdes_batch_info",
-    "tdes_batch_free",
+    "tdes_batch_free", "tdes_server_config_default", "tdes_server_create", "tdes_server_submit",
+    "tdes_server_poll", "tdes_server_wait", "tdes_server_destroy", "tdes_serve_loadtest",
     "tdes_sbox_gate_count", "tdes_strerror", "tdes_last_error",
 )
 
@@ -45,6 +46,32 @@ class Desc(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("key_index", ctypes.c_uint32),
                 ("iv_or_ctr", ctypes.c_uint64), ("in_ptr", ctypes.c_void_p),
                 ("out_ptr", ctypes.c_void_p), ("nbytes", ctypes.c_uint64)]
+
+
+class ServerConfig(ctypes.Structure):
+    """tdes_server_config_t"""
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int),
+                ("reserve_ctas_per_sm", ctypes.c_int), ("ring_entries", ctypes.c_uint32)]
+
+
+class LoadtestConfig(ctypes.Structure):
+    """tdes_loadtest_config_t"""
+    _fields_ = [("n_requests", ctypes.c_uint64), ("offered_gbps", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("small_frac", ctypes.c_double),
+                ("small_min", ctypes.c_uint32), ("small_max", ctypes.c_uint32),
+                ("large_min", ctypes.c_uint64), ("large_max", ctypes.c_uint64),
+                ("mode_probs", ctypes.c_double * 3), ("n_keys", ctypes.c_uint32),
+                ("in_pool", ctypes.c_void_p), ("in_pool_bytes", ctypes.c_uint64),
+                ("out_pool", ctypes.c_void_p), ("out_pool_bytes", ctypes.c_uint64)]
+
+
+class LoadtestResult(ctypes.Structure):
+    """tdes_loadtest_result_t"""
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "p50_ms", "p90_ms", "p99_ms", "p999_ms", "mean_ms", "max_ms", "small_p50_ms",
+        "small_p99_ms", "large_p50_ms", "large_p99_ms", "gbps", "offered_gbps", "duration_s")] + [
+        ("requests", ctypes.c_uint64), ("bytes", ctypes.c_uint64), ("batches", ctypes.c_uint64)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -92,6 +119,16 @@ def load(path: str = LIB_PATH):
     lib.tdes_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     lib.tdes_batch_free.argtypes = [vp]
     lib.tdes_batch_free.restype = None
+    lib.tdes_server_config_default.argtypes = [ctypes.POINTER(ServerConfig)]
+    lib.tdes_server_config_default.restype = None
+    lib.tdes_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.tdes_server_submit.argtypes = [vp, ctypes.POINTER(Desc), ctypes.POINTER(u64)]
+    lib.tdes_server_poll.argtypes = [vp, u64]
+    lib.tdes_server_wait.argtypes = [vp, u64, u64]
+    lib.tdes_server_destroy.argtypes = [vp]
+    lib.tdes_server_destroy.restype = None
+    lib.tdes_serve_loadtest.argtypes = [vp, ctypes.POINTER(LoadtestConfig),
+                                        ctypes.POINTER(LoadtestResult)]
     lib.tdes_sbox_gate_count.argtypes = []
     lib.tdes_strerror.argtypes = [ctypes.c_int]
     lib.tdes_strerror.restype = ctypes.c_char_p
@@ -307,6 +344,57 @@ class Batch:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns a tdes_server_t (continuous-batching request server)."""
+
+    def __init__(self, kt: KeyTable, **config):
+        lib = load()
+        cfg = ServerConfig()
+        lib.tdes_server_config_default(ctypes.byref(cfg))
+        for k, v in config.items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        _check(lib.tdes_server_create(kt.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self.kt = kt
+        self.config = {f: getattr(cfg, f) for f, _ in ServerConfig._fields_}
+
+    def submit(self, mode, key_index, iv_or_ctr, inp, out, nbytes=None) -> int:
+        n = _nbytes(inp) if nbytes is None else nbytes
+        d = Desc(mode, key_index, iv_or_ctr & (2**64 - 1), _ptr(inp), _ptr(out), n)
+        t = ctypes.c_uint64()
+        _check(load().tdes_server_submit(self.handle, ctypes.byref(d), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return int(load().tdes_server_poll(self.handle, ticket))
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        return int(load().tdes_server_wait(self.handle, ticket, int(timeout_s * 1e9)))
+
+    def loadtest(self, in_pool, out_pool, n_requests, offered_gbps, seed=1, small_frac=0.8,
+                 small=(64, 4096), large=(64 << 10, 16 << 20), mode_probs=(1, 1, 1),
+                 n_keys=None) -> dict:
+        c = LoadtestConfig(n_requests, offered_gbps, seed, small_frac, small[0], small[1],
+                           large[0], large[1], (ctypes.c_double * 3)(*mode_probs),
+                           self.kt.count if n_keys is None else n_keys, _ptr(in_pool),
+                           _nbytes(in_pool), _ptr(out_pool), _nbytes(out_pool))
+        r = LoadtestResult()
+        _check(load().tdes_serve_loadtest(self.handle, ctypes.byref(c), ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in LoadtestResult._fields_}
+
+    def close(self):
+        if self.handle:
+            load().tdes_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 

@@ -1,0 +1,113 @@
+"""The continuous-batching server through the C ABI: every request's result
+equals the oracle and the same request run alone; requests submitted while
+others run are batched separately and overlap; the HBM budget queues work
+instead of failing it; waits are bounded; the load generator reports sane
+latency statistics."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_10752_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(mode, keys, iv, data):
+    if mode == 0:
+        return oracle.tdes_ecb(keys, data)
+    if mode == 2:
+        return oracle.tdes_ctr(keys, iv >> 32, iv & 0xFFFFFFFF, data)
+    return oracle.tdes_cbc_decrypt(keys, iv, data)
+
+
+def _requests(seed, n, n_keys, big_every=0):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        if big_every and i % big_every == 0:
+            nb = int(rng.integers(8192, 2 * 8192 + 5))      # 64-128 KiB
+        elif rng.random() < 0.8:
+            nb = int(rng.integers(8, 513))                   # 64 B .. 4 KiB
+        else:
+            nb = int(rng.integers(513, 6000))
+        mode = int(rng.choice([0, 2, 3]))
+        iv = int(synth.words(seed, i, 1, synth.STREAM_IV)[0])
+        if mode == 2:
+            iv &= 0xFFFFFFFF00000000
+        reqs.append(dict(mode=mode, key=int(rng.integers(0, n_keys)), iv=iv,
+                         data=synth.random_bytes(seed * 7919 + i, 8 * nb)))
+    return reqs
+
+
+def _run(T, srv, reqs, keys):
+    ins = [torch.from_numpy(r["data"]).cuda() for r in reqs]
+    outs = [torch.empty_like(x) for x in ins]
+    torch.cuda.synchronize()
+    tickets = [srv.submit(r["mode"], r["key"], r["iv"], x, y) for r, x, y in zip(reqs, ins, outs)]
+    for t in tickets:
+        assert srv.wait(t, 60.0) == 0
+    return [y.cpu().numpy() for y in outs]
+
+
+def test_server_results_match_oracle_and_alone(cuda_lib):
+    T = cuda_lib
+    keys = synth.key_triples(21, 64)
+    kt = T.KeyTable(keys)
+    srv = T.Server(kt)
+    reqs = _requests(21, 400, 64, big_every=37)
+    got = _run(T, srv, reqs, keys)
+    for i, (r, g) in enumerate(zip(reqs, got)):
+        want = _oracle(r["mode"], keys[r["key"]].tobytes(), r["iv"], r["data"])
+        assert (g == want).all(), f"request {i}"
+    # the same requests one at a time (each alone in its batch) give the same bytes
+    for i in range(0, len(reqs), 23):
+        alone = _run(T, srv, [reqs[i]], keys)[0]
+        assert (alone == got[i]).all(), f"request {i} alone vs in the mix"
+    srv.close()
+
+
+def test_budget_queues_instead_of_failing(cuda_lib):
+    T = cuda_lib
+    keys = synth.key_triples(22, 8)
+    kt = T.KeyTable(keys)
+    srv = T.Server(kt, budget_bytes=256 << 10, slots=2)  # far below the total submitted
+    reqs = _requests(22, 120, 8, big_every=10)
+    got = _run(T, srv, reqs, keys)
+    for r, g in zip(reqs, got):
+        assert (g == _oracle(r["mode"], keys[r["key"]].tobytes(), r["iv"], r["data"])).all()
+    big = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(T.TdesError):  # larger than the whole budget
+        srv.submit(0, 0, 0, big, torch.empty_like(big))
+    srv.close()
+
+
+def test_bounded_wait_and_bad_requests(cuda_lib):
+    T = cuda_lib
+    kt = T.KeyTable(synth.key_triples(23, 2))
+    srv = T.Server(kt)
+    # a ticket that was never issued stays pending: the wait gives up
+    assert srv.wait(10 ** 9, 0.01) == T.TDES_ETIMEDOUT
+    buf = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    with pytest.raises(T.TdesError):
+        srv.submit(0, 5, 0, buf, torch.empty_like(buf))        # key index out of range
+    with pytest.raises(T.TdesError):
+        srv.submit(9, 0, 0, buf, torch.empty_like(buf))        # bad mode
+    t = srv.submit(0, 0, 0, buf[:0], buf[:0])                  # empty request completes
+    assert srv.poll(t) == 0
+    srv.close()
+
+
+def test_loadtest_reports(cuda_lib):
+    T = cuda_lib
+    kt = T.KeyTable(synth.key_triples(24, 256))
+    srv = T.Server(kt)
+    pool = torch.from_numpy(synth.random_bytes(24, 64 << 20)).cuda()
+    out = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    r = srv.loadtest(pool, out, 3000, 20.0, large=(64 << 10, 4 << 20))
+    assert r["requests"] == 3000 and r["batches"] >= 1
+    assert 0 < r["p50_ms"] <= r["p99_ms"] <= r["max_ms"]
+    assert r["gbps"] > 0
+    sat = srv.loadtest(pool, out, 3000, 0.0, large=(64 << 10, 4 << 20))
+    assert sat["gbps"] > 0
+    srv.close()
