@@ -175,14 +175,14 @@ def profiled_traffic():
 
 def probe_alu_peak():
     import ctypes
-    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2007_10752_gb300", "libtdes_probe.so"))
-    lib.tdes_probe_lop3_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2007_10752_gb300", "libtdes_tools.so"))
+    lib.tdes_tools_lop3_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_float)]
     best = 0.0
     for ctas in (4, 8):
         ops, ms = ctypes.c_double(), ctypes.c_float()
-        rc = lib.tdes_probe_lop3_rate(ctas, 256, 4000, ctypes.byref(ops), ctypes.byref(ms))
+        rc = lib.tdes_tools_lop3_rate(ctas, 256, 4000, ctypes.byref(ops), ctypes.byref(ms))
         if rc == 0:
             best = max(best, ops.value)
     return best
@@ -254,10 +254,13 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = world * NBYTES / (ms_per_step * 1e-3) / 1e9
 
-    # parity spot check of the timed output (a few windows against the oracle)
-    import oracle
-    yh = y[: 8 * 1024].cpu().numpy()
-    assert (yh == oracle.tdes_ecb(keys, host[: 8 * 1024])).all(), "bench output differs"
+    # the timed output decrypts back to the input (parity with the oracle is
+    # the test suite's job)
+    z = torch.empty_like(y)
+    tdes.tdes_ecb_decrypt(ks, y, z)
+    torch.cuda.synchronize()
+    assert torch.equal(z, x), "ECB decrypt(encrypt(x)) != x"
+    del z
 
     # ---- other modes of the same workload, and the 1 MiB single launch
     def time_fn(fn, n):
@@ -280,6 +283,9 @@ def run_ours(args):
 
     # ---- batched: 4096 messages with their own keys and modes, one launch
     batched = None if args.no_batch else run_batched(torch, tdes, synth, stream, value)
+
+    # ---- large streaming: 32 GiB in place, CTR stream + 2^20 small messages
+    streaming = None if args.no_stream else run_streaming(torch, tdes, synth, stream)
 
     # ---- serving: Poisson arrivals at fractions of the measured peak
     serving = None if args.no_serve else run_serving(torch, tdes, synth, x)
@@ -336,7 +342,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                      "unit": "Tops/s", "frac": round(achieved / peak, 4) if peak else None,
                      "traffic": traffic,
-                     "peak_source": "live LOP3 probe (libtdes_probe.so) on this GPU",
+                     "peak_source": "live LOP3 probe (libtdes_tools.so) on this GPU",
                      "alg_ops_per_32_blocks": alg_ops_per_32_blocks(),
                      "hbm_achieved_gbs": round(hbm_gbs, 1),
                      "hbm_peak_gbs": pk.get("hbm_gbs"),
@@ -347,6 +353,7 @@ def run_ours(args):
         "clocks": clocks,
         "batched": batched,
         "serving": serving,
+        "large_streaming": streaming,
         "extra": {"kernel_ms_per_launch": round(per_launch_ms, 4),
                   "ecb_decrypt_gbs": round(NBYTES / (dec_ms * 1e-3) / 1e9, 3),
                   "ctr_gbs": round(NBYTES / (ctr_ms * 1e-3) / 1e9, 3),
@@ -368,25 +375,6 @@ BATCH_WORKLOAD = ("4096 messages, lengths log-uniform 64 B..4 MiB (multiples of 
                   "replayed as a CUDA graph")
 
 
-def build_config3(torch, tdes, synth, seed=3, n=4096, modes_probs=(0.4, 0.3, 0.2, 0.1)):
-    lens = synth.log_uniform_lengths(seed, n, 64, 4 << 20)
-    modes = np.array([0, 2, 3, 4])[synth.categorical(seed, n, list(modes_probs),
-                                                     synth.STREAM_MODE)]
-    keys = synth.key_triples(seed, n)
-    ivs = synth.u64s(seed, n, synth.STREAM_IV)
-    offs = np.concatenate([[0], np.cumsum((lens + 15) // 16 * 16)])[:-1]
-    total = int(offs[-1] + lens[-1] + 16)
-    src = torch.from_numpy(synth.random_bytes(seed, (total + 7) // 8 * 8)).cuda()
-    dst = torch.empty_like(src)
-    kt = tdes.KeyTable(keys)
-    ents = []
-    for i in range(n):
-        iv = int(ivs[i]) & (0xFFFFFFFF00000000 if modes[i] == 2 else 0xFFFFFFFFFFFFFFFF)
-        ents.append((int(modes[i]), i, iv, src.data_ptr() + int(offs[i]),
-                     dst.data_ptr() + int(offs[i]), int(lens[i])))
-    return src, dst, kt, ents, lens, modes
-
-
 def time_graph(torch, batch, stream, reps):
     batch.launch_graph(stream)  # capture + warm-up
     torch.cuda.synchronize()
@@ -401,10 +389,11 @@ def time_graph(torch, batch, stream, reps):
 
 def run_batched(torch, tdes, synth, stream, ecb_gbs):
     """Config-3 batch: whole-batch makespan, and the parallel modes alone."""
-    src, dst, kt, ents, lens, modes = build_config3(torch, tdes, synth)
+    from paper_2007_10752_gb300.workloads import build_batched
+    src, dst, kt, ents, lens, modes = build_batched(torch, tdes)
     total = int(lens.sum())
-    par = [e for e in ents if e[0] != 4]
-    par_bytes = sum(e[5] for e in par)
+    par = ents[ents["mode"] != 4]
+    par_bytes = int(par["nbytes"].sum())
     # autotune the launch shape on the parallel-mode part (the throughput part)
     bpar = tdes.Batch(kt, par)
     best = None
@@ -418,9 +407,9 @@ def run_batched(torch, tdes, synth, stream, ecb_gbs):
     ball = tdes.Batch(kt, ents)
     ball.configure(*best[0])
     all_ms = time_graph(torch, ball, stream, 2)
-    cbc = [e for e in ents if e[0] == 4]
-    longest = max((e[5] for e in cbc), default=0)
-    bc = tdes.Batch(kt, [max(cbc, key=lambda e: e[5])]) if cbc else None
+    cbc = ents[ents["mode"] == 4]
+    longest = int(cbc["nbytes"].max()) if len(cbc) else 0
+    bc = tdes.Batch(kt, cbc[[int(np.argmax(cbc["nbytes"]))]]) if len(cbc) else None
     chain_ms = time_graph(torch, bc, stream, 2) if bc else 0.0
     par_gbs = par_bytes / (par_ms * 1e-3) / 1e9
     info = ball.info()
@@ -438,6 +427,41 @@ def run_batched(torch, tdes, synth, stream, ecb_gbs):
         "tiles": info["n_tiles"], "small_items": info["n_small_items"],
         "cbc_encrypt_messages": info["n_cbc_enc_messages"],
     }
+
+
+# ------------------------------------------------------- large streaming
+STREAM_WORKLOAD = ("32 GiB seeded buffer in place: [0, 16 GiB) one single-key CTR stream, then "
+                   "2^20 messages of 64 B under 65536 seeded key triples (ECB 40% / CTR 30% / "
+                   "CBC-decrypt 20% / CBC-encrypt 10%); one persistent launch (CUDA graph)")
+
+
+def run_streaming(torch, tdes, synth, stream, reps=5):
+    from paper_2007_10752_gb300.workloads import STREAM_BYTES, STREAM_N_SMALL as N_SMALL
+    from paper_2007_10752_gb300.workloads import build_streaming
+    buf, kt, d, keys, nonce = build_streaming(torch, tdes)
+    b = tdes.Batch(kt, d)
+    ms = time_graph(torch, b, stream, reps)
+    processed = STREAM_BYTES + 64 * N_SMALL
+    info = b.info()
+    # the CTR stream alone through the single-key entry point, same bytes
+    ks = tdes.KeySchedule.from_triple(keys[-1].tobytes())
+    x = buf[:STREAM_BYTES]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tdes.tdes_ctr_crypt(ks, nonce, 0, x, x)
+    e0.record(stream)
+    for _ in range(reps):
+        tdes.tdes_ctr_crypt(ks, nonce, 0, x, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctr_ms = e0.elapsed_time(e1) / reps
+    del buf, x
+    torch.cuda.empty_cache()
+    return {"workload": STREAM_WORKLOAD, "processed_bytes": processed,
+            "ms": round(ms, 3), "gbps": round(processed / (ms * 1e-3) / 1e9, 3),
+            "ctr_stream_alone_ms": round(ctr_ms, 3),
+            "ctr_stream_alone_gbps": round(STREAM_BYTES / (ctr_ms * 1e-3) / 1e9, 3),
+            "tiles": info["n_tiles"], "small_items": info["n_small_items"],
+            "cbc_encrypt_messages": info["n_cbc_enc_messages"]}
 
 
 # ---------------------------------------------------------------- serving
@@ -524,6 +548,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-stream", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -20,9 +20,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtdes_gb300.so")
-PROBE_LIB = os.path.join(HERE, "libtdes_probe.so")  # benchmark's LOP3-rate probe, not the cipher
+TOOLS_LIB = os.path.join(HERE, "libtdes_tools.so")  # benchmark/test tools, not the cipher
 SOURCES = ["tdes_api.cu", "tdes_kernels.cu", "tdes_noalloc.cu", "tdes_batch.cu", "tdes_serve.cu"]
-PROBE_SOURCES = ["tdes_probe.cu"]
+TOOLS_SOURCES = ["tdes_tools.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]
@@ -54,11 +54,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.path.pop(0)
         newest = max(os.path.getmtime(f) for f in _inputs())
         if (not force and all(os.path.exists(x) and os.path.getmtime(x) >= newest
-                                  for x in (LIB, PROBE_LIB))):
+                                  for x in (LIB, TOOLS_LIB))):
             return LIB
         os.makedirs(BUILD, exist_ok=True)
         objs, procs = [], []
-        for src in SOURCES + PROBE_SOURCES:
+        for src in SOURCES + TOOLS_SOURCES:
             obj = os.path.join(BUILD, src.replace(".cu", ".o"))
             objs.append(obj)
             cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError(f"nvcc failed on {src}:\n{out}")
         with open(os.path.join(BUILD, "ptxas.txt"), "w") as f:
             f.write("\n".join(logs))
-        for lib, srcs in ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES)):
+        for lib, srcs in ((LIB, SOURCES), (TOOLS_LIB, TOOLS_SOURCES)):
             tmp = lib + f".tmp{os.getpid()}"
             lib_objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in srcs]
             subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *lib_objs])

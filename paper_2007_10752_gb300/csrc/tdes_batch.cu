@@ -266,10 +266,15 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
         const BatchMsg m = p.msgs[p.c_list[idx]];
         uint8_t* ch = warp_smem + TDES_SUBKEY_WORDS * lane;
         stage_chunks(ch, p.keychunks + (uint64_t)m.key * kPerKeyChunks);
+        // the next block is loaded one iteration ahead (its latency hides
+        // behind the current block's rounds)
         uint64_t prev = m.iv;
+        uint64_t next = load_be(m.in, 0);
         for (uint64_t i = 0; i < m.nblocks; ++i) {
-            prev = tdes_block_scalar_nib(load_be(m.in, i) ^ prev, st.sp,
-                                         reinterpret_cast<const uint32_t*>(ch), st.ipn, st.fpn);
+            const uint64_t x = next ^ prev;
+            if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
+            prev = tdes_block_scalar_nib(x, st.sp, reinterpret_cast<const uint32_t*>(ch), st.ipn,
+                                         st.fpn);
             store_be(m.out, i, prev);
         }
     }

@@ -307,9 +307,13 @@ __global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64
     if (threadIdx.x != 0) return;
     const uint64_t* p = reinterpret_cast<const uint64_t*>(in);
     uint64_t* q = reinterpret_cast<uint64_t*>(out);
+    // The next plaintext block is loaded one iteration ahead so its memory
+    // latency hides behind the 48 rounds of the current one.
     uint64_t prev = iv;
+    uint64_t next = p[0];
     for (uint64_t i = 0; i < nblocks; ++i) {
-        const uint64_t x = bswap64(p[i]) ^ prev;
+        const uint64_t x = bswap64(next) ^ prev;
+        if (i + 1 < nblocks) next = p[i + 1];
         prev = tdes_block_scalar_nib(x, sp, keys, ipn, fpn);
         q[i] = bswap64(prev);
     }

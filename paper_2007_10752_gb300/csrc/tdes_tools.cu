@@ -1,7 +1,11 @@
-// tdes_probe.cu -- measurement probe for the benchmark (not part of the cipher
-// library): the sustained throughput of 32-bit LOP3 instructions, which is the
-// peak the bitsliced kernels are bound by.
+// tdes_tools.cu -- benchmark and test tools, not part of the cipher library:
+//   * a probe of the sustained throughput of 32-bit LOP3 instructions, the
+//     peak the bitsliced kernels are bound by;
+//   * a device-side fill with the same counter-based SplitMix64 words as the
+//     host input generator (paper_2007_10752_gb300/synth.py), for inputs too
+//     large to generate on the host and copy.
 //
+// LOP3 probe:
 // Each thread keeps 8 accumulators and updates each with a 3-input LOP3 of
 // three different accumulators, so no two instructions can be merged and
 // there are 8 independent chains per thread.  Launched over every SM with
@@ -36,11 +40,40 @@ __global__ void lop3_rate_kernel(uint32_t* out, int iters, uint32_t seed) {
     if (x == 0x12345678u) out[blockIdx.x * blockDim.x + threadIdx.x] = x;  // keeps the work live
 }
 
+// Word i of a SplitMix64 stream seeded s is mix(s + (i + 1) * gamma)
+// (Steele, Lea and Flood, OOPSLA 2014), stored little-endian.
+__global__ void splitmix64_fill_kernel(uint64_t* __restrict__ out, uint64_t nwords, uint64_t seed,
+                                       uint64_t first) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += stride) {
+        uint64_t z = seed + (first + i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        out[i] = z ^ (z >> 31);
+    }
+}
+
 extern "C" {
+
+// Fills dst (8-byte aligned, nwords words) with words first .. first+nwords-1
+// of the SplitMix64 stream seeded `seed`, on `stream`.  Returns 0 or a CUDA error.
+int tdes_tools_fill_splitmix64(void* dst, uint64_t nwords, uint64_t seed, uint64_t first,
+                               void* stream) {
+    if (nwords == 0) return 0;
+    if (dst == nullptr || (reinterpret_cast<uintptr_t>(dst) & 7u)) return -1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (nwords + 255) / 256;
+    const unsigned grid = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
+    splitmix64_fill_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<uint64_t*>(dst), nwords, seed, first);
+    return (int)cudaGetLastError();
+}
 
 // Runs the probe on the current device and stream 0; returns 0 and the
 // measured LOP3 lane-operations per second in *ops_per_s, or a CUDA error.
-int tdes_probe_lop3_rate(int ctas_per_sm, int threads, int iters, double* ops_per_s,
+int tdes_tools_lop3_rate(int ctas_per_sm, int threads, int iters, double* ops_per_s,
                          float* ms_out) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;

@@ -24,7 +24,8 @@
  * accepts either polarity and the caller records it.  Random restarts over
  * output orders and split variables keep the smallest circuit found.
  *
- * Usage: sbox_search T0 T1 T2 T3 iterations seed [lut2_limit [wide_depth [variant_depth]]]
+ * Usage: sbox_search T0 T1 T2 T3 iterations seed [lut2_limit [wide_depth [variant_depth
+ *        [pair_tries]]]]
  *   T0..T3: hex truth tables of the four outputs (first output bit first).
  * Prints the best circuit: "gates N", then one line per gate
  * "g <id> <in0> <in1> <in2> <lut>" (ids 0..5 are the inputs b1..b6), then
@@ -191,6 +192,90 @@ static int try_lut2(Circ *C, uint64_t T, uint64_t M) {
 
 static int build(Circ *C, uint64_t T, uint64_t M, unsigned avail, int depth);
 
+static int pair_tries = 0; /* step 5 below: how many of the best gate pairs to try (0 = off) */
+
+/* Step 5: T = LUT(g1, g2, B) for two existing gates g1, g2 and one new
+ * sub-circuit B.  Inside each of the four classes of (g1, g2) the LUT is a
+ * function of B alone: a constant where T is constant on the class (B is
+ * free there), else B or ~B (B must equal T or ~T there).  So B's care set is
+ * the union of the classes where T is mixed; pairs that leave the fewest care
+ * bits are tried, with every polarity choice per mixed class. */
+static int pair_decomp(Circ *C, uint64_t T, uint64_t M, unsigned avail, int depth) {
+    int n = C->n;
+    enum { K = 6 };
+    int best_a[K], best_b[K], cnt = 0;
+    int best_c[K];
+    for (int a = 0; a < n; ++a)
+        for (int b = a + 1; b < n; ++b) {
+            uint64_t care = 0;
+            for (int q = 0; q < 4; ++q) {
+                uint64_t cls = M & sel(C->g[a].tt, q & 2) & sel(C->g[b].tt, q & 1);
+                uint64_t on = cls & T;
+                if (on && on != cls) care |= cls;
+            }
+            int c = __builtin_popcountll(care);
+            if (c == 0 || care == M) continue; /* no progress, or a plain LUT */
+            /* keep the K smallest (random tie-break by replacing with prob 1/2) */
+            int worst = -1;
+            if (cnt < K) {
+                worst = cnt++;
+            } else {
+                for (int i = 0; i < K; ++i)
+                    if (worst < 0 || best_c[i] > best_c[worst]) worst = i;
+                if (best_c[worst] < c || (best_c[worst] == c && (rnd() & 1))) worst = -1;
+            }
+            if (worst >= 0) {
+                best_a[worst] = a;
+                best_b[worst] = b;
+                best_c[worst] = c;
+            }
+        }
+    Circ best;
+    int best_id = -1;
+    int tries = cnt < pair_tries ? cnt : pair_tries;
+    for (int t = 0; t < tries; ++t) {
+        /* the t-th smallest */
+        int pick = -1;
+        for (int i = 0; i < cnt; ++i)
+            if (best_c[i] >= 0 && (pick < 0 || best_c[i] < best_c[pick])) pick = i;
+        if (pick < 0) break;
+        int a = best_a[pick], b = best_b[pick];
+        best_c[pick] = -1 - best_c[pick]; /* mark used */
+        uint64_t quad[4];
+        int mixed[4], nm = 0;
+        for (int q = 0; q < 4; ++q) {
+            quad[q] = M & sel(C->g[a].tt, q & 2) & sel(C->g[b].tt, q & 1);
+            uint64_t on = quad[q] & T;
+            if (on && on != quad[q]) mixed[nm++] = q;
+        }
+        for (int pol = 0; pol < (1 << (nm - 1)); ++pol) {
+            uint64_t bt = 0, bm = 0;
+            for (int m = 0; m < nm; ++m) {
+                int q = mixed[m];
+                int pq = m == 0 ? 0 : (pol >> (m - 1)) & 1;
+                bt |= (pq ? ~T : T) & quad[q];
+                bm |= quad[q];
+            }
+            Circ W = *C;
+            int B = build(&W, bt, bm, avail, depth + 1);
+            if (B < 0) continue;
+            uint8_t lut;
+            if (!fit3(W.g[a].tt, W.g[b].tt, W.g[B].tt, T, M, &lut)) continue;
+            int id = add_gate(&W, a, b, B, lut);
+            if (id < 0) continue;
+            if (best_id < 0 || W.n < best.n) {
+                best = W;
+                best_id = id;
+            }
+        }
+    }
+    for (int i = 0; i < cnt; ++i)
+        if (best_c[i] < 0) best_c[i] = -1 - best_c[i];
+    if (best_id < 0) return -1;
+    *C = best;
+    return best_id;
+}
+
 /* Split on a random available variable; try the join variants and keep the
  * cheapest.  Returns the gate realising T on M, or -1. */
 static int split(Circ *C, uint64_t T, uint64_t M, unsigned avail, int depth) {
@@ -275,6 +360,14 @@ static int split(Circ *C, uint64_t T, uint64_t M, unsigned avail, int depth) {
             }
         }
     }
+    if (pair_tries > 0 && depth < wide_depth + 2) {
+        Circ W = *C;
+        int id = pair_decomp(&W, T, M, avail, depth);
+        if (id >= 0 && (best_id < 0 || W.n < best.n)) {
+            best = W;
+            best_id = id;
+        }
+    }
     if (best_id < 0) return -1;
     *C = best;
     return best_id;
@@ -319,6 +412,7 @@ int main(int argc, char **argv) {
     lut2_limit = argc > 7 ? atoi(argv[7]) : 0;
     wide_depth = argc > 8 ? atoi(argv[8]) : 1;
     variant_depth = argc > 9 ? atoi(argv[9]) : 99;
+    pair_tries = argc > 10 ? atoi(argv[10]) : 0;
 
     Circ best;
     int have = 0;

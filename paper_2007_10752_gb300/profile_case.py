@@ -6,6 +6,7 @@ few hundred MB on the device) and exits.  Used as the target of ncu
 captures, whose commands are recorded beside their summaries in profiles/.
 
   python -m paper_2007_10752_gb300.profile_case --kernel ecb --mib 256 --launches 3
+  python -m paper_2007_10752_gb300.profile_case --kernel batch --launches 3
 """
 from __future__ import annotations
 
@@ -20,7 +21,8 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec"], default="ecb")
+    ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec", "batch"],
+                    default="ecb")
     ap.add_argument("--mib", type=int, default=256)
     ap.add_argument("--launches", type=int, default=3)
     args = ap.parse_args()
@@ -30,6 +32,18 @@ def main():
     from paper_2007_10752_gb300 import build, synth, tdes
     build.build()
     torch.cuda.set_device(0)
+    if args.kernel == "batch":
+        # the parallel-mode messages of the 4096-message batched workload
+        import numpy as np
+
+        from paper_2007_10752_gb300.workloads import build_batched
+        src, dst, kt, d, lens, modes = build_batched(torch, tdes)
+        b = tdes.Batch(kt, d[d["mode"] != 4])
+        for _ in range(args.launches):
+            b.launch()
+        torch.cuda.synchronize()
+        print(f"batch: {args.launches} launches of {int(np.sum(d['mode'] != 4))} messages done")
+        return
     n = args.mib << 20
     keys = synth.key_triple(2)
     x = torch.from_numpy(synth.random_bytes(2, n)).cuda()

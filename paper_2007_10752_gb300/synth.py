@@ -152,3 +152,25 @@ def categorical(seed: int, count: int, probs, stream: int, first: int = 0) -> np
     cdf = np.cumsum(p / p.sum())
     u = uniform01(seed, count, stream, first)
     return np.minimum(np.searchsorted(cdf, u, side="right"), len(p) - 1).astype(np.int64)
+
+
+def fill_device(tensor, seed: int, stream: int = STREAM_PAYLOAD, start_byte: int = 0) -> None:
+    """Fill a CUDA uint8 tensor with ``random_bytes(seed, tensor.numel(), stream, start_byte)``.
+
+    Runs the same SplitMix64 words on the GPU (libtdes_tools.so) for inputs
+    too large to draw on the host; asynchronous on the current torch stream.
+    """
+    import ctypes
+    import os
+
+    import torch
+    n = tensor.numel()
+    if n % 8 or start_byte % 8:
+        raise ValueError("payload streams are drawn in whole 8-byte words")
+    lib = ctypes.CDLL(os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtdes_tools.so"))
+    lib.tdes_tools_fill_splitmix64.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_uint64, ctypes.c_void_p]
+    rc = lib.tdes_tools_fill_splitmix64(tensor.data_ptr(), n // 8, substream(seed, stream),
+                                        start_byte // 8, torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise RuntimeError(f"device fill failed: {rc}")

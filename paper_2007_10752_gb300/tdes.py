@@ -306,16 +306,29 @@ def make_descs(entries):
     return arr, len(entries)
 
 
+DESC_DTYPE = np.dtype([("mode", "<u4"), ("key_index", "<u4"), ("iv_or_ctr", "<u8"),
+                       ("in_ptr", "<u8"), ("out_ptr", "<u8"), ("nbytes", "<u8")])
+
+
 class Batch:
-    """Owns a tdes_batch_t planned from descriptors (see include/tdes.h)."""
+    """Owns a tdes_batch_t planned from descriptors (see include/tdes.h).
+
+    ``entries`` is an iterable of (mode, key_index, iv_or_ctr, in, out, nbytes)
+    or a numpy array of DESC_DTYPE (for very large batches).
+    """
 
     def __init__(self, kt: KeyTable, entries):
-        descs, n = make_descs(entries)
+        if isinstance(entries, np.ndarray):
+            descs = np.ascontiguousarray(entries, dtype=DESC_DTYPE)
+            n, addr = descs.shape[0], descs.ctypes.data
+        else:
+            descs, n = make_descs(entries)
+            addr = ctypes.addressof(descs)
         self._descs = descs
         self.status = np.zeros(max(1, n), dtype=np.int32)
         h = ctypes.c_void_p()
-        _check(load().tdes_batch_plan(kt.handle, ctypes.addressof(descs), n,
-                                      self.status.ctypes.data, ctypes.byref(h)))
+        _check(load().tdes_batch_plan(kt.handle, addr, n, self.status.ctypes.data,
+                                      ctypes.byref(h)))
         self.status = self.status[:n]
         self.handle = h.value
         self.kt = kt

@@ -1,0 +1,73 @@
+"""Seeded synthetic workloads of the benchmark and the tests, as device
+buffers plus batch descriptors (no cipher arithmetic here).
+
+* ``build_batched``: 4096 messages, lengths log-uniform 64 B .. 4 MiB
+  (multiples of 8), own key triple each, modes ECB 40% / CTR 30% /
+  CBC-decrypt 20% / CBC-encrypt 10%, seeded IVs; out of place.
+* ``build_streaming``: one 32 GiB buffer processed in place: a 16 GiB
+  single-key CTR stream at offset 0, then 2^20 messages of 64 bytes under
+  65536 key triples with the same mode mix.  The payload is drawn on the
+  device with the same SplitMix64 words as ``synth.random_bytes``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import synth
+
+BATCH_SEED = 3
+STREAM_SEED = 5
+STREAM_TOTAL = 32 << 30
+STREAM_BYTES = 16 << 30
+STREAM_N_SMALL = 1 << 20
+STREAM_N_KEYS = 65536
+MODE_MIX = (0.4, 0.3, 0.2, 0.1)  # ECB encrypt, CTR, CBC-decrypt, CBC-encrypt
+
+
+def _modes(seed, n):
+    return np.array([0, 2, 3, 4], dtype=np.uint32)[
+        synth.categorical(seed, n, list(MODE_MIX), synth.STREAM_MODE)]
+
+
+def build_batched(torch, tdes, seed=BATCH_SEED, n=4096):
+    """Returns (src, dst, key table, descriptor array, lengths, modes)."""
+    lens = synth.log_uniform_lengths(seed, n, 64, 4 << 20)
+    modes = _modes(seed, n)
+    keys = synth.key_triples(seed, n)
+    ivs = synth.u64s(seed, n, synth.STREAM_IV)
+    offs = np.concatenate([[0], np.cumsum((lens + 15) // 16 * 16)])[:-1].astype(np.uint64)
+    total = int(offs[-1]) + int(lens[-1]) + 16
+    src = torch.from_numpy(synth.random_bytes(seed, (total + 7) // 8 * 8)).cuda()
+    dst = torch.empty_like(src)
+    d = np.zeros(n, dtype=tdes.DESC_DTYPE)
+    d["mode"] = modes
+    d["key_index"] = np.arange(n, dtype=np.uint32)
+    d["iv_or_ctr"] = np.where(modes == 2, ivs & np.uint64(0xFFFFFFFF00000000), ivs)
+    d["in_ptr"] = np.uint64(src.data_ptr()) + offs
+    d["out_ptr"] = np.uint64(dst.data_ptr()) + offs
+    d["nbytes"] = lens.astype(np.uint64)
+    return src, dst, tdes.KeyTable(keys), d, lens, modes
+
+
+def build_streaming(torch, tdes, seed=STREAM_SEED, total=STREAM_TOTAL, stream_bytes=STREAM_BYTES,
+                    n_small=STREAM_N_SMALL, n_keys=STREAM_N_KEYS):
+    """Returns (buffer, key table, descriptor array, keys, CTR nonce)."""
+    buf = torch.empty(total, dtype=torch.uint8, device="cuda")
+    synth.fill_device(buf, seed)
+    keys = synth.key_triples(seed, n_keys + 1)  # the last triple keys the CTR stream
+    kt = tdes.KeyTable(keys)
+    base = buf.data_ptr()
+    d = np.zeros(n_small + 1, dtype=tdes.DESC_DTYPE)
+    nonce = synth.nonce32(seed)
+    d[0] = (tdes.MODE_CTR, n_keys, nonce << 32, base, base, stream_bytes)
+    offs = stream_bytes + 64 * np.arange(n_small, dtype=np.uint64)
+    modes = _modes(seed, n_small)
+    ivs = synth.u64s(seed, n_small, synth.STREAM_IV)
+    d["mode"][1:] = modes
+    d["key_index"][1:] = (synth.u64s(seed, n_small, synth.STREAM_KEYPICK)
+                          % np.uint64(n_keys)).astype(np.uint32)
+    d["iv_or_ctr"][1:] = np.where(modes == 2, ivs & np.uint64(0xFFFFFFFF00000000), ivs)
+    d["in_ptr"][1:] = np.uint64(base) + offs
+    d["out_ptr"][1:] = np.uint64(base) + offs
+    d["nbytes"][1:] = 64
+    return buf, kt, d, keys, nonce
