@@ -78,6 +78,12 @@ struct SharedTables {
     uint64_t fpn[16 * 16];
 };
 
+// Shared memory of the batch kernel, at namespace scope so that the scalar
+// item functions (real calls, see below) address it as shared memory rather
+// than through generic pointers.
+__shared__ __align__(16) SharedTables g_st;
+extern __shared__ __align__(16) uint8_t g_dyn[];  // kWarpSmemBytes per warp
+
 __device__ __forceinline__ int dir_of(uint32_t mode) {
     return (mode == TDES_MODE_ECB_DECRYPT || mode == TDES_MODE_CBC_DECRYPT) ? 1 : 0;
 }
@@ -207,9 +213,10 @@ __device__ __forceinline__ void stage_chunks(uint8_t* dst, const uint8_t* __rest
 // force spills there; as calls they have their own allocation.
 
 // S item: whole small messages, one block per lane.
-__device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
-                                               uint8_t* warp_smem, const SharedTables& st,
+__device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item, uint32_t warp,
                                                uint32_t lane) {
+    uint8_t* warp_smem = g_dyn + (size_t)warp * kWarpSmemBytes;
+    const SharedTables& st = g_st;
     // find this lane's (message, block): walk the item's messages in order
     uint32_t msg = 0xFFFFFFFFu;
     uint64_t blk = 0;
@@ -252,8 +259,9 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
 // C item: CBC-encryption chains, one per lane.  The first n_c_solo items
 // (the longest chains) hold one chain each; the rest hold up to 32.
 __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t item,
-                                                uint8_t* warp_smem, const SharedTables& st,
-                                                uint32_t lane) {
+                                                uint32_t warp, uint32_t lane) {
+    uint8_t* warp_smem = g_dyn + (size_t)warp * kWarpSmemBytes;
+    const SharedTables& st = g_st;
     uint32_t idx, end;
     if (item < p.n_c_solo) {
         idx = lane == 0 ? item : p.n_c;
@@ -282,55 +290,57 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
 }
 
 __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
-    extern __shared__ __align__(16) uint8_t dyn_smem[];
-    __shared__ __align__(16) SharedTables st;
-    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) st.sp[i] = (&kBatchSP[0][0])[i];
+    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) g_st.sp[i] = (&kBatchSP[0][0])[i];
     for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) {
-        st.ipn[i] = (&kBatchIPN[0][0])[i];
-        st.fpn[i] = (&kBatchFPN[0][0])[i];
+        g_st.ipn[i] = (&kBatchIPN[0][0])[i];
+        g_st.fpn[i] = (&kBatchFPN[0][0])[i];
     }
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint8_t* wsm = dyn_smem + (size_t)warp * kWarpSmemBytes;
-    uint32_t* wtab = reinterpret_cast<uint32_t*>(wsm);
-    uint64_t staged = ~0ull;  // (key << 1 | dir) of the table in wtab
-    const uint64_t total = (uint64_t)p.n_c_items + p.n_b_tiles + p.n_s_items;
+    uint32_t* wtab = reinterpret_cast<uint32_t*>(g_dyn + (size_t)warp * kWarpSmemBytes);
+    uint32_t staged = ~0u;  // (key << 1 | dir) of the table in wtab
+    const uint64_t total = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(p.counter, 1ull);
         item = __shfl_sync(0xFFFFFFFFu, item, 0);
         if (item >= total) break;
         if (item < p.n_c_items) {
-            batch_cbc_enc_item(p, (uint32_t)item, wsm, st, lane);
-            staged = ~0ull;
+            batch_cbc_enc_item(p, (uint32_t)item, warp, lane);
+            staged = ~0u;
             continue;
         }
         item -= p.n_c_items;
-        if (item < p.n_b_tiles) {
-            // the large message holding global tile `item` (warp-uniform search)
-            uint32_t lo = 0, hi = p.n_b;  // b_prefix[lo] <= item < b_prefix[hi]
+        if (item < p.n_b_chunks) {
+            // a run of b_chunk consecutive tiles: one message search for the
+            // run, then a step forward at each message boundary
+            const uint64_t t0 = item * p.b_chunk;
+            uint32_t lo = 0, hi = p.n_b;  // b_prefix[lo] <= t0 < b_prefix[hi]
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (p.b_prefix[mid] <= item) lo = mid; else hi = mid;
+                if (p.b_prefix[mid] <= t0) lo = mid; else hi = mid;
             }
-            const BatchMsg* mp = p.msgs + p.b_msg[lo];
-            const uint32_t key = mp->key, dir = (uint32_t)dir_of(mp->mode);
-            const uint64_t want = ((uint64_t)key << 1) | dir;
-            if (want != staged) {
-                __syncwarp();
-                const uint4* src = reinterpret_cast<const uint4*>(
-                    p.keytab + (uint64_t)key * kPerKeyWords + TDES_TABLE_WORDS * dir);
-                for (int i = lane; i < TDES_TABLE_WORDS / 4; i += 32)
-                    reinterpret_cast<uint4*>(wtab)[i] = __ldg(src + i);
-                __syncwarp();
-                staged = want;
+            for (uint64_t t = t0; t < min(t0 + p.b_chunk, p.n_b_tiles); ++t) {
+                while (t >= p.b_prefix[lo + 1]) ++lo;
+                const BatchMsg* mp = p.msgs + p.b_msg[lo];
+                const uint32_t key = mp->key, dir = (uint32_t)dir_of(mp->mode);
+                const uint32_t want = (key << 1) | dir;
+                if (want != staged) {
+                    __syncwarp();
+                    const uint4* src = reinterpret_cast<const uint4*>(
+                        p.keytab + (uint64_t)key * kPerKeyWords + TDES_TABLE_WORDS * dir);
+                    for (int i = lane; i < TDES_TABLE_WORDS / 4; i += 32)
+                        reinterpret_cast<uint4*>(wtab)[i] = __ldg(src + i);
+                    __syncwarp();
+                    staged = want;
+                }
+                batch_bs_tile(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane);
             }
-            batch_bs_tile(mp, item - p.b_prefix[lo], item, wtab, p.halo, lane);
             continue;
         }
-        item -= p.n_b_tiles;
-        batch_scalar_item(p, p.s_items[item], wsm, st, lane);
-        staged = ~0ull;
+        item -= p.n_b_chunks;
+        batch_scalar_item(p, p.s_items[item], warp, lane);
+        staged = ~0u;
     }
 }
 
@@ -475,16 +485,23 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
     return cudaSuccess;
 }
 
-cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo, int warps,
+cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool needs_halo, int warps,
                           size_t dyn_smem, uint64_t max_ctas, cudaStream_t s) {
     if (total_items == 0) return cudaSuccess;
+    // Tiles per claim: enough to amortise a warp's message search and key
+    // staging, few enough that every warp still gets about four claims.
+    BatchParams p = p_in;
+    const uint64_t warps_total = std::max<uint64_t>(1, max_ctas * (uint64_t)warps);
+    p.b_chunk = (uint32_t)std::min<uint64_t>(8, std::max<uint64_t>(1, p.n_b_tiles / (4 * warps_total)));
+    p.n_b_chunks = (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk;
+    total_items = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
     cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (needs_halo && p.n_b_tiles) {
         tdes_batch_halo_kernel<<<(unsigned)((p.n_b_tiles + 255) / 256), 256, 0, s>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const uint64_t want = (total_items + warps - 1) / warps;
+    const uint64_t want = (total_items + warps - 1) / (uint64_t)warps;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
     tdes_batch_kernel<<<grid, 32 * warps, dyn_smem, s>>>(p);
     return cudaGetLastError();

@@ -43,6 +43,8 @@ struct BatchParams {
     uint32_t n_s_items;
     uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
     unsigned long long* counter;
+    uint32_t b_chunk;          // B tiles per claimed item (set at launch)
+    uint64_t n_b_chunks;       // ceil(n_b_tiles / b_chunk)
 };
 
 

@@ -143,21 +143,41 @@ cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t 
 
 // ------------------------------------------------------------------- CTR
 // Keystream block i = E(nonce || ctr0 + i); the counter blocks are built in
-// registers, then the data tile is loaded and XORed on the way out.
+// registers.  The data tile the keystream is XORed into is copied into the
+// warp's 8 KiB of shared memory with cp.async before the rounds start, so
+// its memory latency hides behind them.
+constexpr int kCtrWarpBytes = 8 * kTileBlocks;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <bool VEC>
 __global__ void __launch_bounds__(256, 2)
 tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr0,
                 const uint8_t* in, uint8_t* out, uint64_t nblocks) {
     __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
+    extern __shared__ __align__(16) uint4 ctr_data[];  // kCtrWarpBytes per warp
     stage_table(tab, table);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = blockDim.x >> 5;
+    uint4* wbuf = ctr_data + (threadIdx.x >> 5) * (kCtrWarpBytes / 16);
     const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
     const uint32_t nw = bswap32(nonce);
     for (uint64_t t = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles;
          t += (uint64_t)gridDim.x * warps) {
         const uint64_t b0 = t * kTileBlocks;
+        const bool full = VEC && b0 + kTileBlocks <= nblocks;
+        if (full) {  // each lane copies, and later reads back, only its own 16 x 16 bytes
+            const uint4* p = reinterpret_cast<const uint4*>(in) + (b0 >> 1) + lane;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cp_async16(wbuf + 32 * j + lane, p + 32 * j);
+            cp_async_commit();
+        }
         uint32_t A0[32], A1[32];
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -168,12 +188,12 @@ tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr
                 A1[2 * j + h] = bswap32(ctr0 + b);
             }
         tdes_process32(A0, A1, tab);
-        if (VEC && b0 + kTileBlocks <= nblocks) {
-            const uint4* p = reinterpret_cast<const uint4*>(in) + (b0 >> 1) + lane;
+        if (full) {
+            cp_async_wait_all();
             uint4* q = reinterpret_cast<uint4*>(out) + (b0 >> 1) + lane;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const uint4 v = __ldcs(p + 32 * j);
+                const uint4 v = wbuf[32 * j + lane];
                 __stcs(q + 32 * j, make_uint4(v.x ^ A0[2 * j], v.y ^ A1[2 * j],
                                               v.z ^ A0[2 * j + 1], v.w ^ A1[2 * j + 1]));
             }
@@ -194,14 +214,29 @@ tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr
     }
 }
 
+static bool ctr_smem_ready[64];
+
 cudaError_t launch_ctr(const uint32_t* tab_enc, uint32_t nonce, uint32_t ctr0, const void* in,
                        void* out, uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !ctr_smem_ready[dev]) {
+        const int dyn = kWideWarps * kCtrWarpBytes;
+        cudaError_t e = cudaFuncSetAttribute(tdes_ctr_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tdes_ctr_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        ctr_smem_ready[dev] = true;
+    }
+    const size_t dyn = (size_t)(g.threads / 32) * kCtrWarpBytes;
     if (vec16)
-        tdes_ctr_kernel<true><<<g.grid, g.threads, 0, s>>>(
+        tdes_ctr_kernel<true><<<g.grid, g.threads, dyn, s>>>(
             tab_enc, nonce, ctr0, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out),
             nblocks);
     else
-        tdes_ctr_kernel<false><<<g.grid, g.threads, 0, s>>>(
+        tdes_ctr_kernel<false><<<g.grid, g.threads, dyn, s>>>(
             tab_enc, nonce, ctr0, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out),
             nblocks);
     return cudaGetLastError();
@@ -336,7 +371,12 @@ int wide_ctas_per_sm(int kernel_id) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ecb_kernel<true>, threads, 0);
             break;
         case kCtr:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ctr_kernel<true>, threads, 0);
+            e = cudaFuncSetAttribute(tdes_ctr_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWideWarps * kCtrWarpBytes);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ctr_kernel<true>, threads,
+                                                                  kWideWarps * kCtrWarpBytes);
             break;
         default:
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_cbc_dec_kernel<true>,
