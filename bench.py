@@ -188,6 +188,21 @@ def probe_alu_peak():
     return best
 
 
+# ------------------------------------------------------------- multi-rank
+def reduce_max(x: float, device: str) -> float:
+    """Max of x over all ranks of the default process group (the slowest rank's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_rank: int, world: int, slowest_s: float) -> float:
+    """Whole-job GB/s: every rank's bytes over the slowest rank's time."""
+    return world * bytes_per_rank / slowest_s / 1e9
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -247,12 +262,10 @@ def run_ours(args):
     clocks = stop_clock_sampler(sampler)
     total_ms = start.elapsed_time(end)
     if world > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max(total_ms, f"cuda:{dev}")
     per_launch_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
     ms_per_step = total_ms / args.steps
-    value = world * NBYTES / (ms_per_step * 1e-3) / 1e9
+    value = job_throughput(NBYTES, world, ms_per_step * 1e-3)
 
     # the timed output decrypts back to the input (parity with the oracle is
     # the test suite's job)
@@ -304,9 +317,7 @@ def run_ours(args):
             tdes.tdes_ecb_crypt_host(ks, False, hbuf, hbuf, dev_buf)
         el = (time.perf_counter() - t) / n_e2e
         if world > 1:
-            tt = torch.tensor([el], device=f"cuda:{dev}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+            el = reduce_max(el, f"cuda:{dev}")
         e2e = {"value": world * NBYTES / el / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": NBYTES, "d2h_bytes_per_step": NBYTES,
                "api": "tdes_ecb_crypt_host (pinned host buffer, 256 MiB device staging)"}

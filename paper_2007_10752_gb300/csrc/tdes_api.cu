@@ -60,6 +60,8 @@ int check_call(const tdes_ks_t* ks, const void* in, const void* out, size_t nbyt
     if (nbytes % 8 != 0) return fail(TDES_EINVAL, "nbytes = %zu is not a multiple of 8", nbytes);
     *nblocks = nbytes / 8;
     if (nbytes == 0) return TDES_OK;
+    if (*nblocks / tdes::kTileBlocks >= (1ull << 32) - 1)
+        return fail(TDES_EINVAL, "a call is limited to 2^32 - 1 tiles of 8 KiB");
     if (in == nullptr || out == nullptr) return fail(TDES_EINVAL, "NULL data pointer");
     const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
     if ((a | b) & 7u) return fail(TDES_EINVAL, "data pointers must be 8-byte aligned");
@@ -230,10 +232,14 @@ int tdes_cbc_encrypt(const tdes_ks_t* ks, uint64_t iv, const void* in, void* out
     return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CBC-encrypt kernel launch");
 }
 
-// Host-buffer ECB.  The device buffer is split into two halves; chunk k goes
-// host->device on the copy-in stream, through the kernel on the compute
-// stream, and device->host on the copy-out stream, with events ordering the
-// three and letting chunk k+1's copy-in overlap chunk k's kernel.
+// Host-buffer ECB.  The device buffer is split into kHostBufs equal parts
+// used round-robin; chunk k goes host->device on the copy-in stream, through
+// the kernel on the compute stream, and device->host on the copy-out stream,
+// with events ordering the three.  A part is refilled only after its previous
+// chunk has been copied out, so up to kHostBufs chunks are in flight and the
+// two copy directions and the kernel overlap.
+constexpr int kHostBufs = 4;
+
 int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, void* host_out,
                         size_t nbytes, void* dev_buf, size_t dev_bytes) {
     if (ks == nullptr) return fail(TDES_EINVAL, "key schedule is NULL");
@@ -243,20 +249,19 @@ int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, v
         return fail(TDES_EINVAL, "NULL pointer");
     if (reinterpret_cast<uintptr_t>(dev_buf) & 15u)
         return fail(TDES_EINVAL, "device buffer must be 16-byte aligned");
-    const size_t half = (dev_bytes / 2) & ~(size_t)(8 * tdes::kTileBlocks - 1);
-    if (half < 64 * 1024) return fail(TDES_EINVAL, "device buffer smaller than 2 x 64 KiB");
+    const size_t part = (dev_bytes / kHostBufs) & ~(size_t)(8 * tdes::kTileBlocks - 1);
+    if (part < 32 * 1024) return fail(TDES_EINVAL, "device buffer smaller than 4 x 32 KiB");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev != ks->device) return fail(TDES_EINVAL, "key schedule lives on another device");
 
     cudaStream_t sin = nullptr, scomp = nullptr, sout = nullptr;
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[kHostBufs] = {}, ev_k[kHostBufs] = {}, ev_out[kHostBufs] = {};
     e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < kHostBufs && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_k[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming);
@@ -264,27 +269,27 @@ int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, v
     const char* what = "stream/event setup";
     const uint8_t* src = static_cast<const uint8_t*>(host_in);
     uint8_t* dst = static_cast<uint8_t*>(host_out);
-    uint8_t* buf[2] = {static_cast<uint8_t*>(dev_buf), static_cast<uint8_t*>(dev_buf) + half};
-    bool used[2] = {false, false};
-    for (size_t off = 0, k = 0; e == cudaSuccess && off < nbytes; off += half, ++k) {
-        const int b = (int)(k & 1);
-        const size_t n = (nbytes - off < half) ? nbytes - off : half;
+    bool used[kHostBufs] = {};
+    for (size_t off = 0, k = 0; e == cudaSuccess && off < nbytes; off += part, ++k) {
+        const int b = (int)(k % kHostBufs);
+        uint8_t* buf = static_cast<uint8_t*>(dev_buf) + (size_t)b * part;
+        const size_t n = (nbytes - off < part) ? nbytes - off : part;
         const uint64_t nblocks = n / 8;
         const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
         what = "host-to-device copy";
-        if (used[b]) e = cudaStreamWaitEvent(sin, ev_out[b], 0);  // buffer drained
-        if (e == cudaSuccess) e = cudaMemcpyAsync(buf[b], src + off, n, cudaMemcpyHostToDevice, sin);
+        if (used[b]) e = cudaStreamWaitEvent(sin, ev_out[b], 0);  // part drained
+        if (e == cudaSuccess) e = cudaMemcpyAsync(buf, src + off, n, cudaMemcpyHostToDevice, sin);
         if (e == cudaSuccess) e = cudaEventRecord(ev_in[b], sin);
         what = "ECB kernel";
         if (e == cudaSuccess) e = cudaStreamWaitEvent(scomp, ev_in[b], 0);
         if (e == cudaSuccess) {
             const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kEcb, ks->device);
-            e = tdes::launch_ecb(ks->tab[decrypt ? 1 : 0], buf[b], buf[b], nblocks, true, g, scomp);
+            e = tdes::launch_ecb(ks->tab[decrypt ? 1 : 0], buf, buf, nblocks, true, g, scomp);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev_k[b], scomp);
         what = "device-to-host copy";
         if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_k[b], 0);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + off, buf[b], n, cudaMemcpyDeviceToHost, sout);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + off, buf, n, cudaMemcpyDeviceToHost, sout);
         if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], sout);
         used[b] = true;
     }
@@ -295,7 +300,7 @@ int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, v
         e = es;
         what = "synchronise";
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kHostBufs; ++i) {
         if (ev_in[i]) cudaEventDestroy(ev_in[i]);
         if (ev_k[i]) cudaEventDestroy(ev_k[i]);
         if (ev_out[i]) cudaEventDestroy(ev_out[i]);

@@ -488,11 +488,15 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
 cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool needs_halo, int warps,
                           size_t dyn_smem, uint64_t max_ctas, cudaStream_t s) {
     if (total_items == 0) return cudaSuccess;
-    // Tiles per claim: enough to amortise a warp's message search and key
-    // staging, few enough that every warp still gets about four claims.
+    // Tiles per claim.  A claimed tile takes a warp tens of microseconds at
+    // full occupancy, which already hides its message search and key staging
+    // behind the other warps, so claims are single tiles unless a batch has
+    // so many tiles (over 256 per warp) that the atomic counter itself and
+    // the restaging become worth amortising; the tail of a batch then costs
+    // at most one claim.
     BatchParams p = p_in;
     const uint64_t warps_total = std::max<uint64_t>(1, max_ctas * (uint64_t)warps);
-    p.b_chunk = (uint32_t)std::min<uint64_t>(8, std::max<uint64_t>(1, p.n_b_tiles / (4 * warps_total)));
+    p.b_chunk = p.n_b_tiles > 256 * warps_total ? 4u : 1u;
     p.n_b_chunks = (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk;
     total_items = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
     cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s);

@@ -158,16 +158,22 @@ TDES_HD uint64_t permute64(uint64_t v, const uint8_t* __restrict__ src) {
 // 1, 7, 5, 3 are the four bytes of rotr(R, 27) and those of S-boxes 2, 8, 6, 4
 // the four bytes of rotr(R, 23) (six bits each, first bit most significant),
 // so two rotates and two XORs with the round's key words ke/ko form all eight
-// S-box inputs; sp[64g + x] is S-box g followed by the permutation.
+// S-box inputs; sp[64g + x] is S-box g followed by the permutation.  Each
+// six-bit index is extracted already scaled by 4 (a byte offset into sp).
+TDES_HD uint32_t sp_at(const uint32_t* __restrict__ sp, int g, uint32_t byte_off) {
+    return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint8_t*>(sp + 64 * g) +
+                                               byte_off);
+}
+
 TDES_HD uint32_t tdes_f_scalar(uint32_t R, uint32_t ke, uint32_t ko,
                                const uint32_t* __restrict__ sp) {
     const uint32_t we = rotr32(R, 27) ^ ke;
     const uint32_t wo = rotr32(R, 23) ^ ko;
-    const uint32_t a = sp[0 * 64 + (we & 63u)] ^ sp[6 * 64 + ((we >> 8) & 63u)] ^
-                       sp[4 * 64 + ((we >> 16) & 63u)];
-    const uint32_t b = sp[2 * 64 + ((we >> 24) & 63u)] ^ sp[1 * 64 + (wo & 63u)] ^
-                       sp[7 * 64 + ((wo >> 8) & 63u)];
-    const uint32_t c = sp[5 * 64 + ((wo >> 16) & 63u)] ^ sp[3 * 64 + ((wo >> 24) & 63u)];
+    const uint32_t a = sp_at(sp, 0, (we << 2) & 0xFCu) ^ sp_at(sp, 6, (we >> 6) & 0xFCu) ^
+                       sp_at(sp, 4, (we >> 14) & 0xFCu);
+    const uint32_t b = sp_at(sp, 2, (we >> 22) & 0xFCu) ^ sp_at(sp, 1, (wo << 2) & 0xFCu) ^
+                       sp_at(sp, 7, (wo >> 6) & 0xFCu);
+    const uint32_t c = sp_at(sp, 5, (wo >> 14) & 0xFCu) ^ sp_at(sp, 3, (wo >> 22) & 0xFCu);
     return a ^ b ^ c;
 }
 
@@ -203,25 +209,28 @@ TDES_HD uint64_t permute64_nib(uint64_t v, const uint64_t* __restrict__ tab) {
 
 // The same EDE3 block as tdes_block_scalar with the permutations by nibble
 // tables (ipn/fpn: 16 x 16 words each) instead of bit loops.  The 16 rounds
-// of a DES pass are unrolled by two so that the halves alternate in place.
+// of a DES pass are unrolled by two so that the halves alternate in place,
+// and each round's key words are loaded one round ahead, off the chain of
+// dependent operations that sets the latency of a block.
 TDES_HD uint64_t tdes_block_scalar_nib(uint64_t v, const uint32_t* __restrict__ sp,
                                        const uint32_t* __restrict__ keys,
                                        const uint64_t* __restrict__ ipn,
                                        const uint64_t* __restrict__ fpn) {
     v = permute64_nib(v, ipn);
     uint32_t L = (uint32_t)(v >> 32), R = (uint32_t)v;
-    for (int pass = 0; pass < 3; ++pass) {
-        const uint32_t* k = keys + 32 * pass;
-#pragma unroll 2
-        for (int r = 0; r < 16; r += 2) {
-            L ^= tdes_f_scalar(R, k[2 * r], k[2 * r + 1], sp);
-            R ^= tdes_f_scalar(L, k[2 * r + 2], k[2 * r + 3], sp);
+    uint32_t ke = keys[0], ko = keys[1];
+    for (int r = 0; r < 48; r += 2) {
+        const uint32_t ke1 = keys[2 * r + 2], ko1 = keys[2 * r + 3];
+        L ^= tdes_f_scalar(R, ke, ko, sp);
+        const int rn = r + 2 < 48 ? r + 2 : r;  // the last prefetch rereads round 46
+        ke = keys[2 * rn];
+        ko = keys[2 * rn + 1];
+        R ^= tdes_f_scalar(L, ke1, ko1, sp);
+        if ((r & 15) == 14) {  // end of a DES pass: R16 || L16 continues as the next L0 || R0
+            const uint32_t u = L;
+            L = R;
+            R = u;
         }
-        // after 16 in-place rounds L = L16, R = R16; the next pass (or the
-        // output R16 || L16) starts from the swapped halves
-        const uint32_t u = L;
-        L = R;
-        R = u;
     }
     return permute64_nib(((uint64_t)L << 32) | R, fpn);
 }

@@ -72,15 +72,16 @@ __device__ __forceinline__ void load_tile(const uint8_t* base, uint64_t b0, uint
             A0[2 * j + 1] = v.z;
             A1[2 * j + 1] = v.w;
         }
-    } else {
-        const uint2* p = reinterpret_cast<const uint2*>(base);
+    } else {  // ragged tile or 8-byte-aligned buffer: 64-bit accesses, bounds-checked
+        const uint2* p = reinterpret_cast<const uint2*>(base) + b0;
+        const uint32_t nvalid = (uint32_t)min((uint64_t)kTileBlocks, nblocks - b0);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint64_t b = b0 + 2 * (32 * j + lane) + h;
+                const uint32_t i = 2u * (32u * j + lane) + h;
                 uint2 v = make_uint2(0u, 0u);
-                if (b < nblocks) v = __ldcs(p + b);
+                if (i < nvalid) v = __ldcs(p + i);
                 A0[2 * j + h] = v.x;
                 A1[2 * j + h] = v.y;
             }
@@ -97,13 +98,14 @@ __device__ __forceinline__ void store_tile(uint8_t* base, uint64_t b0, uint64_t 
         for (int j = 0; j < 16; ++j)
             __stcs(p + 32 * j, make_uint4(A0[2 * j], A1[2 * j], A0[2 * j + 1], A1[2 * j + 1]));
     } else {
-        uint2* p = reinterpret_cast<uint2*>(base);
+        uint2* p = reinterpret_cast<uint2*>(base) + b0;
+        const uint32_t nvalid = (uint32_t)min((uint64_t)kTileBlocks, nblocks - b0);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint64_t b = b0 + 2 * (32 * j + lane) + h;
-                if (b < nblocks) __stcs(p + b, make_uint2(A0[2 * j + h], A1[2 * j + h]));
+                const uint32_t i = 2u * (32u * j + lane) + h;
+                if (i < nvalid) __stcs(p + i, make_uint2(A0[2 * j + h], A1[2 * j + h]));
             }
     }
 }
@@ -120,13 +122,13 @@ tdes_ecb_kernel(const uint32_t* __restrict__ table, const uint8_t* in, uint8_t* 
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = blockDim.x >> 5;
-    const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
-    for (uint64_t t = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles;
-         t += (uint64_t)gridDim.x * warps) {
+    // tile indices fit 32 bits: the host caps a call at 2^32 tiles (32 TiB)
+    const uint32_t ntiles = (uint32_t)((nblocks + kTileBlocks - 1) / kTileBlocks);
+    for (uint32_t t = blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles; t += gridDim.x * warps) {
         uint32_t A0[32], A1[32];
-        load_tile<VEC>(in, t * kTileBlocks, nblocks, lane, A0, A1);
+        load_tile<VEC>(in, (uint64_t)t * kTileBlocks, nblocks, lane, A0, A1);
         tdes_process32(A0, A1, tab);
-        store_tile<VEC>(out, t * kTileBlocks, nblocks, lane, A0, A1);
+        store_tile<VEC>(out, (uint64_t)t * kTileBlocks, nblocks, lane, A0, A1);
     }
 }
 

@@ -180,14 +180,32 @@ def plane_index(k):
     return w, 8 * byte + 7 - (k - 1) % 8
 
 
-def emit_sbox(lines, g, circ):
+def emit_sbox(lines, g, circ, targets):
+    """The S-box's gates in order; each output's update (the XOR into the
+    other half, with the key swap) follows right after the output's gate, so
+    the output need not stay live to the end of the S-box."""
     xs = [f"x{u}" for u in range(6)]
     names = list(xs)
+    comps = ["x", "y", "z", "w"]
+    by_gate = {}
+    for t, (gid, neg) in enumerate(circ["outputs"]):
+        by_gate.setdefault(gid, []).append((t, neg))
+    lines.append(f"    const uint4 kc = *reinterpret_cast<const uint4*>(k + {8 * g});")
+
+    def updates(gid):
+        for t, neg in by_gate.get(gid, []):
+            i = targets[t]
+            lut = 0x69 if neg else 0x96
+            lines.append(f"    T[{i}] = lop3<0x{lut:02x}>(T[{i}], {names[gid]}, kc.{comps[t]});")
+
+    for gid in range(6):
+        updates(gid)
     for n, (a, b, c, lut) in enumerate(circ["gates"]):
         nm = f"s{g}_{n}"
         lines.append(f"    const uint32_t {nm} = lop3<0x{lut:02x}>({names[a]}, {names[b]}, {names[c]});")
         names.append(nm)
-    return [(names[gid], neg) for gid, neg in circ["outputs"]]
+        updates(6 + n)
+    return None
 
 
 def emit(path: str = OUT) -> str:
@@ -221,7 +239,6 @@ def emit(path: str = OUT) -> str:
     for g in range(8):
         circ = sboxes[g]
         L.append(f"    {{  // S-box {g + 1}")
-        L.append(f"    const uint4 kc = *reinterpret_cast<const uint4*>(k + {8 * g});")
         L.append(f"    const uint4 kd = *reinterpret_cast<const uint4*>(k + {8 * g + 4});")
         for u in range(6):
             j = 6 * g + u
@@ -232,13 +249,7 @@ def emit(path: str = OUT) -> str:
                 L.append(f"    const uint32_t x1 = S[{i}] * kd.w + kd.y;")
             else:
                 L.append(f"    const uint32_t x{u} = S[{i}];")
-        outs = emit_sbox(L, g, circ)
-        comps = ["x", "y", "z", "w"]
-        for t in range(4):
-            i = P_INV[4 * g + t]
-            nm, neg = outs[t]
-            lut = 0x69 if neg else 0x96
-            L.append(f"    T[{i}] = lop3<0x{lut:02x}>(T[{i}], {nm}, kc.{comps[t]});")
+        outs = emit_sbox(L, g, circ, P_INV[4 * g:4 * g + 4])
         L.append("    }")
     L.append("}")
     L.append("")
