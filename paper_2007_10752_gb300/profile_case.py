@@ -21,9 +21,10 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec", "batch"],
+    ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec", "cbc_enc", "batch"],
                     default="ecb")
     ap.add_argument("--mib", type=int, default=256)
+    ap.add_argument("--kib", type=int, default=0, help="size in KiB (overrides --mib)")
     ap.add_argument("--launches", type=int, default=3)
     args = ap.parse_args()
 
@@ -44,7 +45,7 @@ def main():
         torch.cuda.synchronize()
         print(f"batch: {args.launches} launches of {int(np.sum(d['mode'] != 4))} messages done")
         return
-    n = args.mib << 20
+    n = (args.kib << 10) if args.kib else (args.mib << 20)
     keys = synth.key_triple(2)
     x = torch.from_numpy(synth.random_bytes(2, n)).cuda()
     y = torch.empty_like(x)
@@ -56,6 +57,8 @@ def main():
             tdes.tdes_ecb_decrypt(ks, x, y)
         elif args.kernel == "ctr":
             tdes.tdes_ctr_crypt(ks, 1, 0, x, y)
+        elif args.kernel == "cbc_enc":
+            tdes.tdes_cbc_encrypt(ks, 1, x, y)
         else:
             tdes.tdes_cbc_decrypt(ks, 1, x, y)
     torch.cuda.synchronize()
