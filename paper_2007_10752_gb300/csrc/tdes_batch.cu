@@ -256,20 +256,46 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
     __syncwarp();
 }
 
-// C item: CBC-encryption chains, one per lane.  The first n_c_solo items
-// (the longest chains) hold one chain each; the rest hold up to 32.
+__device__ const uint32_t kBatchLaneSbox[32][4] = TDES_LANE_SBOX_INIT;
+__device__ const uint32_t kBatchLaneIP[32][2] = TDES_LANE_IP_INIT;
+__device__ const uint32_t kBatchLaneFP[32][2] = TDES_LANE_FP_INIT;
+
+// C item: CBC-encryption chains.  The first n_c_solo items (the longest
+// chains) hold one chain each, walked by the whole warp (tdes_block_warp: a
+// ballot per round, so the dependent chain per block is short); the rest hold
+// up to 32 short chains, one per lane, with the scalar round.
 __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t item,
                                                 uint32_t warp, uint32_t lane) {
     uint8_t* warp_smem = g_dyn + (size_t)warp * kWarpSmemBytes;
     const SharedTables& st = g_st;
-    uint32_t idx, end;
     if (item < p.n_c_solo) {
-        idx = lane == 0 ? item : p.n_c;
-        end = p.n_c_solo;
-    } else {
-        idx = p.n_c_solo + 32u * (item - p.n_c_solo) + lane;
-        end = p.n_c;
+        const BatchMsg m = p.msgs[p.c_list[item]];
+        const uint8_t* kg = p.keychunks + (uint64_t)m.key * kPerKeyChunks;
+        for (int i = lane; i < TDES_SUBKEY_WORDS / 16; i += 32)
+            reinterpret_cast<uint4*>(warp_smem)[i] = __ldg(reinterpret_cast<const uint4*>(kg) + i);
+        __syncwarp();
+        LaneConsts c;
+        c.mlo = kBatchLaneSbox[lane][0];
+        c.mhi = kBatchLaneSbox[lane][1];
+        c.rot = kBatchLaneSbox[lane][2];
+        c.keypos = kBatchLaneSbox[lane][3];
+        c.ip_hi = kBatchLaneIP[lane][0];
+        c.ip_lo = kBatchLaneIP[lane][1];
+        c.fp_hi = kBatchLaneFP[lane][0];
+        c.fp_lo = kBatchLaneFP[lane][1];
+        uint64_t prev = m.iv;
+        uint64_t next = load_be(m.in, 0);
+        for (uint64_t i = 0; i < m.nblocks; ++i) {
+            const uint64_t x = next ^ prev;
+            if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
+            prev = tdes_block_warp(x, c, warp_smem);
+            if (lane == 0) store_be(m.out, i, prev);
+        }
+        __syncwarp();
+        return;
     }
+    const uint32_t idx = p.n_c_solo + 32u * (item - p.n_c_solo) + lane;
+    const uint32_t end = p.n_c;
     if (idx < end) {
         const BatchMsg m = p.msgs[p.c_list[idx]];
         uint8_t* ch = warp_smem + TDES_SUBKEY_WORDS * lane;

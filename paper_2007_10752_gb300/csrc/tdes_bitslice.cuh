@@ -235,6 +235,51 @@ TDES_HD uint64_t tdes_block_scalar_nib(uint64_t v, const uint32_t* __restrict__ 
     return permute64_nib(((uint64_t)L << 32) | R, fpn);
 }
 
+#ifdef __CUDACC__
+// Warp-cooperative EDE3 block for one serial chain per warp: lane l holds
+// the constants of half bit i = 32 - l (TDES_LANE_SBOX_INIT) and computes that
+// bit of the round function from its S-box output mask; one ballot gathers the
+// 32 bits, so a round is rotate, XOR, shift and ballot instead of eight table
+// lookups and their XOR tree.  IP and FP are two ballots each.  Every lane
+// returns the same value.  keys: the chain's 384-byte round-key words (the
+// scalar layout), in shared memory.
+struct LaneConsts {
+    uint32_t mlo, mhi, rot, keypos;
+    uint32_t ip_hi, ip_lo, fp_hi, fp_lo;
+};
+
+__device__ __forceinline__ uint32_t lane_bit(uint64_t v, uint32_t src) {
+    return (uint32_t)(v >> (63u - src)) & 1u;
+}
+
+__device__ __forceinline__ uint64_t tdes_block_warp(uint64_t v, const LaneConsts& c,
+                                                    const uint8_t* __restrict__ keys) {
+    uint32_t L = __ballot_sync(0xFFFFFFFFu, lane_bit(v, c.ip_hi));
+    uint32_t R = __ballot_sync(0xFFFFFFFFu, lane_bit(v, c.ip_lo));
+    uint32_t k = keys[c.keypos];
+#pragma unroll 2
+    for (int r = 0; r < 48; ++r) {
+        const uint32_t kn = keys[8 * (r + 1 < 48 ? r + 1 : r) + c.keypos];
+        const uint32_t x = ((rotr32(R, (int)c.rot) & 63u) ^ k);
+        const uint32_t w = (x & 32u) ? c.mhi : c.mlo;
+        const uint32_t f = __ballot_sync(0xFFFFFFFFu, (w >> (x & 31u)) & 1u);
+        const uint32_t t = L ^ f;
+        L = R;
+        R = t;
+        if ((r & 15) == 15) {  // end of a DES pass: R16 || L16 continues as L0 || R0
+            const uint32_t u = L;
+            L = R;
+            R = u;
+        }
+        k = kn;
+    }
+    const uint64_t pre = ((uint64_t)L << 32) | R;
+    const uint32_t hi = __ballot_sync(0xFFFFFFFFu, lane_bit(pre, c.fp_hi));
+    const uint32_t lo = __ballot_sync(0xFFFFFFFFu, lane_bit(pre, c.fp_lo));
+    return ((uint64_t)hi << 32) | lo;
+}
+#endif
+
 TDES_HD uint64_t bswap64(uint64_t x) {
     x = ((x & 0x00FF00FF00FF00FFull) << 8) | ((x >> 8) & 0x00FF00FF00FF00FFull);
     x = ((x & 0x0000FFFF0000FFFFull) << 16) | ((x >> 16) & 0x0000FFFF0000FFFFull);

@@ -19,9 +19,7 @@ static_assert(kChunkBytes == TDES_SUBKEY_WORDS, "chunk size mismatch");
 
 __device__ const uint8_t kRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
 __device__ const uint8_t kSubkeyBits[2][48][48] = TDES_SUBKEY_INIT;
-__device__ const uint32_t kSP[8][64] = TDES_SP_INIT;
-__device__ const uint64_t kIPN[16][16] = TDES_IPN_INIT;
-__device__ const uint64_t kFPN[16][16] = TDES_FPN_INIT;
+
 
 int sbox_gate_count() { return TDES_SBOX_GATES; }
 
@@ -325,34 +323,43 @@ cudaError_t launch_cbc_dec(const uint32_t* tab_dec, uint64_t iv, const void* in,
 }
 
 // --------------------------------------------------------------- CBC encrypt
-// C_i = E(P_i XOR C_{i-1}): serial, one thread walks the chain with the
-// scalar round (S-box/permutation words and nibble permutation tables in
-// shared memory).
+// C_i = E(P_i XOR C_{i-1}): serial.  One warp walks the chain cooperatively
+// (tdes_block_warp: each lane one bit of the round function, a ballot per
+// round); the next plaintext block is loaded one block ahead.
+__device__ const uint32_t kLaneSbox[32][4] = TDES_LANE_SBOX_INIT;
+__device__ const uint32_t kLaneIP[32][2] = TDES_LANE_IP_INIT;
+__device__ const uint32_t kLaneFP[32][2] = TDES_LANE_FP_INIT;
+
+__device__ __forceinline__ LaneConsts lane_consts(uint32_t lane) {
+    LaneConsts c;
+    c.mlo = kLaneSbox[lane][0];
+    c.mhi = kLaneSbox[lane][1];
+    c.rot = kLaneSbox[lane][2];
+    c.keypos = kLaneSbox[lane][3];
+    c.ip_hi = kLaneIP[lane][0];
+    c.ip_lo = kLaneIP[lane][1];
+    c.fp_hi = kLaneFP[lane][0];
+    c.fp_lo = kLaneFP[lane][1];
+    return c;
+}
+
 __global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64_t iv,
                                     const uint8_t* in, uint8_t* out, uint64_t nblocks) {
-    __shared__ __align__(16) uint32_t sp[8 * 64];
-    __shared__ __align__(16) uint32_t keys[TDES_SUBKEY_WORDS / 4];
-    __shared__ __align__(16) uint64_t ipn[16 * 16], fpn[16 * 16];
-    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) sp[i] = (&kSP[0][0])[i];
-    for (int i = threadIdx.x; i < TDES_SUBKEY_WORDS / 4; i += blockDim.x)
-        keys[i] = reinterpret_cast<const uint32_t*>(chunks_g)[i];
-    for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) {
-        ipn[i] = (&kIPN[0][0])[i];
-        fpn[i] = (&kFPN[0][0])[i];
-    }
+    __shared__ __align__(16) uint8_t keys[TDES_SUBKEY_WORDS];
+    const uint32_t lane = threadIdx.x & 31u;
+    for (int i = threadIdx.x; i < TDES_SUBKEY_WORDS; i += blockDim.x) keys[i] = chunks_g[i];
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
+    const LaneConsts c = lane_consts(lane);
     const uint64_t* p = reinterpret_cast<const uint64_t*>(in);
     uint64_t* q = reinterpret_cast<uint64_t*>(out);
-    // The next plaintext block is loaded one iteration ahead so its memory
-    // latency hides behind the 48 rounds of the current one.
     uint64_t prev = iv;
     uint64_t next = p[0];
     for (uint64_t i = 0; i < nblocks; ++i) {
         const uint64_t x = bswap64(next) ^ prev;
         if (i + 1 < nblocks) next = p[i + 1];
-        prev = tdes_block_scalar_nib(x, sp, keys, ipn, fpn);
-        q[i] = bswap64(prev);
+        prev = tdes_block_warp(x, c, keys);
+        if (lane == 0) q[i] = bswap64(prev);
     }
 }
 

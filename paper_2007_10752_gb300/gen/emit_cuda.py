@@ -328,6 +328,33 @@ def emit(path: str = OUT) -> str:
         L.append("  {" + ",".join(vals) + "}, \\")
     L.append("}")
     L.append("")
+    L.append("// Warp-cooperative round (one chain per warp): lane l computes half bit")
+    L.append("// i = 32 - l of the round function, S-box output bit P[i].  Per lane:")
+    L.append("// {mask of that output bit over the 64 S-box inputs (low, high word),")
+    L.append("//  right-rotation of R that puts the S-box's expansion window at bits 5..0,")
+    L.append("//  byte of the round-key word pair holding the S-box's key group}.")
+    L.append("#define TDES_LANE_SBOX_INIT { \\")
+    for lane in range(32):
+        i = 32 - lane
+        q = T.P[i - 1] - 1
+        g, t = q // 4, q % 4
+        mask = 0
+        for x in range(64):
+            b1, b6 = (x >> 5) & 1, x & 1
+            v = T.SBOX[g][2 * b1 + b6][(x >> 1) & 0xF]
+            if (v >> (3 - t)) & 1:
+                mask |= 1 << x
+        rot = (27 - 4 * g) % 32
+        pos = SCALAR_GROUP_ORDER.index(g)
+        L.append(f"  {{0x{mask & 0xFFFFFFFF:08x}u, 0x{mask >> 32:08x}u, {rot}u, {pos}u}}, \\")
+    L.append("}")
+    L.append("// Per lane l: 0-based source bit of output bits 32 - l and 64 - l of IP and FP.")
+    for name, perm in (("IP", T.IP), ("FP", T.FP)):
+        L.append(f"#define TDES_LANE_{name}_INIT {{ \\")
+        L.append("  " + ", ".join("{%du, %du}" % (perm[32 - l - 1] - 1, perm[64 - l - 1] - 1)
+                               for l in range(32)) + " \\")
+        L.append("}")
+    L.append("")
     L.append("// Initial / final permutation by nibbles: entry [n][v] is the output word")
     L.append("// contribution of value v in input nibble n (input bits 4n+1..4n+4).")
     for name, perm in (("IPN", T.IP), ("FPN", T.FP)):
