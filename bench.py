@@ -303,6 +303,9 @@ def run_ours(args):
     # ---- serving: Poisson arrivals at fractions of the measured peak
     serving = None if args.no_serve else run_serving(torch, tdes, synth, x)
 
+    # ---- context: the paper's own design on this GPU, at the paper's sizes
+    paper_ctx = None if args.no_paper else run_paper_context(torch, tdes, synth, x, y, ks, stream)
+
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -378,6 +381,7 @@ def run_ours(args):
         "batched": batched,
         "serving": serving,
         "large_streaming": streaming,
+        "paper_design_context": paper_ctx,
         "extra": {"kernel_ms_per_launch": round(per_launch_ms, 4),
                   "ecb_decrypt_gbs": round(NBYTES / (dec_ms * 1e-3) / 1e9, 3),
                   "ctr_gbs": round(NBYTES / (ctr_ms * 1e-3) / 1e9, 3),
@@ -451,6 +455,41 @@ def run_batched(torch, tdes, synth, stream, ecb_gbs):
         "tiles": info["n_tiles"], "small_items": info["n_small_items"],
         "cbc_encrypt_messages": info["n_cbc_enc_messages"],
     }
+
+
+# -------------------------------------------- paper's design, as context
+# Table I, GPU-1 (RTX 2060 Super) of the paper: 3DES ECB encryption time in ms
+# (three kernel launches) for 2^2 .. 2^17 blocks.
+PAPER_TABLE1_GPU1_MS = [0.032, 0.033, 0.033, 0.032, 0.033, 0.032, 0.035, 0.050, 0.089, 0.161,
+                        0.305, 0.592, 1.184, 2.324, 4.511, 8.399]
+
+
+def run_paper_context(torch, tdes, synth, x, y, ks, stream):
+    """The paper's kernels (one CTA per block, a thread per bit, three launches)
+    rebuilt on this GB300, against the bitsliced ECB kernel, at Table I's sizes."""
+    from paper_2007_10752_gb300 import paper_design
+    keys = synth.key_triple(SEED)
+    rows = []
+    for e, paper_ms in zip(range(2, 18), PAPER_TABLE1_GPU1_MS):
+        n = 8 << e
+        xs, ys = x[:n], y[:n]
+        times = sorted(paper_design.paper_ecb(keys, xs, ys) for _ in range(5))
+        pd_ms = times[2]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            tdes.tdes_ecb_encrypt(ks, xs, ys)
+        e0.record(stream)
+        for _ in range(20):
+            tdes.tdes_ecb_encrypt(ks, xs, ys)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ours_ms = e0.elapsed_time(e1) / 20
+        rows.append({"blocks": 1 << e, "paper_table1_rtx2060s_ms": paper_ms,
+                     "paper_design_gb300_ms": round(pd_ms, 4), "bitsliced_gb300_ms": round(ours_ms, 4),
+                     "speedup_vs_paper_design_gb300": round(pd_ms / ours_ms, 1)})
+    return {"note": "paper's design rebuilt on GB300 (libtdes_tools.so); times of the three "
+                    "encryption launches vs one bitsliced launch; Table I numbers are the paper's "
+                    "own hardware, context only", "rows": rows}
 
 
 # ------------------------------------------------------- large streaming
@@ -573,6 +612,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

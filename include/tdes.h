@@ -121,7 +121,7 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t *ks, uint64_t iv, const void *in, v
 /* Host-buffer ECB: encrypts (decrypt == 0) or decrypts host memory
  * host_in[0, nbytes) into host_out, streaming it through the caller's device
  * buffer dev_buf of dev_bytes bytes (16-byte aligned, at least 4 x 32 KiB,
- * used as 4 rotating parts): host-to-device copies, the kernel and
+ * used as 4 to 16 rotating parts of about 32 MiB): host-to-device copies, the kernel and
  * device-to-host copies of successive chunks overlap on internal streams.  Host buffers should be pinned
  * (cudaHostAlloc / page-locked) for full copy speed.  Synchronous: returns
  * when host_out is complete.  in == out is allowed. */

@@ -3,6 +3,7 @@
 // All cipher arithmetic runs in the kernels of tdes_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -232,13 +233,14 @@ int tdes_cbc_encrypt(const tdes_ks_t* ks, uint64_t iv, const void* in, void* out
     return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CBC-encrypt kernel launch");
 }
 
-// Host-buffer ECB.  The device buffer is split into kHostBufs equal parts
-// used round-robin; chunk k goes host->device on the copy-in stream, through
-// the kernel on the compute stream, and device->host on the copy-out stream,
-// with events ordering the three.  A part is refilled only after its previous
-// chunk has been copied out, so up to kHostBufs chunks are in flight and the
-// two copy directions and the kernel overlap.
-constexpr int kHostBufs = 4;
+// Host-buffer ECB.  The device buffer is split into 4..16 equal parts (about
+// 32 MiB each) used round-robin; chunk k goes host->device on the copy-in
+// stream, through the kernel on the compute stream, and device->host on the
+// copy-out stream, with events ordering the three.  A part is refilled only
+// after its previous chunk has been copied out, so every part's chunk is in
+// flight at once and the two copy directions and the kernel overlap; small
+// parts keep the pipeline's fill and drain short.
+constexpr int kHostBufs = 16;
 
 int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, void* host_out,
                         size_t nbytes, void* dev_buf, size_t dev_bytes) {
@@ -249,7 +251,8 @@ int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, v
         return fail(TDES_EINVAL, "NULL pointer");
     if (reinterpret_cast<uintptr_t>(dev_buf) & 15u)
         return fail(TDES_EINVAL, "device buffer must be 16-byte aligned");
-    const size_t part = (dev_bytes / kHostBufs) & ~(size_t)(8 * tdes::kTileBlocks - 1);
+    const int nparts = (int)std::max<size_t>(4, std::min<size_t>(kHostBufs, dev_bytes >> 25));
+    const size_t part = (dev_bytes / nparts) & ~(size_t)(8 * tdes::kTileBlocks - 1);
     if (part < 32 * 1024) return fail(TDES_EINVAL, "device buffer smaller than 4 x 32 KiB");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -271,7 +274,7 @@ int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, v
     uint8_t* dst = static_cast<uint8_t*>(host_out);
     bool used[kHostBufs] = {};
     for (size_t off = 0, k = 0; e == cudaSuccess && off < nbytes; off += part, ++k) {
-        const int b = (int)(k % kHostBufs);
+        const int b = (int)(k % nparts);
         uint8_t* buf = static_cast<uint8_t*>(dev_buf) + (size_t)b * part;
         const size_t n = (nbytes - off < part) ? nbytes - off : part;
         const uint64_t nblocks = n / 8;

@@ -3,7 +3,9 @@
 //     peak the bitsliced kernels are bound by;
 //   * a device-side fill with the same counter-based SplitMix64 words as the
 //     host input generator (paper_2007_10752_gb300/synth.py), for inputs too
-//     large to generate on the host and copy.
+//     large to generate on the host and copy;
+//   * (tdes_paper_design.cu) the paper's own one-thread-per-bit kernels, as a
+//     context point for the benchmark.
 //
 // LOP3 probe:
 // Each thread keeps 8 accumulators and updates each with a 3-input LOP3 of
