@@ -141,13 +141,14 @@ def alg_ops_per_32_blocks() -> int:
     """Logic-pipe operations the bitsliced ECB algorithm needs per 32 blocks.
 
     48 rounds x (8 S-box circuits of G LOP3 in total + 32 fused XOR updates),
-    4 bit-matrix transposes x 256 operations, and 4 x 64 key-mask XORs
-    (prologue, two re-keyings, epilogue).  The 16 doubled expansion inputs
-    per round are XORed on the integer multiply-add pipe and not counted.
+    4 bit-matrix transposes x 256 operations, and 4 x 32 key-mask XORs
+    (prologue, two re-keyings, epilogue, one half each).  The 16 doubled
+    expansion inputs per round are XORed on the integer multiply-add pipe and
+    not counted.
     """
     with open(os.path.join(ROOT, "paper_2007_10752_gb300", "gen", "sbox_lop3.json")) as f:
         g = sum(len(s["gates"]) for s in json.load(f)["sboxes"])
-    return 48 * (g + 32) + 4 * 256 + 4 * 64
+    return 48 * (g + 32) + 4 * 256 + 4 * 32
 
 
 def kernel_source_hash() -> str:
@@ -347,7 +348,12 @@ def run_ours(args):
     pk, pk_kind = peaks()
     ops = alg_ops_per_32_blocks() * (NBYTES // 8 // 32)
     achieved = ops / (per_launch_ms * 1e-3) / 1e12
-    peak = alu_peak / 1e12
+    # ALU peak from unit counts and clock: SMs x 64 logic lanes per SM per clock
+    # (the lane count the live probe measures) x the maximum SM clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak = sms * 64 * max_mhz * 1e6 / 1e12
+    probe_lanes = alu_peak / (sms * max_mhz * 1e6) if alu_peak else None
     hbm_gbs = 16 * (NBYTES // 8) / (per_launch_ms * 1e-3) / 1e9
     traffic = profiled_traffic()
     line = {
@@ -369,7 +375,10 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                      "unit": "Tops/s", "frac": round(achieved / peak, 4) if peak else None,
                      "traffic": traffic,
-                     "peak_source": "live LOP3 probe (libtdes_tools.so) on this GPU",
+                     "peak_source": (f"{sms} SMs x 64 LOP3 lanes/clk x {max_mhz:.0f} MHz "
+                                     "(max SM clock, MEASURED_PEAKS.json)"),
+                     "peak_probe": round(alu_peak / 1e12, 3),
+                     "probe_lanes_per_sm_clk": round(probe_lanes, 2) if probe_lanes else None,
                      "alg_ops_per_32_blocks": alg_ops_per_32_blocks(),
                      "hbm_achieved_gbs": round(hbm_gbs, 1),
                      "hbm_peak_gbs": pk.get("hbm_gbs"),

@@ -103,30 +103,35 @@ TDES_HD void xor_planes(uint32_t (&H)[32], const uint32_t* __restrict__ k) {
 // The 48 rounds of EDE3 on keyed planes.  tab is the per-key round-constant
 // table (TDES_TABLE_WORDS words, encryption or decryption order) built by
 // the key-schedule kernel.
+// Each key-mask pass (prologue, the two re-keyings, epilogue) touches only the
+// half whose stored key bits change there; the generator checks that the
+// other half's constants are zero and says which half it is (TDES_*_HALF_R).
+#define TDES_KEY_PASS(NAME, BASE)                                  \
+    do {                                                           \
+        if (TDES_##NAME##_HALF_R) xor_planes(Rh, tab + (BASE) + 32); \
+        else xor_planes(Lh, tab + (BASE));                         \
+    } while (0)
+
 TDES_HD void tdes_rounds(uint32_t (&Lh)[32], uint32_t (&Rh)[32], const uint32_t* __restrict__ tab) {
-    xor_planes(Lh, tab + TDES_TABLE_PRO);
-    xor_planes(Rh, tab + TDES_TABLE_PRO + 32);
+    TDES_KEY_PASS(PRO, TDES_TABLE_PRO);
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {  // first DES pass: rounds 0..15
         tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it));
         tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it + 1));
     }
-    xor_planes(Lh, tab + TDES_TABLE_REKEY16);
-    xor_planes(Rh, tab + TDES_TABLE_REKEY16 + 32);
+    TDES_KEY_PASS(REKEY16, TDES_TABLE_REKEY16);
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {  // second pass: the XOR target repeats at its start
         tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (16 + 2 * it));
         tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (17 + 2 * it));
     }
-    xor_planes(Lh, tab + TDES_TABLE_REKEY32);
-    xor_planes(Rh, tab + TDES_TABLE_REKEY32 + 32);
+    TDES_KEY_PASS(REKEY32, TDES_TABLE_REKEY32);
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {  // third pass
         tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (32 + 2 * it));
         tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (33 + 2 * it));
     }
-    xor_planes(Lh, tab + TDES_TABLE_EPI);
-    xor_planes(Rh, tab + TDES_TABLE_EPI + 32);
+    TDES_KEY_PASS(EPI, TDES_TABLE_EPI);
 }
 
 // 32 blocks: A0[s], A1[s] are the first and second little-endian 32-bit

@@ -281,23 +281,25 @@ tdes_cbc_dec_kernel(const uint32_t* __restrict__ table, uint64_t iv, const uint8
         uint32_t A0[32], A1[32];
         load_tile<VEC>(in, b0, nblocks, lane, A0, A1);
         tdes_process32(A0, A1, tab);
+        const uint2* ct = c + b0;  // this tile's ciphertext, 32-bit indices below
+        const uint32_t nvalid = (uint32_t)min((uint64_t)kTileBlocks, nblocks - b0);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const uint64_t b = b0 + 2 * (32 * j + lane);  // slot 2j; slot 2j+1 is b + 1
+            const uint32_t i = 2u * (32u * j + lane);  // slot 2j; slot 2j+1 is i + 1
             uint2 prev0, prev1 = make_uint2(0u, 0u);
-            if (b == 0) {
-                prev0 = ivw;
-            } else if (j == 0 && lane == 0) {
-                if (halo != nullptr) {
+            if (j == 0 && lane == 0) {  // the block before the tile
+                if (b0 == 0) {
+                    prev0 = ivw;
+                } else if (halo != nullptr) {
                     const uint64_t hv = halo[t];
                     prev0 = make_uint2((uint32_t)hv, (uint32_t)(hv >> 32));
                 } else {
-                    prev0 = c[b - 1];
+                    prev0 = c[b0 - 1];
                 }
             } else {
-                prev0 = (b - 1 < nblocks) ? c[b - 1] : make_uint2(0u, 0u);
+                prev0 = (i - 1 < nvalid) ? ct[i - 1] : make_uint2(0u, 0u);
             }
-            if (b < nblocks) prev1 = c[b];
+            if (i < nvalid) prev1 = ct[i];
             A0[2 * j] ^= prev0.x;
             A1[2 * j] ^= prev0.y;
             A0[2 * j + 1] ^= prev1.x;

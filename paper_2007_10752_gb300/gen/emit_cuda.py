@@ -228,6 +228,14 @@ def emit(path: str = OUT) -> str:
     L.append(f"#define TDES_TABLE_EPI {EPI}")
     gates = sum(len(c["gates"]) for c in sboxes)
     L.append(f"#define TDES_SBOX_GATES {gates}  // LOP3 per round for the eight S-boxes")
+    # Which half each key-mask pass touches: the other half's words are all
+    # zero by construction of the keyed-plane schedule (checked here).
+    zero = lambda base: all(not words[base + i][0] for i in range(32))  # noqa: E731
+    passes = {"PRO": PRO, "REKEY16": REKEY[0], "REKEY32": REKEY[1], "EPI": EPI}
+    for name, base in passes.items():
+        l_zero, r_zero = zero(base), zero(base + 32)
+        assert l_zero != r_zero, f"{name}: expected exactly one half to need key masks"
+        L.append(f"#define TDES_{name}_HALF_R {0 if r_zero else 1}  // 1: the R half, 0: the L half")
     L.append("")
     L.append("// Needs TDES_HD and lop3<LUT>(a, b, c) from tdes_bitslice.cuh.")
     L.append("")
