@@ -111,29 +111,86 @@ __device__ __forceinline__ void store_tile(uint8_t* base, uint64_t b0, uint64_t 
 __device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0u, 0x0123); }
 
 // ------------------------------------------------------------------- ECB
+// Full tiles of 16-byte-aligned buffers are prefetched one tile ahead into the
+// warp's 8 KiB of shared memory with cp.async, so the next tile's memory
+// latency hides behind the current tile's rounds.  Each lane copies, and
+// later reads back, only its own 16 x 16 bytes; it reads a tile out of the
+// buffer before it issues the copy of the next one into the same place.
+constexpr int kCtrWarpBytes = 8 * kTileBlocks;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+
 template <bool VEC>
 __global__ void __launch_bounds__(256, 2)
 tdes_ecb_kernel(const uint32_t* __restrict__ table, const uint8_t* in, uint8_t* out,
                 uint64_t nblocks) {
     __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
+    extern __shared__ __align__(16) uint4 ecb_data[];  // kCtrWarpBytes per warp (VEC only)
     stage_table(tab, table);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = blockDim.x >> 5;
+    uint4* wbuf = ecb_data + (threadIdx.x >> 5) * (kCtrWarpBytes / 16);
     // tile indices fit 32 bits: the host caps a call at 2^32 tiles (32 TiB)
     const uint32_t ntiles = (uint32_t)((nblocks + kTileBlocks - 1) / kTileBlocks);
-    for (uint32_t t = blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles; t += gridDim.x * warps) {
+    const uint32_t nfull = (uint32_t)(nblocks / kTileBlocks);  // tiles [0, nfull) are full
+    const uint32_t stride = gridDim.x * warps;
+    uint32_t t = blockIdx.x * warps + (threadIdx.x >> 5);
+    if (VEC && t < nfull) {
+        const uint4* p = reinterpret_cast<const uint4*>(in) + (uint64_t)t * (kTileBlocks / 2) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) cp_async16(wbuf + 32 * j + lane, p + 32 * j);
+        cp_async_commit();
+    }
+    for (; t < ntiles; t += stride) {
         uint32_t A0[32], A1[32];
-        load_tile<VEC>(in, (uint64_t)t * kTileBlocks, nblocks, lane, A0, A1);
+        if (VEC && t < nfull) {
+            cp_async_wait_all();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint4 v = wbuf[32 * j + lane];
+                A0[2 * j] = v.x;
+                A1[2 * j] = v.y;
+                A0[2 * j + 1] = v.z;
+                A1[2 * j + 1] = v.w;
+            }
+            const uint32_t tn = t + stride;
+            if (tn < nfull) {
+                const uint4* p =
+                    reinterpret_cast<const uint4*>(in) + (uint64_t)tn * (kTileBlocks / 2) + lane;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) cp_async16(wbuf + 32 * j + lane, p + 32 * j);
+                cp_async_commit();
+            }
+        } else {
+            load_tile<VEC>(in, (uint64_t)t * kTileBlocks, nblocks, lane, A0, A1);
+        }
         tdes_process32(A0, A1, tab);
         store_tile<VEC>(out, (uint64_t)t * kTileBlocks, nblocks, lane, A0, A1);
     }
 }
 
+static bool ecb_smem_ready[64];
+
 cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t nblocks,
                        bool vec16, Geometry g, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !ecb_smem_ready[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(tdes_ecb_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kWideWarps * kCtrWarpBytes);
+        if (e != cudaSuccess) return e;
+        ecb_smem_ready[dev] = true;
+    }
     if (vec16)
-        tdes_ecb_kernel<true><<<g.grid, g.threads, 0, s>>>(
+        tdes_ecb_kernel<true><<<g.grid, g.threads, (size_t)(g.threads / 32) * kCtrWarpBytes, s>>>(
             tab, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks);
     else
         tdes_ecb_kernel<false><<<g.grid, g.threads, 0, s>>>(
@@ -146,15 +203,6 @@ cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t 
 // registers.  The data tile the keystream is XORed into is copied into the
 // warp's 8 KiB of shared memory with cp.async before the rounds start, so
 // its memory latency hides behind them.
-constexpr int kCtrWarpBytes = 8 * kTileBlocks;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 template <bool VEC>
 __global__ void __launch_bounds__(256, 2)
 tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr0,
@@ -379,7 +427,12 @@ int wide_ctas_per_sm(int kernel_id) {
     cudaError_t e = cudaSuccess;
     switch (kernel_id) {
         case kEcb:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ecb_kernel<true>, threads, 0);
+            e = cudaFuncSetAttribute(tdes_ecb_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWideWarps * kCtrWarpBytes);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ecb_kernel<true>, threads,
+                                                                  kWideWarps * kCtrWarpBytes);
             break;
         case kCtr:
             e = cudaFuncSetAttribute(tdes_ctr_kernel<true>,
