@@ -562,10 +562,23 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
                        "large_p99_ms": round(r["large_p99_ms"], 4),
                        "requests": r["requests"], "batches": r["batches"],
                        "duration_s": round(r["duration_s"], 3)})
+    # host payloads: request buffers in pinned host memory, read and written by
+    # the kernels over the host link (no staging copies)
+    host_in = in_pool[: 1 << 30].cpu().pin_memory()
+    host_out = torch.empty(2 << 30, dtype=torch.uint8).pin_memory()
+    hpeak = srv.loadtest(host_in, host_out, n_peak, 0.0, seed=7)
+    hhalf = srv.loadtest(host_in, host_out, n_points // 2, 0.5 * hpeak["gbps"], seed=8)
     srv.close()
-    del out_pool
+    del out_pool, host_in, host_out
     return {"workload": SERVE_WORKLOAD, "peak_closed_loop_gbs": round(peak["gbps"], 2),
             "peak_p50_ms": round(peak["p50_ms"], 3), "points": points,
+            "host_payloads": {"note": "same request mix, payloads in pinned host memory "
+                                      "(kernels access it over NVLink-C2C)",
+                              "peak_closed_loop_gbs": round(hpeak["gbps"], 2),
+                              "load_0.5": {"offered_gbs": round(hhalf["offered_gbps"], 2),
+                                           "achieved_gbs": round(hhalf["gbps"], 2),
+                                           "p50_ms": round(hhalf["p50_ms"], 4),
+                                           "p99_ms": round(hhalf["p99_ms"], 4)}},
             "server": srv.config}
 
 

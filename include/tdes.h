@@ -18,9 +18,15 @@
  *   - A block is 8 bytes, big-endian: bit 1 of the paper's numbering is the
  *     most significant bit of the first byte.  Keys use the same order; the
  *     parity bits (bit 8 of every byte) are ignored, as PC-1 drops them.
- *   - Data pointers are DEVICE pointers owned by the caller, on the device
- *     that was current when the key schedule was made.  They must be 8-byte
- *     aligned; 16-byte aligned buffers take the fastest load path.
+ *   - Data pointers are owned by the caller and must be addressable by the
+ *     GPU with the same pointer: device memory of the device that was current
+ *     when the key schedule was made, or page-locked host memory mapped into
+ *     the device address space (cudaHostAlloc on a unified-address system;
+ *     the kernels then read and write it over the host link, e.g.
+ *     NVLink-C2C).  Single-message calls and server requests refuse other
+ *     pointers with TDES_EINVAL; batch plans, which may hold millions of
+ *     descriptors, trust the caller.  Pointers must be 8-byte aligned;
+ *     16-byte aligned buffers take the fastest load path.
  *     `nbytes` must be a multiple of 8 (the paper's input consists of whole
  *     64-bit blocks); 0 is a valid empty call.  in == out (in place) is
  *     allowed; any other overlap of the two ranges returns TDES_EINVAL.

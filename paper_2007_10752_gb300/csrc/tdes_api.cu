@@ -74,6 +74,8 @@ int check_call(const tdes_ks_t* ks, const void* in, const void* out, size_t nbyt
     if (dev != ks->device)
         return fail(TDES_EINVAL, "key schedule lives on device %d but device %d is current",
                     ks->device, dev);
+    if (!tdes::gpu_addressable(in) || !tdes::gpu_addressable(out))
+        return fail(TDES_EINVAL, "buffers must be device memory or pinned, mapped host memory");
     return TDES_OK;
 }
 
@@ -86,6 +88,23 @@ bool aligned16(const void* in, const void* out) {
 namespace tdes {
 
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+bool gpu_addressable(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of the query
+        return false;
+    }
+    switch (a.type) {
+        case cudaMemoryTypeDevice:
+        case cudaMemoryTypeManaged:
+            return true;
+        case cudaMemoryTypeHost:
+            return a.devicePointer == p;
+        default:
+            return false;
+    }
+}
 
 // Small inputs: one warp per CTA so the few tiles spread over many SMs.
 // Large inputs: kWideWarps warps per CTA, a grid of every resident CTA,

@@ -500,8 +500,11 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
 
 cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
     const size_t dyn = (size_t)warps * kWarpSmemBytes;
+    // The limit is a property of the kernel function shared by every plan, so
+    // it is always set for the largest shape (8 warps) rather than this one.
     cudaError_t e = cudaFuncSetAttribute(tdes_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * kWarpSmemBytes);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_batch_kernel, 32 * warps, dyn);

@@ -18,6 +18,12 @@ namespace tdes {
 // Records the message tdes_last_error() returns on this host thread.
 void set_last_error(const char* msg);
 
+// True if the GPU can address `p` with the same pointer: device or managed
+// memory, or page-locked host memory mapped into the device address space
+// (what cudaHostAlloc gives on a unified-address system).  Pageable host
+// memory is refused: a kernel access to it could fault.
+bool gpu_addressable(const void* p);
+
 constexpr int kTileBlocks = 1024;  // blocks per warp tile: 32 lanes x 32 blocks
 constexpr int kWideWarps = 8;      // warps per CTA for large inputs
 constexpr int kTableWords = 3328;  // words of one bitsliced round-constant table

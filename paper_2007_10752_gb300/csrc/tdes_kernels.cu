@@ -9,6 +9,8 @@
 // into shared memory once per CTA and read with broadcast 128-bit loads.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "tdes_internal.h"
 #include "tdes_keysched.cuh"
 
@@ -176,7 +178,7 @@ tdes_ecb_kernel(const uint32_t* __restrict__ table, const uint8_t* in, uint8_t* 
     }
 }
 
-static bool ecb_smem_ready[64];
+static std::atomic<bool> ecb_smem_ready[64];
 
 cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t nblocks,
                        bool vec16, Geometry g, cudaStream_t s) {
@@ -262,7 +264,7 @@ tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr
     }
 }
 
-static bool ctr_smem_ready[64];
+static std::atomic<bool> ctr_smem_ready[64];
 
 cudaError_t launch_ctr(const uint32_t* tab_enc, uint32_t nonce, uint32_t ctr0, const void* in,
                        void* out, uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s) {

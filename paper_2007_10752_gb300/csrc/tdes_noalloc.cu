@@ -78,6 +78,8 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t* ks, uint64_t iv, const void* in, v
     if (dev != ks->device)
         return fail(TDES_EINVAL, "key schedule lives on device %d but device %d is current",
                     ks->device, dev);
+    if (!tdes::gpu_addressable(in) || !tdes::gpu_addressable(out))
+        return fail(TDES_EINVAL, "buffers must be device memory or pinned, mapped host memory");
     const uint64_t nblocks = nbytes / 8;
     const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

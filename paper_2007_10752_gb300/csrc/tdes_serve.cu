@@ -263,6 +263,8 @@ int tdes_server_submit(tdes_server_t* s, const tdes_desc_t* req, uint64_t* ticke
         return sfail(TDES_EINVAL, "NULL argument");
     if (tdes::validate_desc(*req, s->kt->count) != TDES_OK)
         return sfail(TDES_EINVAL, "invalid request descriptor");
+    if (req->nbytes && (!tdes::gpu_addressable(req->in) || !tdes::gpu_addressable(req->out)))
+        return sfail(TDES_EINVAL, "request buffers must be device memory or pinned host memory");
     const uint64_t cost = cost_of(*req);
     if (cost > s->cfg.budget_bytes)
         return sfail(TDES_EINVAL, "request of %llu bytes exceeds the admission budget",

@@ -228,3 +228,18 @@ def test_config3_shape_sampled(cuda_lib):
                 prev = iv if s == 0 else int.from_bytes(hd[o + 8 * s - 8:o + 8 * s].tobytes(), "big")
                 ref = oracle.tdes_cbc_encrypt(k, prev, x)
             assert (y == ref).all(), f"message {i} mode {mode} window {s}"
+
+
+def test_plans_with_different_shapes_coexist(mix):
+    """Each plan keeps its own launch shape; configuring a small plan must not
+    stop a larger-shaped plan from launching afterwards."""
+    T, arena, msgs, keys, kt, want = mix
+    big = T.Batch(kt, entries_for(arena, msgs))
+    small = T.Batch(kt, entries_for(arena, msgs))
+    big.configure(8, 0)
+    small.configure(2, 1)
+    for b in (big, small, big):
+        restage(arena, msgs)
+        b.launch()
+        for i, (got, w) in enumerate(zip(outputs(arena, msgs), want)):
+            assert (got == w).all(), f"message {i}"

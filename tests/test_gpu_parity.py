@@ -232,3 +232,22 @@ def test_full_size_1gib_sampled(cuda_lib):
         assert (yh[w] == oracle.tdes_ctr(keys, nonce, int(s), host[w])).all(), f"CTR at {s}"
     del x, y
     torch.cuda.empty_cache()
+
+
+def test_pinned_host_buffers_zero_copy(cuda_lib):
+    """The kernels read and write page-locked host memory directly over the
+    host link; pageable memory is refused before any launch."""
+    keys = synth.key_triple(7000)
+    data = synth.random_bytes(7000, 8 * (3 * 1024 + 77))
+    ks = cuda_lib.KeySchedule.from_triple(keys)
+    hin = torch.from_numpy(data).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    cuda_lib.tdes_ecb_encrypt(ks, hin, hout)
+    cuda_lib.tdes_ctr_crypt(ks, 5, 0, hout, hout)  # in place, host to host
+    torch.cuda.synchronize()
+    want = oracle.tdes_ctr(keys, 5, 0, oracle.tdes_ecb(keys, data))
+    assert (hout.numpy() == want).all()
+    pageable = np.zeros_like(data)
+    with pytest.raises(cuda_lib.TdesError) as e:
+        cuda_lib.tdes_ecb_encrypt(ks, pageable, pageable)
+    assert e.value.status == cuda_lib.TDES_EINVAL

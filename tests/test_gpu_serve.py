@@ -111,3 +111,24 @@ def test_loadtest_reports(cuda_lib):
     sat = srv.loadtest(pool, out, 3000, 0.0, large=(64 << 10, 4 << 20))
     assert sat["gbps"] > 0
     srv.close()
+
+
+def test_server_host_payloads(cuda_lib):
+    """Requests whose buffers are pinned host memory (the kernels work on them
+    over the host link); pageable host buffers are refused at submit."""
+    T = cuda_lib
+    keys = synth.key_triples(25, 16)
+    kt = T.KeyTable(keys)
+    srv = T.Server(kt)
+    reqs = _requests(25, 120, 16, big_every=40)
+    ins = [torch.from_numpy(r["data"]).pin_memory() for r in reqs]
+    outs = [torch.empty_like(x).pin_memory() for x in ins]
+    tickets = [srv.submit(r["mode"], r["key"], r["iv"], x, y) for r, x, y in zip(reqs, ins, outs)]
+    for t in tickets:
+        assert srv.wait(t, 60.0) == 0
+    for r, y in zip(reqs, outs):
+        assert (y.numpy() == _oracle(r["mode"], keys[r["key"]].tobytes(), r["iv"], r["data"])).all()
+    page = np.zeros(4096, dtype=np.uint8)
+    with pytest.raises(T.TdesError):
+        srv.submit(0, 0, 0, page, page)
+    srv.close()
