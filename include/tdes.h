@@ -62,10 +62,29 @@ typedef struct tdes_ks tdes_ks_t;          /* opaque, library-owned key schedule
  * round-constant tables of the bitsliced kernels for encryption and for
  * decryption (the decryption table is the round keys in reverse order,
  * Sec. III-B) and the six-bit round-key groups of the scalar path.  Weak
- * keys and K1 = K2 = K3 (which reduces EDE3 to single DES, Sec. III-B) are
- * accepted.  Free with tdes_key_free(). */
+ * keys are accepted.  Free with tdes_key_free().
+ *
+ * A triple whose middle key equals one of its neighbours in the 56 bits the
+ * key schedule uses (parity bits ignored) reduces EDE3 to one DES pass:
+ * K1 = K2 gives DES under K3 (E_K3(D_K1(E_K1(x))) = E_K3(x)), K2 = K3 gives
+ * DES under K1, and K1 = K2 = K3 gives DES under K (Sec. III-B).  Such a
+ * triple gets a single-DES schedule: the same results, 16 rounds per block
+ * instead of 48 (tdes_key_schedule_stages() reports 1). */
 int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3[8],
                       tdes_ks_t **out);
+
+/* Two-key 3DES: EDE3 under (k1, k2, k1).  Same as tdes_key_schedule(k1, k2,
+ * k1, out). */
+int tdes_key_schedule_2key(const uint8_t k1[8], const uint8_t k2[8], tdes_ks_t **out);
+
+/* Single DES (Sec. III-A and the DES rounds of Sec. III-B) under the 8-byte
+ * key k: the data calls below then compute DES_k with one 16-round pass per
+ * block -- the result EDE3 gives under (k, k, k). */
+int tdes_des_key_schedule(const uint8_t k[8], tdes_ks_t **out);
+
+/* DES passes per block that data calls with this schedule run: 3 (EDE3) or
+ * 1 (single DES).  TDES_EINVAL for NULL. */
+int tdes_key_schedule_stages(const tdes_ks_t *ks);
 
 /* Releases a key schedule (NULL is ignored).  The caller must ensure no
  * kernel that uses it is still running. */
@@ -94,8 +113,9 @@ int tdes_cbc_decrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out
                      size_t nbytes, tdes_stream_t stream);
 
 /* CBC encryption: out_i = E(in_i XOR out_{i-1}), out_{-1} = iv.  Each block
- * depends on the previous one, so one GPU thread walks the whole message
- * (latency about 48 dependent rounds per block); batch many messages to get
+ * depends on the previous one, so one warp walks the whole message (each
+ * lane one bit of the round function; latency about 48 dependent rounds per
+ * block, 16 for a single-DES schedule); batch many messages to get
  * throughput. */
 int tdes_cbc_encrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out,
                      size_t nbytes, tdes_stream_t stream);
@@ -289,6 +309,17 @@ int tdes_serve_loadtest(tdes_server_t *s, const tdes_loadtest_config_t *cfg,
 /* Number of LOP3 instructions the eight generated S-box circuits take per
  * round, i.e. per 32 blocks per round (the circuit size fixed at build time). */
 int tdes_sbox_gate_count(void);
+
+/* Small calls.  ECB, CTR and CBC-decryption calls of at most this many
+ * blocks run one block per GPU thread (the scalar round: latency of 48
+ * dependent rounds, 16 for single DES) instead of bitsliced tiles of 1024
+ * blocks (latency of a whole tile, however few blocks it holds).  In-place
+ * CBC decryption takes that path only up to 1024 blocks.  Results are
+ * identical either way.  Process-wide; the default, TDES_SMALL_CUTOFF_DEFAULT,
+ * is about where the two paths take equally long on GB300.  0 sends every
+ * call to the bitsliced kernels.  Returns the previous value. */
+#define TDES_SMALL_CUTOFF_DEFAULT 196608u
+uint64_t tdes_set_small_cutoff(uint64_t nblocks);
 
 /* Short English text of a status code. */
 const char *tdes_strerror(int status);

@@ -17,6 +17,10 @@ from .oracle import (  # noqa: F401
     compile_oracle,
     default,
     des_block,
+    des_cbc_decrypt,
+    des_cbc_encrypt,
+    des_ctr,
+    des_ecb,
     des_round_keys,
     sbox,
     tdes_block,

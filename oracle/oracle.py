@@ -62,6 +62,13 @@ def _keys(keys) -> np.ndarray:
     return k
 
 
+def _key8(key) -> np.ndarray:
+    k = _u8(key).reshape(-1)
+    if k.size != 8:
+        raise ValueError("a DES key is 8 bytes")
+    return k
+
+
 def _blocks(data) -> np.ndarray:
     d = _u8(data).reshape(-1)
     if d.size % 8:
@@ -86,6 +93,12 @@ class Oracle:
         lib.oracle_tdes_ctr.restype = ctypes.c_int
         lib.oracle_tdes_cbc_encrypt.argtypes = [u8p, ctypes.c_uint64, u8p, u8p, ctypes.c_uint64]
         lib.oracle_tdes_cbc_decrypt.argtypes = [u8p, ctypes.c_uint64, u8p, u8p, ctypes.c_uint64]
+        lib.oracle_des_ecb.argtypes = [u8p, ctypes.c_int, u8p, u8p, ctypes.c_uint64]
+        lib.oracle_des_ctr.argtypes = [u8p, ctypes.c_uint32, ctypes.c_uint32, u8p, u8p,
+                                       ctypes.c_uint64]
+        lib.oracle_des_ctr.restype = ctypes.c_int
+        lib.oracle_des_cbc_encrypt.argtypes = [u8p, ctypes.c_uint64, u8p, u8p, ctypes.c_uint64]
+        lib.oracle_des_cbc_decrypt.argtypes = [u8p, ctypes.c_uint64, u8p, u8p, ctypes.c_uint64]
         lib.oracle_tdes_parallel.argtypes = [u8p, ctypes.c_int, ctypes.c_uint32,
                                              ctypes.c_uint32, u8p, u8p, ctypes.c_uint64,
                                              ctypes.c_int]
@@ -154,6 +167,36 @@ class Oracle:
                                          d.size // 8)
         return out
 
+    # single DES (one pass of Sec. III-B) in the same modes
+    def des_ecb(self, key, data, decrypt: bool = False) -> np.ndarray:
+        k, d = _key8(key), _blocks(data)
+        out = np.empty_like(d)
+        self.lib.oracle_des_ecb(_ptr(k), int(decrypt), _ptr(d), _ptr(out), d.size // 8)
+        return out
+
+    def des_ctr(self, key, nonce: int, ctr0: int, data) -> np.ndarray:
+        k, d = _key8(key), _blocks(data)
+        out = np.empty_like(d)
+        rc = self.lib.oracle_des_ctr(_ptr(k), nonce & 0xFFFFFFFF, ctr0 & 0xFFFFFFFF, _ptr(d),
+                                     _ptr(out), d.size // 8)
+        if rc != 0:
+            raise ValueError("CTR counter would wrap past 2^32")
+        return out
+
+    def des_cbc_encrypt(self, key, iv: int, data) -> np.ndarray:
+        k, d = _key8(key), _blocks(data)
+        out = np.empty_like(d)
+        self.lib.oracle_des_cbc_encrypt(_ptr(k), iv & (2**64 - 1), _ptr(d), _ptr(out),
+                                        d.size // 8)
+        return out
+
+    def des_cbc_decrypt(self, key, iv: int, data) -> np.ndarray:
+        k, d = _key8(key), _blocks(data)
+        out = np.empty_like(d)
+        self.lib.oracle_des_cbc_decrypt(_ptr(k), iv & (2**64 - 1), _ptr(d), _ptr(out),
+                                        d.size // 8)
+        return out
+
     def tdes_parallel(self, keys, data, mode: str = "ecb_enc", nonce: int = 0, ctr0: int = 0,
                       threads: int = 1) -> np.ndarray:
         """ECB/CTR split over ``threads`` host threads (CPU-baseline timing only)."""
@@ -209,3 +252,19 @@ def tdes_cbc_decrypt(keys, iv, data):
 
 def tdes_parallel(keys, data, mode="ecb_enc", nonce=0, ctr0=0, threads=1):
     return default().tdes_parallel(keys, data, mode, nonce, ctr0, threads)
+
+
+def des_ecb(key, data, decrypt=False):
+    return default().des_ecb(key, data, decrypt)
+
+
+def des_ctr(key, nonce, ctr0, data):
+    return default().des_ctr(key, nonce, ctr0, data)
+
+
+def des_cbc_encrypt(key, iv, data):
+    return default().des_cbc_encrypt(key, iv, data)
+
+
+def des_cbc_decrypt(key, iv, data):
+    return default().des_cbc_decrypt(key, iv, data)

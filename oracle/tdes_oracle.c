@@ -242,17 +242,28 @@ void oracle_des_block(const uint8_t key[8], int decrypt, const uint8_t in[8],
 
 /* ---- Sec. III-B, 3DES equations ---- */
 
+/* The block cipher the modes below run: EDE3 under three keys, or a single
+ * DES pass under the first key (passes == 1). */
 typedef struct {
+    int passes;
     uint8_t rk[3][16][48];
 } tdes_keys;
 
 static void tdes_expand(const uint8_t keys[24], tdes_keys *k) {
+    k->passes = 3;
     for (int i = 0; i < 3; ++i) oracle_des_round_keys(keys + 8 * i, k->rk[i]);
+}
+
+static void des_expand(const uint8_t key[8], tdes_keys *k) {
+    k->passes = 1;
+    oracle_des_round_keys(key, k->rk[0]);
 }
 
 static void tdes_block(const tdes_keys *k, int decrypt, const uint8_t in[8], uint8_t out[8]) {
     uint8_t a[8], b[8];
-    if (!decrypt) { /* E_K3(D_K2(E_K1(P))) */
+    if (k->passes == 1) { /* single DES */
+        des_block(k->rk[0], decrypt, in, out);
+    } else if (!decrypt) { /* E_K3(D_K2(E_K1(P))) */
         des_block(k->rk[0], 0, in, a);
         des_block(k->rk[1], 1, a, b);
         des_block(k->rk[2], 0, b, out);
@@ -288,6 +299,13 @@ void oracle_tdes_ecb(const uint8_t keys[24], int decrypt, const uint8_t *in, uin
     ecb_range(&k, decrypt, in, out, 0, nblocks);
 }
 
+void oracle_des_ecb(const uint8_t key[8], int decrypt, const uint8_t *in, uint8_t *out,
+                    uint64_t nblocks) {
+    tdes_keys k;
+    des_expand(key, &k);
+    ecb_range(&k, decrypt, in, out, 0, nblocks);
+}
+
 static void ctr_range(const tdes_keys *k, uint32_t nonce, uint32_t ctr0, const uint8_t *in,
                       uint8_t *out, uint64_t first, uint64_t end) {
     for (uint64_t i = first; i < end; ++i) {
@@ -308,33 +326,66 @@ int oracle_tdes_ctr(const uint8_t keys[24], uint32_t nonce, uint32_t ctr0, const
     return 0;
 }
 
-void oracle_tdes_cbc_encrypt(const uint8_t keys[24], uint64_t iv, const uint8_t *in,
-                             uint8_t *out, uint64_t nblocks) {
+int oracle_des_ctr(const uint8_t key[8], uint32_t nonce, uint32_t ctr0, const uint8_t *in,
+                   uint8_t *out, uint64_t nblocks) {
+    if ((uint64_t)ctr0 + nblocks > ((uint64_t)1 << 32)) return -1; /* counter would wrap */
     tdes_keys k;
-    tdes_expand(keys, &k);
+    des_expand(key, &k);
+    ctr_range(&k, nonce, ctr0, in, out, 0, nblocks);
+    return 0;
+}
+
+static void cbc_encrypt(const tdes_keys *k, uint64_t iv, const uint8_t *in, uint8_t *out,
+                        uint64_t nblocks) {
     uint8_t prev[8];
     be64_store(iv, prev);
     for (uint64_t i = 0; i < nblocks; ++i) {
         uint8_t x[8];
         for (int t = 0; t < 8; ++t) x[t] = (uint8_t)(in[8 * i + t] ^ prev[t]);
-        tdes_block(&k, 0, x, out + 8 * i);
+        tdes_block(k, 0, x, out + 8 * i);
         memcpy(prev, out + 8 * i, 8);
     }
+}
+
+static void cbc_decrypt(const tdes_keys *k, uint64_t iv, const uint8_t *in, uint8_t *out,
+                        uint64_t nblocks) {
+    uint8_t prev[8];
+    be64_store(iv, prev);
+    for (uint64_t i = 0; i < nblocks; ++i) {
+        uint8_t cur[8], y[8];
+        memcpy(cur, in + 8 * i, 8); /* copy first so that in == out works */
+        tdes_block(k, 1, cur, y);
+        for (int t = 0; t < 8; ++t) out[8 * i + t] = (uint8_t)(y[t] ^ prev[t]);
+        memcpy(prev, cur, 8);
+    }
+}
+
+void oracle_tdes_cbc_encrypt(const uint8_t keys[24], uint64_t iv, const uint8_t *in,
+                             uint8_t *out, uint64_t nblocks) {
+    tdes_keys k;
+    tdes_expand(keys, &k);
+    cbc_encrypt(&k, iv, in, out, nblocks);
 }
 
 void oracle_tdes_cbc_decrypt(const uint8_t keys[24], uint64_t iv, const uint8_t *in,
                              uint8_t *out, uint64_t nblocks) {
     tdes_keys k;
     tdes_expand(keys, &k);
-    uint8_t prev[8];
-    be64_store(iv, prev);
-    for (uint64_t i = 0; i < nblocks; ++i) {
-        uint8_t cur[8], y[8];
-        memcpy(cur, in + 8 * i, 8); /* copy first so that in == out works */
-        tdes_block(&k, 1, cur, y);
-        for (int t = 0; t < 8; ++t) out[8 * i + t] = (uint8_t)(y[t] ^ prev[t]);
-        memcpy(prev, cur, 8);
-    }
+    cbc_decrypt(&k, iv, in, out, nblocks);
+}
+
+void oracle_des_cbc_encrypt(const uint8_t key[8], uint64_t iv, const uint8_t *in, uint8_t *out,
+                            uint64_t nblocks) {
+    tdes_keys k;
+    des_expand(key, &k);
+    cbc_encrypt(&k, iv, in, out, nblocks);
+}
+
+void oracle_des_cbc_decrypt(const uint8_t key[8], uint64_t iv, const uint8_t *in, uint8_t *out,
+                            uint64_t nblocks) {
+    tdes_keys k;
+    des_expand(key, &k);
+    cbc_decrypt(&k, iv, in, out, nblocks);
 }
 
 /* ---- multi-threaded ECB/CTR for the CPU timing baseline only ----

@@ -42,6 +42,17 @@ void oracle_tdes_cbc_encrypt(const uint8_t keys[24], uint64_t iv, const uint8_t 
 void oracle_tdes_cbc_decrypt(const uint8_t keys[24], uint64_t iv, const uint8_t *in,
                              uint8_t *out, uint64_t nblocks);
 
+/* The same modes over single DES under one 8-byte key (Sec. III-B: one
+ * pass of 16 rounds; EDE3 under (K, K, K) gives the same result). */
+void oracle_des_ecb(const uint8_t key[8], int decrypt, const uint8_t *in, uint8_t *out,
+                    uint64_t nblocks);
+int oracle_des_ctr(const uint8_t key[8], uint32_t nonce, uint32_t ctr0, const uint8_t *in,
+                   uint8_t *out, uint64_t nblocks);
+void oracle_des_cbc_encrypt(const uint8_t key[8], uint64_t iv, const uint8_t *in, uint8_t *out,
+                            uint64_t nblocks);
+void oracle_des_cbc_decrypt(const uint8_t key[8], uint64_t iv, const uint8_t *in, uint8_t *out,
+                            uint64_t nblocks);
+
 /* ECB (mode 0 encrypt, 1 decrypt) or CTR (mode 2) split over nthreads host
  * threads; used only to time the CPU baseline.  Returns 0 or -1. */
 int oracle_tdes_parallel(const uint8_t keys[24], int mode, uint32_t nonce, uint32_t ctr0,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -83,6 +84,10 @@ bool aligned16(const void* in, const void* out) {
     return ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
 }
 
+// Calls of at most this many blocks run one block per thread (tdes_small.cu).
+std::atomic<uint64_t> g_small_cutoff{TDES_SMALL_CUTOFF_DEFAULT};
+constexpr int kSmallThreads = 128;  // per CTA: spreads a small call over many SMs
+
 }  // namespace
 
 namespace tdes {
@@ -121,17 +126,20 @@ Geometry geometry_for(uint64_t ntiles, int kernel_id, int device) {
 
 }  // namespace tdes
 
-extern "C" {
+namespace {
 
-int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3[8],
-                      tdes_ks_t** out) {
-    if (out == nullptr || k1 == nullptr || k2 == nullptr || k3 == nullptr)
-        return fail(TDES_EINVAL, "NULL argument to tdes_key_schedule");
-    *out = nullptr;
-    tdes::Keys24 keys;
-    memcpy(keys.b, k1, 8);
-    memcpy(keys.b + 8, k2, 8);
-    memcpy(keys.b + 16, k3, 8);
+// Equal in the 56 bits PC-1 selects (the low bit of each byte is parity).
+bool same_des_key(const uint8_t* a, const uint8_t* b) {
+    for (int i = 0; i < 8; ++i)
+        if ((a[i] ^ b[i]) & 0xFEu) return false;
+    return true;
+}
+
+// Builds the device tables for `keys` with `stages` DES passes.  A
+// single-DES schedule is given (K, K, K): its one-pass tables read the
+// first key, and its scalar round-key groups are EDE3's under (K, K, K),
+// whose first 16 rounds are DES_K's in both directions.
+int make_schedule(tdes::Keys24& keys, int stages, tdes_ks_t** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -146,6 +154,7 @@ int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3
         return fail(TDES_ENOMEM, "host allocation failed");
     }
     ks->device = dev;
+    ks->stages = stages;
     ks->mem = mem;
     ks->tab[0] = static_cast<uint32_t*>(mem);
     ks->tab[1] = ks->tab[0] + tdes::kTableWords;
@@ -154,7 +163,8 @@ int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3
     cudaStream_t s = nullptr;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
-        e = tdes::launch_keysched(keys, ks->tab[0], ks->tab[1], ks->chunk[0], ks->chunk[1], s);
+        e = tdes::launch_keysched(keys, stages, ks->tab[0], ks->tab[1], ks->chunk[0],
+                                  ks->chunk[1], s);
         cudaError_t e2 = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = e2;
         cudaStreamDestroy(s);
@@ -167,6 +177,40 @@ int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3
     }
     *out = ks;
     return TDES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdes_key_schedule(const uint8_t k1[8], const uint8_t k2[8], const uint8_t k3[8],
+                      tdes_ks_t** out) {
+    if (out == nullptr || k1 == nullptr || k2 == nullptr || k3 == nullptr)
+        return fail(TDES_EINVAL, "NULL argument to tdes_key_schedule");
+    *out = nullptr;
+    // E_K3(D_K2(E_K1(x))) is E_K3(x) when K1 = K2 and E_K1(x) when K2 = K3.
+    const uint8_t* single = same_des_key(k1, k2) ? k3 : same_des_key(k2, k3) ? k1 : nullptr;
+    tdes::Keys24 keys;
+    const uint8_t* parts[3] = {k1, k2, k3};
+    for (int i = 0; i < 3; ++i) memcpy(keys.b + 8 * i, single ? single : parts[i], 8);
+    return make_schedule(keys, single ? 1 : 3, out);
+}
+
+int tdes_key_schedule_2key(const uint8_t k1[8], const uint8_t k2[8], tdes_ks_t** out) {
+    return tdes_key_schedule(k1, k2, k1, out);
+}
+
+int tdes_des_key_schedule(const uint8_t k[8], tdes_ks_t** out) {
+    if (out == nullptr || k == nullptr) return fail(TDES_EINVAL, "NULL argument to tdes_des_key_schedule");
+    *out = nullptr;
+    tdes::Keys24 keys;
+    for (int i = 0; i < 3; ++i) memcpy(keys.b + 8 * i, k, 8);
+    return make_schedule(keys, 1, out);
+}
+
+int tdes_key_schedule_stages(const tdes_ks_t* ks) {
+    if (ks == nullptr) return fail(TDES_EINVAL, "key schedule is NULL");
+    return ks->stages;
 }
 
 void tdes_key_free(tdes_ks_t* ks) {
@@ -184,10 +228,16 @@ static int ecb(const tdes_ks_t* ks, int dir, const void* in, void* out, size_t n
     uint64_t nblocks = 0;
     int rc = check_call(ks, in, out, nbytes, &nblocks);
     if (rc != TDES_OK || nblocks == 0) return rc;
-    const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
-    const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kEcb, ks->device);
-    cudaError_t e = tdes::launch_ecb(ks->tab[dir], in, out, nblocks, aligned16(in, out), g,
-                                     reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (nblocks <= g_small_cutoff.load(std::memory_order_relaxed)) {
+        e = tdes::launch_small(ks->chunk[dir], ks->stages, tdes::kSmallEcb, 0, in, out, nblocks,
+                               kSmallThreads, s);
+    } else {
+        const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+        const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kEcb, ks->device);
+        e = tdes::launch_ecb(ks->tab[dir], ks->stages, in, out, nblocks, aligned16(in, out), g, s);
+    }
     return e == cudaSuccess ? TDES_OK : cuda_fail(e, "ECB kernel launch");
 }
 
@@ -209,11 +259,17 @@ int tdes_ctr_crypt(const tdes_ks_t* ks, uint32_t nonce, uint32_t ctr0, const voi
     if ((uint64_t)ctr0 + nblocks > (1ull << 32))
         return fail(TDES_EINVAL, "CTR counter would wrap: ctr0 %u + %llu blocks > 2^32", ctr0,
                     (unsigned long long)nblocks);
-    const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
-    const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kCtr, ks->device);
-    cudaError_t e = tdes::launch_ctr(ks->tab[0], nonce, ctr0, in, out, nblocks,
-                                     aligned16(in, out), g,
-                                     reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (nblocks <= g_small_cutoff.load(std::memory_order_relaxed)) {
+        e = tdes::launch_small(ks->chunk[0], ks->stages, tdes::kSmallCtr,
+                               (uint64_t)nonce << 32 | ctr0, in, out, nblocks, kSmallThreads, s);
+    } else {
+        const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+        const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kCtr, ks->device);
+        e = tdes::launch_ctr(ks->tab[0], ks->stages, nonce, ctr0, in, out, nblocks,
+                             aligned16(in, out), g, s);
+    }
     return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CTR kernel launch");
 }
 
@@ -223,6 +279,13 @@ int tdes_cbc_decrypt(const tdes_ks_t* ks, uint64_t iv, const void* in, void* out
     int rc = check_call(ks, in, out, nbytes, &nblocks);
     if (rc != TDES_OK || nblocks == 0) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // one block per thread; in place only as a single CTA (all reads before writes)
+    if (nblocks <= g_small_cutoff.load(std::memory_order_relaxed) && (in != out || nblocks <= 1024)) {
+        const int threads = in != out ? kSmallThreads : (int)((nblocks + 31) / 32 * 32);
+        cudaError_t e = tdes::launch_small(ks->chunk[1], ks->stages, tdes::kSmallCbcDec, iv, in,
+                                           out, nblocks, threads, s);
+        return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CBC-decrypt kernel launch");
+    }
     const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
     uint64_t* halo = nullptr;
     cudaError_t e = cudaSuccess;
@@ -233,7 +296,8 @@ int tdes_cbc_decrypt(const tdes_ks_t* ks, uint64_t iv, const void* in, void* out
     }
     if (e == cudaSuccess) {
         const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kCbcDec, ks->device);
-        e = tdes::launch_cbc_dec(ks->tab[1], iv, in, out, nblocks, halo, aligned16(in, out), g, s);
+        e = tdes::launch_cbc_dec(ks->tab[1], ks->stages, iv, in, out, nblocks, halo,
+                                 aligned16(in, out), g, s);
     }
     if (halo != nullptr) {
         cudaError_t e2 = cudaFreeAsync(halo, s);
@@ -247,7 +311,7 @@ int tdes_cbc_encrypt(const tdes_ks_t* ks, uint64_t iv, const void* in, void* out
     uint64_t nblocks = 0;
     int rc = check_call(ks, in, out, nbytes, &nblocks);
     if (rc != TDES_OK || nblocks == 0) return rc;
-    cudaError_t e = tdes::launch_cbc_enc(ks->chunk[0], iv, in, out, nblocks,
+    cudaError_t e = tdes::launch_cbc_enc(ks->chunk[0], ks->stages, iv, in, out, nblocks,
                                          reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? TDES_OK : cuda_fail(e, "CBC-encrypt kernel launch");
 }
@@ -306,7 +370,8 @@ int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, v
         if (e == cudaSuccess) e = cudaStreamWaitEvent(scomp, ev_in[b], 0);
         if (e == cudaSuccess) {
             const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kEcb, ks->device);
-            e = tdes::launch_ecb(ks->tab[decrypt ? 1 : 0], buf, buf, nblocks, true, g, scomp);
+            e = tdes::launch_ecb(ks->tab[decrypt ? 1 : 0], ks->stages, buf, buf, nblocks, true,
+                                 g, scomp);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev_k[b], scomp);
         what = "device-to-host copy";
@@ -334,6 +399,10 @@ int tdes_ecb_crypt_host(const tdes_ks_t* ks, int decrypt, const void* host_in, v
 }
 
 int tdes_sbox_gate_count(void) { return tdes::sbox_gate_count(); }
+
+uint64_t tdes_set_small_cutoff(uint64_t nblocks) {
+    return g_small_cutoff.exchange(nblocks, std::memory_order_relaxed);
+}
 
 const char* tdes_strerror(int status) {
     switch (status) {

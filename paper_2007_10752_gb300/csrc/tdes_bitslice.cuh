@@ -106,42 +106,57 @@ TDES_HD void xor_planes(uint32_t (&H)[32], const uint32_t* __restrict__ k) {
 // Each key-mask pass (prologue, the two re-keyings, epilogue) touches only the
 // half whose stored key bits change there; the generator checks that the
 // other half's constants are zero and says which half it is (TDES_*_HALF_R).
-#define TDES_KEY_PASS(NAME, BASE)                                  \
-    do {                                                           \
-        if (TDES_##NAME##_HALF_R) xor_planes(Rh, tab + (BASE) + 32); \
-        else xor_planes(Lh, tab + (BASE));                         \
+#define TDES_KEY_PASS(NAME, BASE)                           \
+    do {                                                    \
+        if (NAME##_HALF_R) xor_planes(Rh, tab + (BASE) + 32); \
+        else xor_planes(Lh, tab + (BASE));                  \
     } while (0)
 
+//
+// STAGES = 1 runs a single DES pass (16 rounds) on a single-DES table
+// (TDES1_TABLE_WORDS words: prologue, 16 rounds, epilogue).  The first
+// pass of EDE3 targets the halves in the same order, so tdes_fp applies.
+template <int STAGES = 3>
 TDES_HD void tdes_rounds(uint32_t (&Lh)[32], uint32_t (&Rh)[32], const uint32_t* __restrict__ tab) {
-    TDES_KEY_PASS(PRO, TDES_TABLE_PRO);
+    static_assert(STAGES == 1 || STAGES == 3, "one DES pass or EDE3");
+    if (STAGES == 1) {
+        TDES_KEY_PASS(TDES1_PRO, TDES_TABLE_PRO);
+    } else {
+        TDES_KEY_PASS(TDES_PRO, TDES_TABLE_PRO);
+    }
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {  // first DES pass: rounds 0..15
         tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it));
         tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it + 1));
     }
-    TDES_KEY_PASS(REKEY16, TDES_TABLE_REKEY16);
+    if (STAGES == 1) {
+        TDES_KEY_PASS(TDES1_EPI, TDES1_TABLE_EPI);
+        return;
+    }
+    TDES_KEY_PASS(TDES_REKEY16, TDES_TABLE_REKEY16);
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {  // second pass: the XOR target repeats at its start
         tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (16 + 2 * it));
         tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (17 + 2 * it));
     }
-    TDES_KEY_PASS(REKEY32, TDES_TABLE_REKEY32);
+    TDES_KEY_PASS(TDES_REKEY32, TDES_TABLE_REKEY32);
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {  // third pass
         tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (32 + 2 * it));
         tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (33 + 2 * it));
     }
-    TDES_KEY_PASS(EPI, TDES_TABLE_EPI);
+    TDES_KEY_PASS(TDES_EPI, TDES_TABLE_EPI);
 }
 
 // 32 blocks: A0[s], A1[s] are the first and second little-endian 32-bit
 // words of block s on entry and of its result on return.
+template <int STAGES = 3>
 TDES_HD void tdes_process32(uint32_t (&A0)[32], uint32_t (&A1)[32], const uint32_t* __restrict__ tab) {
     transpose32(A0);
     transpose32(A1);
     uint32_t Lh[32], Rh[32];
     tdes_ip(A0, A1, Lh, Rh);
-    tdes_rounds(Lh, Rh, tab);
+    tdes_rounds<STAGES>(Lh, Rh, tab);
     tdes_fp(Lh, Rh, A0, A1);
     transpose32(A0);
     transpose32(A1);
@@ -216,7 +231,9 @@ TDES_HD uint64_t permute64_nib(uint64_t v, const uint64_t* __restrict__ tab) {
 // tables (ipn/fpn: 16 x 16 words each) instead of bit loops.  The 16 rounds
 // of a DES pass are unrolled by two so that the halves alternate in place,
 // and each round's key words are loaded one round ahead, off the chain of
-// dependent operations that sets the latency of a block.
+// dependent operations that sets the latency of a block.  ROUNDS = 16 runs
+// single DES on the first 16 rounds' key words.
+template <int ROUNDS = 48>
 TDES_HD uint64_t tdes_block_scalar_nib(uint64_t v, const uint32_t* __restrict__ sp,
                                        const uint32_t* __restrict__ keys,
                                        const uint64_t* __restrict__ ipn,
@@ -224,10 +241,10 @@ TDES_HD uint64_t tdes_block_scalar_nib(uint64_t v, const uint32_t* __restrict__ 
     v = permute64_nib(v, ipn);
     uint32_t L = (uint32_t)(v >> 32), R = (uint32_t)v;
     uint32_t ke = keys[0], ko = keys[1];
-    for (int r = 0; r < 48; r += 2) {
+    for (int r = 0; r < ROUNDS; r += 2) {
         const uint32_t ke1 = keys[2 * r + 2], ko1 = keys[2 * r + 3];
         L ^= tdes_f_scalar(R, ke, ko, sp);
-        const int rn = r + 2 < 48 ? r + 2 : r;  // the last prefetch rereads round 46
+        const int rn = r + 2 < ROUNDS ? r + 2 : r;  // the last prefetch rereads the last pair
         ke = keys[2 * rn];
         ko = keys[2 * rn + 1];
         R ^= tdes_f_scalar(L, ke1, ko1, sp);
@@ -257,14 +274,16 @@ __device__ __forceinline__ uint32_t lane_bit(uint64_t v, uint32_t src) {
     return (uint32_t)(v >> (63u - src)) & 1u;
 }
 
+// ROUNDS = 16 runs single DES on the first 16 rounds' key words.
+template <int ROUNDS = 48>
 __device__ __forceinline__ uint64_t tdes_block_warp(uint64_t v, const LaneConsts& c,
                                                     const uint8_t* __restrict__ keys) {
     uint32_t L = __ballot_sync(0xFFFFFFFFu, lane_bit(v, c.ip_hi));
     uint32_t R = __ballot_sync(0xFFFFFFFFu, lane_bit(v, c.ip_lo));
     uint32_t k = keys[c.keypos];
 #pragma unroll 2
-    for (int r = 0; r < 48; ++r) {
-        const uint32_t kn = keys[8 * (r + 1 < 48 ? r + 1 : r) + c.keypos];
+    for (int r = 0; r < ROUNDS; ++r) {
+        const uint32_t kn = keys[8 * (r + 1 < ROUNDS ? r + 1 : r) + c.keypos];
         const uint32_t x = ((rotr32(R, (int)c.rot) & 63u) ^ k);
         const uint32_t w = (x & 32u) ? c.mhi : c.mlo;
         const uint32_t f = __ballot_sync(0xFFFFFFFFu, (w >> (x & 31u)) & 1u);

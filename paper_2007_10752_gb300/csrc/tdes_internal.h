@@ -8,6 +8,7 @@
 // The library's key-schedule object (opaque tdes_ks_t in include/tdes.h).
 struct tdes_ks {
     int device;
+    int stages;             // DES passes per block: 3 (EDE3) or 1 (single DES)
     void* mem;              // one cudaMalloc holding everything below
     uint32_t* tab[2];       // bitsliced round-constant tables: [0] encrypt, [1] decrypt
     uint8_t* chunk[2];      // scalar-path round-key groups: [0] encrypt, [1] decrypt
@@ -42,18 +43,28 @@ Geometry geometry_for(uint64_t ntiles, int kernel_id, int device);
 
 enum KernelId { kEcb = 0, kCtr = 1, kCbcDec = 2, kNumKernels = 3 };
 
-cudaError_t launch_keysched(const Keys24& keys, uint32_t* tab_enc, uint32_t* tab_dec,
+// `stages` (1 or 3) selects the single-DES or the EDE3 kernels; the tables
+// passed must have been built for the same number of stages.
+cudaError_t launch_keysched(const Keys24& keys, int stages, uint32_t* tab_enc, uint32_t* tab_dec,
                             uint8_t* chunk_enc, uint8_t* chunk_dec, cudaStream_t s);
-cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t nblocks,
-                       bool vec16, Geometry g, cudaStream_t s);
-cudaError_t launch_ctr(const uint32_t* tab_enc, uint32_t nonce, uint32_t ctr0, const void* in,
-                       void* out, uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s);
+cudaError_t launch_ecb(const uint32_t* tab, int stages, const void* in, void* out,
+                       uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s);
+cudaError_t launch_ctr(const uint32_t* tab_enc, int stages, uint32_t nonce, uint32_t ctr0,
+                       const void* in, void* out, uint64_t nblocks, bool vec16, Geometry g,
+                       cudaStream_t s);
 cudaError_t launch_cbc_halo(const void* in, uint64_t* halo, uint64_t nblocks, cudaStream_t s);
-cudaError_t launch_cbc_dec(const uint32_t* tab_dec, uint64_t iv, const void* in, void* out,
-                           uint64_t nblocks, const uint64_t* halo, bool vec16, Geometry g,
-                           cudaStream_t s);
-cudaError_t launch_cbc_enc(const uint8_t* chunk_enc, uint64_t iv, const void* in, void* out,
-                           uint64_t nblocks, cudaStream_t s);
+cudaError_t launch_cbc_dec(const uint32_t* tab_dec, int stages, uint64_t iv, const void* in,
+                           void* out, uint64_t nblocks, const uint64_t* halo, bool vec16,
+                           Geometry g, cudaStream_t s);
+cudaError_t launch_cbc_enc(const uint8_t* chunk_enc, int stages, uint64_t iv, const void* in,
+                           void* out, uint64_t nblocks, cudaStream_t s);
+
+// One block per thread (tdes_small.cu), for calls too small to fill the GPU
+// with bitsliced tiles.  chunks: the call's scalar round-key groups of the
+// wanted direction; iv: the CBC IV, or nonce << 32 | ctr0 for CTR.
+enum SmallMode { kSmallEcb = 0, kSmallCtr = 1, kSmallCbcDec = 2 };
+cudaError_t launch_small(const uint8_t* chunks, int stages, int mode, uint64_t iv, const void* in,
+                         void* out, uint64_t nblocks, int threads, cudaStream_t s);
 
 // Occupancy (CTAs per SM) of a bitsliced kernel at kWideWarps warps per CTA.
 int wide_ctas_per_sm(int kernel_id);

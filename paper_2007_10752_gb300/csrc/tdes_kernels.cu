@@ -20,41 +20,52 @@ static_assert(kTableWords == TDES_TABLE_WORDS, "table size mismatch with the gen
 static_assert(kChunkBytes == TDES_SUBKEY_WORDS, "chunk size mismatch");
 
 __device__ const uint8_t kRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
+__device__ const uint8_t kRecipe1[2][TDES1_TABLE_WORDS][3] = TDES1_RECIPE_INIT;
 __device__ const uint8_t kSubkeyBits[2][48][48] = TDES_SUBKEY_INIT;
 
 
 int sbox_gate_count() { return TDES_SBOX_GATES; }
 
 // ------------------------------------------------------------ key schedule
-// One thread per output word: 2 bitsliced tables then 2 chunk tables.
-__global__ void tdes_keysched_kernel(Keys24 keys, uint32_t* __restrict__ tab_enc,
+// One thread per output word: 2 bitsliced tables then 2 chunk tables.  A
+// single-DES schedule (stages = 1) gets the short tables of the one-pass
+// recipe; its chunk tables are those of EDE3 under (K, K, K), whose first 16
+// rounds are the rounds of DES_K in both directions.
+__global__ void tdes_keysched_kernel(Keys24 keys, int stages, uint32_t* __restrict__ tab_enc,
                                      uint32_t* __restrict__ tab_dec, uint8_t* __restrict__ ch_enc,
                                      uint8_t* __restrict__ ch_dec) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < 2 * TDES_TABLE_WORDS) {
-        const int dir = e / TDES_TABLE_WORDS, w = e % TDES_TABLE_WORDS;
-        (dir ? tab_dec : tab_enc)[w] = tdes_table_word(keys.b, kRecipe[dir][w]);
-    } else if (e < 2 * TDES_TABLE_WORDS + 2 * TDES_SUBKEY_WORDS) {
-        const int f = e - 2 * TDES_TABLE_WORDS;
+    const int nw = stages == 1 ? TDES1_TABLE_WORDS : TDES_TABLE_WORDS;
+    if (e < 2 * nw) {
+        const int dir = e / nw, w = e % nw;
+        (dir ? tab_dec : tab_enc)[w] = tdes_table_word(
+            keys.b, stages == 1 ? kRecipe1[dir][w] : kRecipe[dir][w]);
+    } else if (e < 2 * nw + 2 * TDES_SUBKEY_WORDS) {
+        const int f = e - 2 * nw;
         const int dir = f / TDES_SUBKEY_WORDS, c = f % TDES_SUBKEY_WORDS;
         const int r = c / 8, g = c % 8;
         (dir ? ch_dec : ch_enc)[c] = tdes_subkey_chunk(keys.b, &kSubkeyBits[dir][r][6 * g]);
     }
 }
 
-cudaError_t launch_keysched(const Keys24& keys, uint32_t* tab_enc, uint32_t* tab_dec,
+cudaError_t launch_keysched(const Keys24& keys, int stages, uint32_t* tab_enc, uint32_t* tab_dec,
                             uint8_t* chunk_enc, uint8_t* chunk_dec, cudaStream_t s) {
     const int n = 2 * TDES_TABLE_WORDS + 2 * TDES_SUBKEY_WORDS;
-    tdes_keysched_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, tab_enc, tab_dec, chunk_enc,
-                                                          chunk_dec);
+    tdes_keysched_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, stages, tab_enc, tab_dec,
+                                                          chunk_enc, chunk_dec);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ tile helpers
 
+// Words of the bitsliced table of a schedule with STAGES DES passes.
+template <int STAGES>
+constexpr int table_words() { return STAGES == 1 ? TDES1_TABLE_WORDS : TDES_TABLE_WORDS; }
+
+template <int STAGES>
 __device__ __forceinline__ void stage_table(uint32_t* __restrict__ dst,
                                             const uint32_t* __restrict__ src) {
-    for (int i = 4 * threadIdx.x; i < TDES_TABLE_WORDS; i += 4 * blockDim.x)
+    for (int i = 4 * threadIdx.x; i < table_words<STAGES>(); i += 4 * blockDim.x)
         *reinterpret_cast<uint4*>(dst + i) = __ldg(reinterpret_cast<const uint4*>(src + i));
 }
 
@@ -128,13 +139,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 
-template <bool VEC>
+template <bool VEC, int STAGES>
 __global__ void __launch_bounds__(256, 2)
 tdes_ecb_kernel(const uint32_t* __restrict__ table, const uint8_t* in, uint8_t* out,
                 uint64_t nblocks) {
-    __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
+    __shared__ __align__(16) uint32_t tab[table_words<STAGES>()];
     extern __shared__ __align__(16) uint4 ecb_data[];  // kCtrWarpBytes per warp (VEC only)
-    stage_table(tab, table);
+    stage_table<STAGES>(tab, table);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = blockDim.x >> 5;
@@ -173,30 +184,61 @@ tdes_ecb_kernel(const uint32_t* __restrict__ table, const uint8_t* in, uint8_t* 
         } else {
             load_tile<VEC>(in, (uint64_t)t * kTileBlocks, nblocks, lane, A0, A1);
         }
-        tdes_process32(A0, A1, tab);
+        tdes_process32<STAGES>(A0, A1, tab);
         store_tile<VEC>(out, (uint64_t)t * kTileBlocks, nblocks, lane, A0, A1);
     }
 }
 
-static std::atomic<bool> ecb_smem_ready[64];
+// The kernels that stage data tiles take up to kWideWarps x 8 KiB of dynamic
+// shared memory, above the default limit: raise it once per device.
+template <bool VEC, int STAGES>
+__global__ void tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr0,
+                                const uint8_t* in, uint8_t* out, uint64_t nblocks);
 
-cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t nblocks,
-                       bool vec16, Geometry g, cudaStream_t s) {
+static std::atomic<bool> dyn_smem_ready[64];
+
+static cudaError_t ensure_dyn_smem() {
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !ecb_smem_ready[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(tdes_ecb_kernel<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kWideWarps * kCtrWarpBytes);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && dyn_smem_ready[dev]) return cudaSuccess;
+    const int dyn = kWideWarps * kCtrWarpBytes;
+    const void* fns[] = {
+        reinterpret_cast<const void*>(tdes_ecb_kernel<true, 3>),
+        reinterpret_cast<const void*>(tdes_ecb_kernel<true, 1>),
+        reinterpret_cast<const void*>(tdes_ctr_kernel<true, 3>),
+        reinterpret_cast<const void*>(tdes_ctr_kernel<false, 3>),
+        reinterpret_cast<const void*>(tdes_ctr_kernel<true, 1>),
+        reinterpret_cast<const void*>(tdes_ctr_kernel<false, 1>),
+    };
+    for (const void* f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
-        ecb_smem_ready[dev] = true;
     }
+    if (dev >= 0 && dev < 64) dyn_smem_ready[dev] = true;
+    return cudaSuccess;
+}
+
+template <int STAGES>
+static void ecb_launch(const uint32_t* tab, const void* in, void* out, uint64_t nblocks,
+                       bool vec16, Geometry g, cudaStream_t s) {
     if (vec16)
-        tdes_ecb_kernel<true><<<g.grid, g.threads, (size_t)(g.threads / 32) * kCtrWarpBytes, s>>>(
-            tab, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks);
+        tdes_ecb_kernel<true, STAGES>
+            <<<g.grid, g.threads, (size_t)(g.threads / 32) * kCtrWarpBytes, s>>>(
+                tab, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks);
     else
-        tdes_ecb_kernel<false><<<g.grid, g.threads, 0, s>>>(
+        tdes_ecb_kernel<false, STAGES><<<g.grid, g.threads, 0, s>>>(
             tab, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks);
+}
+
+cudaError_t launch_ecb(const uint32_t* tab, int stages, const void* in, void* out,
+                       uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s) {
+    cudaError_t e = ensure_dyn_smem();
+    if (e != cudaSuccess) return e;
+    if (stages == 1)
+        ecb_launch<1>(tab, in, out, nblocks, vec16, g, s);
+    else
+        ecb_launch<3>(tab, in, out, nblocks, vec16, g, s);
     return cudaGetLastError();
 }
 
@@ -205,13 +247,13 @@ cudaError_t launch_ecb(const uint32_t* tab, const void* in, void* out, uint64_t 
 // registers.  The data tile the keystream is XORed into is copied into the
 // warp's 8 KiB of shared memory with cp.async before the rounds start, so
 // its memory latency hides behind them.
-template <bool VEC>
+template <bool VEC, int STAGES>
 __global__ void __launch_bounds__(256, 2)
 tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr0,
                 const uint8_t* in, uint8_t* out, uint64_t nblocks) {
-    __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
+    __shared__ __align__(16) uint32_t tab[table_words<STAGES>()];
     extern __shared__ __align__(16) uint4 ctr_data[];  // kCtrWarpBytes per warp
-    stage_table(tab, table);
+    stage_table<STAGES>(tab, table);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = blockDim.x >> 5;
@@ -237,7 +279,7 @@ tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr
                 A0[2 * j + h] = nw;
                 A1[2 * j + h] = bswap32(ctr0 + b);
             }
-        tdes_process32(A0, A1, tab);
+        tdes_process32<STAGES>(A0, A1, tab);
         if (full) {
             cp_async_wait_all();
             uint4* q = reinterpret_cast<uint4*>(out) + (b0 >> 1) + lane;
@@ -264,31 +306,29 @@ tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr
     }
 }
 
-static std::atomic<bool> ctr_smem_ready[64];
-
-cudaError_t launch_ctr(const uint32_t* tab_enc, uint32_t nonce, uint32_t ctr0, const void* in,
+template <int STAGES>
+static void ctr_launch(const uint32_t* tab_enc, uint32_t nonce, uint32_t ctr0, const void* in,
                        void* out, uint64_t nblocks, bool vec16, Geometry g, cudaStream_t s) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !ctr_smem_ready[dev]) {
-        const int dyn = kWideWarps * kCtrWarpBytes;
-        cudaError_t e = cudaFuncSetAttribute(tdes_ctr_kernel<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tdes_ctr_kernel<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e != cudaSuccess) return e;
-        ctr_smem_ready[dev] = true;
-    }
     const size_t dyn = (size_t)(g.threads / 32) * kCtrWarpBytes;
     if (vec16)
-        tdes_ctr_kernel<true><<<g.grid, g.threads, dyn, s>>>(
+        tdes_ctr_kernel<true, STAGES><<<g.grid, g.threads, dyn, s>>>(
             tab_enc, nonce, ctr0, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out),
             nblocks);
     else
-        tdes_ctr_kernel<false><<<g.grid, g.threads, dyn, s>>>(
+        tdes_ctr_kernel<false, STAGES><<<g.grid, g.threads, dyn, s>>>(
             tab_enc, nonce, ctr0, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out),
             nblocks);
+}
+
+cudaError_t launch_ctr(const uint32_t* tab_enc, int stages, uint32_t nonce, uint32_t ctr0,
+                       const void* in, void* out, uint64_t nblocks, bool vec16, Geometry g,
+                       cudaStream_t s) {
+    cudaError_t e = ensure_dyn_smem();
+    if (e != cudaSuccess) return e;
+    if (stages == 1)
+        ctr_launch<1>(tab_enc, nonce, ctr0, in, out, nblocks, vec16, g, s);
+    else
+        ctr_launch<3>(tab_enc, nonce, ctr0, in, out, nblocks, vec16, g, s);
     return cudaGetLastError();
 }
 
@@ -313,12 +353,12 @@ cudaError_t launch_cbc_halo(const void* in, uint64_t* halo, uint64_t nblocks, cu
 // the rounds: a lane's own blocks and its neighbours' in the same tile are
 // still intact (the warp stores only after __syncwarp); the block before the
 // tile comes from `halo` when decrypting in place, else from the input.
-template <bool VEC>
+template <bool VEC, int STAGES>
 __global__ void __launch_bounds__(256, 2)
 tdes_cbc_dec_kernel(const uint32_t* __restrict__ table, uint64_t iv, const uint8_t* in,
                     uint8_t* out, uint64_t nblocks, const uint64_t* __restrict__ halo) {
-    __shared__ __align__(16) uint32_t tab[TDES_TABLE_WORDS];
-    stage_table(tab, table);
+    __shared__ __align__(16) uint32_t tab[table_words<STAGES>()];
+    stage_table<STAGES>(tab, table);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = blockDim.x >> 5;
@@ -330,7 +370,7 @@ tdes_cbc_dec_kernel(const uint32_t* __restrict__ table, uint64_t iv, const uint8
         const uint64_t b0 = t * kTileBlocks;
         uint32_t A0[32], A1[32];
         load_tile<VEC>(in, b0, nblocks, lane, A0, A1);
-        tdes_process32(A0, A1, tab);
+        tdes_process32<STAGES>(A0, A1, tab);
         const uint2* ct = c + b0;  // this tile's ciphertext, 32-bit indices below
         const uint32_t nvalid = (uint32_t)min((uint64_t)kTileBlocks, nblocks - b0);
 #pragma unroll
@@ -360,17 +400,27 @@ tdes_cbc_dec_kernel(const uint32_t* __restrict__ table, uint64_t iv, const uint8
     }
 }
 
-cudaError_t launch_cbc_dec(const uint32_t* tab_dec, uint64_t iv, const void* in, void* out,
+template <int STAGES>
+static void cbc_dec_launch(const uint32_t* tab_dec, uint64_t iv, const void* in, void* out,
                            uint64_t nblocks, const uint64_t* halo, bool vec16, Geometry g,
                            cudaStream_t s) {
     if (vec16)
-        tdes_cbc_dec_kernel<true><<<g.grid, g.threads, 0, s>>>(
+        tdes_cbc_dec_kernel<true, STAGES><<<g.grid, g.threads, 0, s>>>(
             tab_dec, iv, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks,
             halo);
     else
-        tdes_cbc_dec_kernel<false><<<g.grid, g.threads, 0, s>>>(
+        tdes_cbc_dec_kernel<false, STAGES><<<g.grid, g.threads, 0, s>>>(
             tab_dec, iv, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks,
             halo);
+}
+
+cudaError_t launch_cbc_dec(const uint32_t* tab_dec, int stages, uint64_t iv, const void* in,
+                           void* out, uint64_t nblocks, const uint64_t* halo, bool vec16,
+                           Geometry g, cudaStream_t s) {
+    if (stages == 1)
+        cbc_dec_launch<1>(tab_dec, iv, in, out, nblocks, halo, vec16, g, s);
+    else
+        cbc_dec_launch<3>(tab_dec, iv, in, out, nblocks, halo, vec16, g, s);
     return cudaGetLastError();
 }
 
@@ -395,6 +445,7 @@ __device__ __forceinline__ LaneConsts lane_consts(uint32_t lane) {
     return c;
 }
 
+template <int ROUNDS>
 __global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64_t iv,
                                     const uint8_t* in, uint8_t* out, uint64_t nblocks) {
     __shared__ __align__(16) uint8_t keys[TDES_SUBKEY_WORDS];
@@ -410,15 +461,19 @@ __global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64
     for (uint64_t i = 0; i < nblocks; ++i) {
         const uint64_t x = bswap64(next) ^ prev;
         if (i + 1 < nblocks) next = p[i + 1];
-        prev = tdes_block_warp(x, c, keys);
+        prev = tdes_block_warp<ROUNDS>(x, c, keys);
         if (lane == 0) q[i] = bswap64(prev);
     }
 }
 
-cudaError_t launch_cbc_enc(const uint8_t* chunk_enc, uint64_t iv, const void* in, void* out,
-                           uint64_t nblocks, cudaStream_t s) {
-    tdes_cbc_enc_kernel<<<1, 32, 0, s>>>(chunk_enc, iv, static_cast<const uint8_t*>(in),
-                                         static_cast<uint8_t*>(out), nblocks);
+cudaError_t launch_cbc_enc(const uint8_t* chunk_enc, int stages, uint64_t iv, const void* in,
+                           void* out, uint64_t nblocks, cudaStream_t s) {
+    if (stages == 1)
+        tdes_cbc_enc_kernel<16><<<1, 32, 0, s>>>(chunk_enc, iv, static_cast<const uint8_t*>(in),
+                                                 static_cast<uint8_t*>(out), nblocks);
+    else
+        tdes_cbc_enc_kernel<48><<<1, 32, 0, s>>>(chunk_enc, iv, static_cast<const uint8_t*>(in),
+                                                 static_cast<uint8_t*>(out), nblocks);
     return cudaGetLastError();
 }
 
@@ -429,23 +484,19 @@ int wide_ctas_per_sm(int kernel_id) {
     cudaError_t e = cudaSuccess;
     switch (kernel_id) {
         case kEcb:
-            e = cudaFuncSetAttribute(tdes_ecb_kernel<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kWideWarps * kCtrWarpBytes);
+            e = ensure_dyn_smem();
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ecb_kernel<true>, threads,
-                                                                  kWideWarps * kCtrWarpBytes);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &n, tdes_ecb_kernel<true, 3>, threads, kWideWarps * kCtrWarpBytes);
             break;
         case kCtr:
-            e = cudaFuncSetAttribute(tdes_ctr_kernel<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kWideWarps * kCtrWarpBytes);
+            e = ensure_dyn_smem();
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_ctr_kernel<true>, threads,
-                                                                  kWideWarps * kCtrWarpBytes);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &n, tdes_ctr_kernel<true, 3>, threads, kWideWarps * kCtrWarpBytes);
             break;
         default:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_cbc_dec_kernel<true>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_cbc_dec_kernel<true, 3>,
                                                               threads, 0);
             break;
     }

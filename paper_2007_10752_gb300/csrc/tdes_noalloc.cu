@@ -100,7 +100,7 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t* ks, uint64_t iv, const void* in, v
     }
     const tdes::Geometry g = tdes::geometry_for(ntiles, tdes::kCbcDec, ks->device);
     const bool vec16 = ((a | b) & 15u) == 0;
-    e = tdes::launch_cbc_dec(ks->tab[1], iv, in, out, nblocks, halo, vec16, g, s);
+    e = tdes::launch_cbc_dec(ks->tab[1], ks->stages, iv, in, out, nblocks, halo, vec16, g, s);
     if (e != cudaSuccess) return fail(TDES_ECUDA, "CBC-decrypt kernel: %s", cudaGetErrorString(e));
     return TDES_OK;
 }

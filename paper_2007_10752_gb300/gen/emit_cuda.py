@@ -40,11 +40,22 @@ OUT_DIR = os.path.join(os.path.dirname(HERE), "csrc", "generated")
 OUT = os.path.join(OUT_DIR, "tdes_generated.cuh")
 
 # ---- table layout (32-bit words) ----
+# A table serves `stages` DES passes (3: EDE3; 1: single DES, which EDE3
+# reduces to when two adjacent keys are equal, Sec. III-B).
 PRO = 0                 # 64 words: prologue XOR of L (0..31) and R (32..63), by half bit
-ROUND0 = 64             # 48 rounds x 64 words; S-box g: 8g + [c0 c1 c2 c3 d1 d2 m1 m2]
-REKEY = (64 + 48 * 64, 64 + 48 * 64 + 64)   # re-keying of the source half at rounds 16, 32
-EPI = 64 + 48 * 64 + 128                    # 64 words: final un-keying of L, R
-TABLE_WORDS = EPI + 64
+ROUND0 = 64             # 16*stages rounds x 64 words; S-box g: 8g + [c0 c1 c2 c3 d1 d2 m1 m2]
+
+
+def layout(stages=3):
+    """Word offsets of the passes of a table for `stages` DES passes:
+    (rekey offsets at the stage boundaries, epilogue offset, table words)."""
+    nr = 16 * stages
+    rekey = tuple(ROUND0 + nr * 64 + 64 * i for i in range(stages - 1))
+    epi = ROUND0 + nr * 64 + 64 * (stages - 1)
+    return rekey, epi, epi + 64
+
+
+REKEY, EPI, TABLE_WORDS = layout(3)  # re-keying of the source half at rounds 16, 32
 
 # secondary expansion positions: inputs b1, b2 of every S-box (their half bits
 # are also inputs b5, b6 of the previous S-box, which take the stored copy)
@@ -61,8 +72,8 @@ for i, q in enumerate(T.P):
     P_INV[q - 1] = i
 
 
-def schedule():
-    """(target, source) half of each of the 48 rounds of EDE3.
+def schedule(stages=3):
+    """(target, source) half of each of the 16*stages rounds (48 for EDE3).
 
     Rounds XOR into the target half in place.  Inside a DES stage the halves
     alternate; between stages the final swap of one stage and the first of
@@ -70,7 +81,7 @@ def schedule():
     stage as R16 || L16), so the target repeats.
     """
     out = []
-    for stage in range(3):
+    for stage in range(stages):
         for k in range(16):
             even = (k % 2 == 0)
             if stage == 1:
@@ -80,21 +91,23 @@ def schedule():
     return out
 
 
-def recipe():
+def recipe(stages=3):
     """For each table word: (set of subkey-bit refs (round, position), kind).
 
     kind 0: word = mask of the XOR of the refs; kind 1: the same mask | 1
     (the multiplier of the multiply-add form of a masked XOR).
     """
-    sched = schedule()
+    sched = schedule(stages)
+    nr = len(sched)
+    rekey, epi, nwords = layout(stages)
     kappa = {"L": [frozenset()] * 32, "R": [frozenset()] * 32}
-    words = [(frozenset(), 0)] * TABLE_WORDS
+    words = [(frozenset(), 0)] * nwords
 
     def need(r, i):
         return frozenset({(r, PRIMARY_POS[i])})
 
     def next_source(half, r):
-        for r2 in range(r + 1, 48):
+        for r2 in range(r + 1, nr):
             if sched[r2][1] == half:
                 return r2
         return None
@@ -106,8 +119,8 @@ def recipe():
         words[base] = (kappa[s0][i] ^ need(0, i), 0)
         kappa[s0] = kappa[s0][:i] + [need(0, i)] + kappa[s0][i + 1:]
     for r, (tgt, src) in enumerate(sched):
-        if r in (16, 32):
-            base = REKEY[0 if r == 16 else 1] + (0 if src == "L" else 32)
+        if r and r % 16 == 0:
+            base = rekey[r // 16 - 1] + (0 if src == "L" else 32)
             kap = list(kappa[src])
             for i in range(32):
                 words[base + i] = (kap[i] ^ need(r, i), 0)
@@ -133,7 +146,7 @@ def recipe():
         kappa[tgt] = kt
     for h, off in (("L", 0), ("R", 32)):
         for i in range(32):
-            words[EPI + off + i] = (kappa[h][i], 0)
+            words[epi + off + i] = (kappa[h][i], 0)
     return words
 
 
@@ -143,15 +156,18 @@ def recipe():
 SCALAR_GROUP_ORDER = (0, 6, 4, 2, 1, 7, 5, 3)
 
 
-def subkey_source(direction, r):
-    """(key index 0..2, DES round-key index 0..15) of EDE3 round r."""
+def subkey_source(direction, r, stages=3):
+    """(key index 0..2, DES round-key index 0..15) of round r: EDE3 for three
+    stages, a single DES pass under the first key for one."""
     stage, k = divmod(r, 16)
+    if stages == 1:
+        return (0, k) if direction == "enc" else (0, 15 - k)
     if direction == "enc":   # E_K1, D_K2, E_K3
         return [(0, k), (1, 15 - k), (2, k)][stage]
     return [(2, 15 - k), (1, k), (0, 15 - k)][stage]   # D_K3, E_K2, D_K1
 
 
-def resolve(words):
+def resolve(words, stages=3):
     """Refs -> key bits: entries (kind, a, b) with a, b = 64*key + (bit-1) or 255."""
     rkb = T.round_key_bits()
     out = {}
@@ -160,7 +176,7 @@ def resolve(words):
         for refs, kind in words:
             bits = []
             for (r, j) in sorted(refs):
-                key, sub = subkey_source(direction, r)
+                key, sub = subkey_source(direction, r, stages)
                 bits.append(64 * key + rkb[sub][j] - 1)
             assert len(bits) <= 2
             bits += [255] * (2 - len(bits))
@@ -213,6 +229,9 @@ def emit(path: str = OUT) -> str:
         sboxes = json.load(f)["sboxes"]
     words = recipe()
     rows = resolve(words)
+    words1 = recipe(1)
+    rows1 = resolve(words1, 1)
+    _, epi1, nwords1 = layout(1)
     L = []
     L.append("// GENERATED by paper_2007_10752_gb300/gen/emit_cuda.py -- do not edit.")
     L.append("// Bitsliced 3DES-EDE3 round, permutations and key-table recipe derived from the")
@@ -230,12 +249,20 @@ def emit(path: str = OUT) -> str:
     L.append(f"#define TDES_SBOX_GATES {gates}  // LOP3 per round for the eight S-boxes")
     # Which half each key-mask pass touches: the other half's words are all
     # zero by construction of the keyed-plane schedule (checked here).
-    zero = lambda base: all(not words[base + i][0] for i in range(32))  # noqa: E731
-    passes = {"PRO": PRO, "REKEY16": REKEY[0], "REKEY32": REKEY[1], "EPI": EPI}
-    for name, base in passes.items():
-        l_zero, r_zero = zero(base), zero(base + 32)
-        assert l_zero != r_zero, f"{name}: expected exactly one half to need key masks"
-        L.append(f"#define TDES_{name}_HALF_R {0 if r_zero else 1}  // 1: the R half, 0: the L half")
+    def half_defs(prefix, ws, passes):
+        zero = lambda base: all(not ws[base + i][0] for i in range(32))  # noqa: E731
+        for name, base in passes.items():
+            l_zero, r_zero = zero(base), zero(base + 32)
+            assert l_zero != r_zero, f"{name}: expected exactly one half to need key masks"
+            L.append(f"#define {prefix}_{name}_HALF_R {0 if r_zero else 1}  // 1: the R half, 0: the L half")
+
+    half_defs("TDES", words, {"PRO": PRO, "REKEY16": REKEY[0], "REKEY32": REKEY[1], "EPI": EPI})
+    L.append("")
+    L.append("// Single-DES tables (one pass of 16 rounds under the first key): the same")
+    L.append("// rounds and prologue layout, no re-keying, its own epilogue.")
+    L.append(f"#define TDES1_TABLE_WORDS {nwords1}")
+    L.append(f"#define TDES1_TABLE_EPI {epi1}")
+    half_defs("TDES1", words1, {"PRO": PRO, "EPI": epi1})
     L.append("")
     L.append("// Needs TDES_HD and lop3<LUT>(a, b, c) from tdes_bitslice.cuh.")
     L.append("")
@@ -282,15 +309,17 @@ def emit(path: str = OUT) -> str:
     L.append("")
     L.append("// Key-table recipe: per word {kind, bit a, bit b}; bit = 64*key + (key bit - 1),")
     L.append("// 255 = none.  Word = -(bit a ^ bit b), OR 1 when kind is 1.  [0] encrypt, [1] decrypt.")
-    L.append("#define TDES_RECIPE_INIT { \\")
-    for direction in ("enc", "dec"):
-        L.append("  { \\")
-        rr = rows[direction]
-        for s0 in range(0, TABLE_WORDS, 8):
-            chunk = ", ".join("{%d,%d,%d}" % r for r in rr[s0:s0 + 8])
-            L.append(f"    {chunk}, \\")
-        L.append("  }, \\")
-    L.append("}")
+    for name, rws, nw in (("TDES_RECIPE_INIT", rows, TABLE_WORDS),
+                          ("TDES1_RECIPE_INIT", rows1, nwords1)):
+        L.append(f"#define {name} {{ \\")
+        for direction in ("enc", "dec"):
+            L.append("  { \\")
+            rr = rws[direction]
+            for s0 in range(0, nw, 8):
+                chunk = ", ".join("{%d,%d,%d}" % r for r in rr[s0:s0 + 8])
+                L.append(f"    {chunk}, \\")
+            L.append("  }, \\")
+        L.append("}")
     text = "\n".join(L) + "\n"
     _write(path, text)
     L = []

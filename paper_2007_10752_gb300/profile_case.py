@@ -7,6 +7,7 @@ captures, whose commands are recorded beside their summaries in profiles/.
 
   python -m paper_2007_10752_gb300.profile_case --kernel ecb --mib 256 --launches 3
   python -m paper_2007_10752_gb300.profile_case --kernel batch --launches 3
+  python -m paper_2007_10752_gb300.profile_case --kernel ecb --des   (single-DES schedule)
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ def main():
     ap.add_argument("--mib", type=int, default=256)
     ap.add_argument("--kib", type=int, default=0, help="size in KiB (overrides --mib)")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--des", action="store_true", help="a single-DES schedule (one pass)")
     args = ap.parse_args()
 
     import torch
@@ -49,7 +51,7 @@ def main():
     keys = synth.key_triple(2)
     x = torch.from_numpy(synth.random_bytes(2, n)).cuda()
     y = torch.empty_like(x)
-    ks = tdes.KeySchedule.from_triple(keys)
+    ks = tdes.KeySchedule.des(keys[:8]) if args.des else tdes.KeySchedule.from_triple(keys)
     for _ in range(args.launches):
         if args.kernel == "ecb":
             tdes.tdes_ecb_encrypt(ks, x, y)

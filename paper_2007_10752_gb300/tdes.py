@@ -25,13 +25,14 @@ TDES_ECUDA = -5
 
 # every symbol include/tdes.h declares
 EXPORTED = (
-    "tdes_key_schedule", "tdes_key_free", "tdes_ecb_encrypt", "tdes_ecb_decrypt",
+    "tdes_key_schedule", "tdes_key_schedule_2key", "tdes_des_key_schedule",
+    "tdes_key_schedule_stages", "tdes_key_free", "tdes_ecb_encrypt", "tdes_ecb_decrypt",
     "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_cbc_decrypt_noalloc",
     "tdes_ecb_crypt_host", "tdes_keytable_create", "tdes_keytable_free", "tdes_batch_plan",
     "tdes_batch_configure", "tdes_batch_launch", "tdes_batch_launch_graph", "tdes_batch_info",
     "tdes_batch_free", "tdes_server_config_default", "tdes_server_create", "tdes_server_submit",
     "tdes_server_poll", "tdes_server_wait", "tdes_server_destroy", "tdes_serve_loadtest",
-    "tdes_sbox_gate_count", "tdes_strerror", "tdes_last_error",
+    "tdes_sbox_gate_count", "tdes_set_small_cutoff", "tdes_strerror", "tdes_last_error",
 )
 
 MODE_ECB_ENCRYPT = 0
@@ -100,6 +101,10 @@ def load(path: str = LIB_PATH):
     vp, sz, u32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64
     u8p = ctypes.POINTER(ctypes.c_uint8)
     lib.tdes_key_schedule.argtypes = [u8p, u8p, u8p, ctypes.POINTER(vp)]
+    lib.tdes_key_schedule_2key.argtypes = [u8p, u8p, ctypes.POINTER(vp)]
+    lib.tdes_des_key_schedule.argtypes = [u8p, ctypes.POINTER(vp)]
+    lib.tdes_key_schedule_stages.argtypes = [vp]
+    lib.tdes_key_schedule_stages.restype = ctypes.c_int
     lib.tdes_key_free.argtypes = [vp]
     lib.tdes_key_free.restype = None
     for name in ("tdes_ecb_encrypt", "tdes_ecb_decrypt"):
@@ -130,6 +135,8 @@ def load(path: str = LIB_PATH):
     lib.tdes_serve_loadtest.argtypes = [vp, ctypes.POINTER(LoadtestConfig),
                                         ctypes.POINTER(LoadtestResult)]
     lib.tdes_sbox_gate_count.argtypes = []
+    lib.tdes_set_small_cutoff.argtypes = [u64]
+    lib.tdes_set_small_cutoff.restype = u64
     lib.tdes_strerror.argtypes = [ctypes.c_int]
     lib.tdes_strerror.restype = ctypes.c_char_p
     lib.tdes_last_error.argtypes = []
@@ -172,17 +179,25 @@ def _stream(stream) -> int:
     return stream.cuda_stream
 
 
-class KeySchedule:
-    """Owns a tdes_ks_t built by tdes_key_schedule on the current device."""
+def _key_ptrs(*keys):
+    if any(len(bytes(k)) != 8 for k in keys):
+        raise ValueError("each key is 8 bytes")
+    bufs = [(ctypes.c_uint8 * 8).from_buffer_copy(bytes(k)) for k in keys]
+    return bufs, [ctypes.cast(b, ctypes.POINTER(ctypes.c_uint8)) for b in bufs]
 
-    def __init__(self, k1: bytes, k2: bytes, k3: bytes):
-        lib = load()
-        if len(k1) != 8 or len(k2) != 8 or len(k3) != 8:
-            raise ValueError("each key is 8 bytes")
-        bufs = [(ctypes.c_uint8 * 8).from_buffer_copy(bytes(k)) for k in (k1, k2, k3)]
+
+class KeySchedule:
+    """Owns a tdes_ks_t built on the current device: EDE3 under (k1, k2, k3)
+    by tdes_key_schedule (a triple that reduces to one DES pass gets a
+    single-DES schedule), or by the named constructors below."""
+
+    def __init__(self, k1: bytes, k2: bytes, k3: bytes, *, _handle=None):
+        if _handle is not None:
+            self.handle = _handle
+            return
+        _bufs, ptrs = _key_ptrs(k1, k2, k3)
         h = ctypes.c_void_p()
-        _check(lib.tdes_key_schedule(*[ctypes.cast(b, ctypes.POINTER(ctypes.c_uint8))
-                                       for b in bufs], ctypes.byref(h)))
+        _check(load().tdes_key_schedule(*ptrs, ctypes.byref(h)))
         self.handle = h.value
 
     @classmethod
@@ -191,6 +206,29 @@ class KeySchedule:
         if len(k) != 24:
             raise ValueError("a key triple is 24 bytes")
         return cls(k[:8], k[8:16], k[16:])
+
+    @classmethod
+    def two_key(cls, k1: bytes, k2: bytes) -> "KeySchedule":
+        """Two-key 3DES: EDE3 under (k1, k2, k1) (tdes_key_schedule_2key)."""
+        _bufs, ptrs = _key_ptrs(k1, k2)
+        h = ctypes.c_void_p()
+        _check(load().tdes_key_schedule_2key(*ptrs, ctypes.byref(h)))
+        return cls(b"", b"", b"", _handle=h.value)
+
+    @classmethod
+    def des(cls, key: bytes) -> "KeySchedule":
+        """Single DES under `key` (tdes_des_key_schedule)."""
+        _bufs, ptrs = _key_ptrs(key)
+        h = ctypes.c_void_p()
+        _check(load().tdes_des_key_schedule(*ptrs, ctypes.byref(h)))
+        return cls(b"", b"", b"", _handle=h.value)
+
+    @property
+    def stages(self) -> int:
+        """DES passes per block: 3 (EDE3) or 1 (single DES)."""
+        rc = load().tdes_key_schedule_stages(self.handle)
+        _check(rc if rc < 0 else 0)
+        return rc
 
     def free(self):
         if self.handle:
@@ -414,6 +452,28 @@ class Server:
 
 def tdes_sbox_gate_count() -> int:
     return int(load().tdes_sbox_gate_count())
+
+
+def tdes_set_small_cutoff(nblocks: int) -> int:
+    """Calls of at most `nblocks` blocks run one block per thread
+    (tdes_set_small_cutoff); returns the previous cutoff."""
+    return int(load().tdes_set_small_cutoff(int(nblocks)))
+
+
+class small_cutoff:
+    """Context manager: run calls with the given small-call cutoff, then
+    restore the previous one (0: always bitsliced)."""
+
+    def __init__(self, nblocks: int):
+        self.nblocks = nblocks
+
+    def __enter__(self):
+        self.prev = tdes_set_small_cutoff(self.nblocks)
+        return self
+
+    def __exit__(self, *exc):
+        tdes_set_small_cutoff(self.prev)
+        return False
 
 
 def tdes_strerror(status: int) -> str:

@@ -4,8 +4,12 @@
 // key-table recipes and plane renames can be checked against the CPU oracle
 // without a GPU.
 //
-// Usage: tdes_host_check <bs_enc|bs_dec|sc_enc|sc_dec|sn_enc|sn_dec> <48 hex K1||K2||K3>
+// Usage: tdes_host_check <bs_enc|bs_dec|b1_enc|b1_dec|sc_enc|sc_dec|sn_enc|sn_dec|s1_enc|s1_dec>
+//                        <48 hex K1||K2||K3>
 //   reads whole 8-byte blocks on stdin, writes the results on stdout.
+//   b1_*: the single-DES (one-pass) bitsliced tables and rounds under K1.
+//   s1_*: the 16-round scalar round on the key words of (K1, K1, K1), as the
+//         library builds them for a single-DES schedule.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -14,6 +18,7 @@
 #include "../../paper_2007_10752_gb300/csrc/tdes_keysched.cuh"
 
 static const uint8_t kRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
+static const uint8_t kRecipe1[2][TDES1_TABLE_WORDS][3] = TDES1_RECIPE_INIT;
 static const uint8_t kSub[2][48][48] = TDES_SUBKEY_INIT;
 static const uint32_t kSP[8][64] = TDES_SP_INIT;
 static const uint8_t kIP[64] = TDES_IP_INIT;
@@ -29,7 +34,12 @@ int main(int argc, char** argv) {
         keys[i] = (uint8_t)strtoul(h, nullptr, 16);
     }
     const bool dec = strstr(argv[1], "dec") != nullptr;
-    const bool bitsliced = strncmp(argv[1], "bs", 2) == 0;
+    if (strncmp(argv[1], "s1", 2) == 0) {  // a single-DES schedule holds (K1, K1, K1)
+        memcpy(keys + 8, keys, 8);
+        memcpy(keys + 16, keys, 8);
+    }
+    const bool bitsliced = argv[1][0] == 'b';
+    const bool one_pass = strncmp(argv[1], "b1", 2) == 0;
     std::vector<uint8_t> data;
     uint8_t buf[1 << 16];
     size_t got;
@@ -40,7 +50,10 @@ int main(int argc, char** argv) {
 
     if (bitsliced) {
         alignas(16) static uint32_t tab[TDES_TABLE_WORDS];
-        for (int e = 0; e < TDES_TABLE_WORDS; ++e) tab[e] = tdes_table_word(keys, kRecipe[dec][e]);
+        if (one_pass)
+            for (int e = 0; e < TDES1_TABLE_WORDS; ++e) tab[e] = tdes_table_word(keys, kRecipe1[dec][e]);
+        else
+            for (int e = 0; e < TDES_TABLE_WORDS; ++e) tab[e] = tdes_table_word(keys, kRecipe[dec][e]);
         for (size_t g0 = 0; g0 < n; g0 += 32) {
             uint32_t A0[32], A1[32];
             for (int s = 0; s < 32; ++s) {
@@ -49,7 +62,10 @@ int main(int argc, char** argv) {
                 A0[s] = w[0];
                 A1[s] = w[1];
             }
-            tdes_process32(A0, A1, tab);
+            if (one_pass)
+                tdes_process32<1>(A0, A1, tab);
+            else
+                tdes_process32<3>(A0, A1, tab);
             for (int s = 0; s < 32 && g0 + s < n; ++s) {
                 uint32_t w[2] = {A0[s], A1[s]};
                 memcpy(&out[8 * (g0 + s)], w, 8);
@@ -66,6 +82,10 @@ int main(int argc, char** argv) {
             if (argv[1][1] == 'n')
                 v = tdes_block_scalar_nib(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks),
                                           &kIPN[0][0], &kFPN[0][0]);
+            else if (argv[1][1] == '1')
+                v = tdes_block_scalar_nib<16>(v, &kSP[0][0],
+                                              reinterpret_cast<const uint32_t*>(chunks),
+                                              &kIPN[0][0], &kFPN[0][0]);
             else
                 v = tdes_block_scalar(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks), kIP,
                                       kFP);

@@ -60,6 +60,18 @@ def test_round_schedule_and_recipe_shape():
     words = emit_cuda.recipe()
     assert len(words) == emit_cuda.TABLE_WORDS
     assert all(len(refs) <= 2 for refs, _ in words)
+    # the single-DES schedule is EDE3's first pass; its table has no re-keying
+    assert emit_cuda.schedule(1) == sched[:16]
+    rekey, epi, nwords = emit_cuda.layout(1)
+    assert rekey == () and epi == emit_cuda.ROUND0 + 16 * 64 and nwords == epi + 64
+    words1 = emit_cuda.recipe(1)
+    assert len(words1) == nwords
+    # rounds 0..14 need the same key bits as in EDE3; the last round's
+    # updates key for nothing further, and single DES reads only one key
+    assert words1[:emit_cuda.ROUND0 + 15 * 64] == words[:emit_cuda.ROUND0 + 15 * 64]
+    rows1 = emit_cuda.resolve(words1, 1)
+    for d in ("enc", "dec"):
+        assert all(b == 255 or b < 64 for _, a, b in rows1[d] for b in (a, b))
 
 
 @pytest.fixture(scope="module")
@@ -89,10 +101,14 @@ KEYSETS = [
 
 
 @pytest.mark.parametrize("name,mk", KEYSETS, ids=[k[0] for k in KEYSETS])
-@pytest.mark.parametrize("mode", ["bs_enc", "bs_dec", "sc_enc", "sc_dec", "sn_enc", "sn_dec"])
+@pytest.mark.parametrize("mode", ["bs_enc", "bs_dec", "b1_enc", "b1_dec", "sc_enc", "sc_dec",
+                                  "sn_enc", "sn_dec", "s1_enc", "s1_dec"])
 def test_generated_code_matches_oracle(host_check, name, mk, mode):
     keys = mk()
     data = synth.random_bytes(len(name) * 31 + 5, 8 * 75)  # 2 full groups of 32 + a ragged one
     got = _run(host_check, mode, keys, data)
-    want = oracle.tdes_ecb(keys, data, decrypt=mode.endswith("dec"))
+    if mode[1] == "1":  # one DES pass under K1
+        want = oracle.des_ecb(keys[:8], data, decrypt=mode.endswith("dec"))
+    else:
+        want = oracle.tdes_ecb(keys, data, decrypt=mode.endswith("dec"))
     assert (got == want).all()

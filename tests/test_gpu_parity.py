@@ -5,7 +5,9 @@ inputs: sizes that hit the empty case, one block, ragged lane groups,
 exactly one and just past one warp tile, many tiles across the wide
 launch geometry, 8-byte-aligned (not 16) buffers, in-place calls, and the
 1 GiB single-key workload in the launch configuration the benchmark times,
-checked on sampled windows the oracle recomputes.
+checked on sampled windows the oracle recomputes.  Sizes small calls can
+take run on both single-key paths (bitsliced tiles, and one block per
+thread), forced with the small-call cutoff.
 """
 import os
 
@@ -65,11 +67,13 @@ def _gpu(T, mode, ks, x, out, iv=0, nonce=0, ctr0=0):
 
 
 MODES = ["ecb_enc", "ecb_dec", "ctr", "cbc_dec", "cbc_enc"]
+PATHS = {"bitsliced": 0, "per_thread": 1 << 40}  # small-call cutoff forcing each path
 
 
+@pytest.mark.parametrize("path", list(PATHS))
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("nblocks", SIZES)
-def test_parity_sizes(cuda_lib, mode, nblocks):
+def test_parity_sizes(cuda_lib, mode, nblocks, path):
     if mode == "cbc_enc" and nblocks > 5000:
         nblocks = 5000  # serial chain: keep the test quick
     seed = 1000 + nblocks
@@ -79,28 +83,35 @@ def test_parity_sizes(cuda_lib, mode, nblocks):
     ks = cuda_lib.KeySchedule.from_triple(keys)
     x = _dev(data)
     out = _dev(np.zeros_like(data))
-    got = _host(_gpu(cuda_lib, mode, ks, x, out, iv, nonce, ctr0))
+    with cuda_lib.small_cutoff(PATHS[path]):
+        got = _host(_gpu(cuda_lib, mode, ks, x, out, iv, nonce, ctr0))
     want = _ref(mode, keys, data, iv, nonce, ctr0)
     assert (got == want).all(), f"{mode} {nblocks}: first diff at byte {np.argmax(got != want)}"
 
 
+@pytest.mark.parametrize("path", list(PATHS))
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("offset", [8, 24])
-def test_parity_8byte_aligned_and_in_place(cuda_lib, mode, offset):
-    nblocks = 2 * 1024 + 77 if mode != "cbc_enc" else 700
+@pytest.mark.parametrize("nblocks", [2 * 1024 + 77, 1000])
+def test_parity_8byte_aligned_and_in_place(cuda_lib, mode, offset, path, nblocks):
+    """Both sizes run in place on the per-thread path: up to 1024 blocks as one
+    CTA, above that the bitsliced kernels take in-place CBC decryption."""
+    if mode == "cbc_enc":
+        nblocks = 700
     seed = 2000 + offset
     keys = synth.key_triple(seed)
     data = synth.random_bytes(seed, 8 * nblocks)
     iv, nonce = synth.iv64(seed), synth.nonce32(seed)
     ks = cuda_lib.KeySchedule.from_triple(keys)
     want = _ref(mode, keys, data, iv, nonce, 0)
-    x = _dev(data, offset)           # 8-byte aligned, not 16
-    out = _dev(np.zeros_like(data), offset)
-    assert (_host(_gpu(cuda_lib, mode, ks, x, out, iv, nonce, 0)) == want).all()
-    y = _dev(data, offset)           # in place
-    assert (_host(_gpu(cuda_lib, mode, ks, y, y, iv, nonce, 0)) == want).all()
-    z = _dev(data, 0)                # in place, 16-byte aligned
-    assert (_host(_gpu(cuda_lib, mode, ks, z, z, iv, nonce, 0)) == want).all()
+    with cuda_lib.small_cutoff(PATHS[path]):
+        x = _dev(data, offset)           # 8-byte aligned, not 16
+        out = _dev(np.zeros_like(data), offset)
+        assert (_host(_gpu(cuda_lib, mode, ks, x, out, iv, nonce, 0)) == want).all()
+        y = _dev(data, offset)           # in place
+        assert (_host(_gpu(cuda_lib, mode, ks, y, y, iv, nonce, 0)) == want).all()
+        z = _dev(data, 0)                # in place, 16-byte aligned
+        assert (_host(_gpu(cuda_lib, mode, ks, z, z, iv, nonce, 0)) == want).all()
 
 
 @pytest.mark.parametrize("mode", ["ecb_enc", "ecb_dec", "ctr", "cbc_dec"])

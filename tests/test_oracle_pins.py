@@ -99,6 +99,21 @@ def check_library_ctr(o: Oracle):
         assert (o.tdes_ctr(keys, nonce, ctr0, data) == (data ^ ks)).all()
 
 
+def check_library_des(o: Oracle):
+    # an 8-byte key makes the library's TripleDES single DES
+    for i, n in enumerate(SIZES):
+        key = synth.key_triple(250 + i)[:8]
+        iv = synth.iv64(250 + i)
+        data = synth.random_bytes(250 + i, 8 * n)
+        assert o.des_ecb(key, data).tobytes() == _lib_ecb(key, data), f"DES ECB, {n} blocks"
+        assert o.des_ecb(key, data, decrypt=True).tobytes() == _lib_ecb(key, data, decrypt=True)
+        assert o.des_cbc_encrypt(key, iv, data).tobytes() == _lib_cbc(key, iv, data)
+        assert o.des_cbc_decrypt(key, iv, data).tobytes() == _lib_cbc(key, iv, data, True)
+        nonce = synth.nonce32(250 + i)
+        ks = np.frombuffer(_lib_ecb(key, _counter_blocks(nonce, 3, n)), dtype=np.uint8)
+        assert (o.des_ctr(key, nonce, 3, data) == (data ^ ks)).all()
+
+
 def check_roundtrips(o: Oracle):
     for i, n in enumerate(SIZES):
         keys = synth.key_triple(400 + i)
@@ -119,6 +134,30 @@ def check_ede3_degenerates_to_des(o: Oracle):
         blk = synth.random_bytes(500 + i, 8)
         for dec in (False, True):
             assert o.tdes_block(k * 3, blk, dec) == o.des_block(k, blk, dec)
+    # D_K(E_K(x)) = x inside EDE3: K1 = K2 leaves E_K3, K2 = K3 leaves E_K1
+    for i in range(4):
+        ka, kb = synth.key_triple(510 + i)[:8], synth.key_triple(510 + i)[8:16]
+        data = synth.random_bytes(510 + i, 8 * 9)
+        for dec in (False, True):
+            assert (o.tdes_ecb(ka + ka + kb, data, dec) == o.des_ecb(kb, data, dec)).all()
+            assert (o.tdes_ecb(ka + kb + kb, data, dec) == o.des_ecb(ka, data, dec)).all()
+
+
+def check_des_modes_are_the_block_cipher_in_modes(o: Oracle):
+    # the single-DES modes are the EDE3 modes under (K, K, K), and each one
+    # is built on des_block the way its definition says
+    for i, n in enumerate([1, 5, 33]):
+        k = synth.key_triple(520 + i)[:8]
+        iv = synth.iv64(520 + i)
+        data = synth.random_bytes(520 + i, 8 * n)
+        assert (o.des_ecb(k, data) == o.tdes_ecb(k * 3, data)).all()
+        assert (o.des_ctr(k, 11, 2, data) == o.tdes_ctr(k * 3, 11, 2, data)).all()
+        assert (o.des_cbc_encrypt(k, iv, data) == o.tdes_cbc_encrypt(k * 3, iv, data)).all()
+        assert (o.des_cbc_decrypt(k, iv, data) == o.tdes_cbc_decrypt(k * 3, iv, data)).all()
+        blocks = [o.des_block(k, data[8 * j:8 * j + 8]) for j in range(n)]
+        assert o.des_ecb(k, data).tobytes() == b"".join(blocks)
+        assert (o.des_ecb(k, o.des_ecb(k, data), decrypt=True) == data).all()
+        assert (o.des_cbc_decrypt(k, iv, o.des_cbc_encrypt(k, iv, data)) == data).all()
 
 
 def check_complementation(o: Oracle):
@@ -182,8 +221,9 @@ def check_sbox_rows_are_permutations(o: Oracle):
             assert vals == set(range(16))
 
 
-LIB_CHECKS = [check_library_ecb, check_library_cbc, check_library_ctr]
-PROPERTY_CHECKS = [check_roundtrips, check_ede3_degenerates_to_des, check_complementation,
+LIB_CHECKS = [check_library_ecb, check_library_cbc, check_library_ctr, check_library_des]
+PROPERTY_CHECKS = [check_roundtrips, check_ede3_degenerates_to_des,
+                   check_des_modes_are_the_block_cipher_in_modes, check_complementation,
                    check_weak_keys, check_parity_ignored, check_worked_example,
                    check_sbox_rows_are_permutations]
 
@@ -304,6 +344,8 @@ MUTANTS = [
      "uint64_t counter = ((uint64_t)nonce << 32) | (uint32_t)(ctr0 + (uint32_t)i);",
      "uint64_t counter = ((uint64_t)(uint32_t)(ctr0 + (uint32_t)i) << 32) | nonce;"),
     ("cbc_dec_chains_plaintext", "memcpy(prev, cur, 8);", "memcpy(prev, out + 8 * i, 8);"),
+    ("single_des_ignores_direction", "des_block(k->rk[0], decrypt, in, out);",
+     "des_block(k->rk[0], 0, in, out);"),
 ]
 
 
