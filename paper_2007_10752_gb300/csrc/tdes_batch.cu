@@ -44,29 +44,47 @@ __device__ const uint32_t kBatchSP[8][64] = TDES_SP_INIT;
 __device__ const uint64_t kBatchIPN[16][16] = TDES_IPN_INIT;
 __device__ const uint64_t kBatchFPN[16][16] = TDES_FPN_INIT;
 __device__ const uint8_t kBatchRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
+__device__ const uint8_t kBatchRecipe1[2][TDES1_TABLE_WORDS][3] = TDES1_RECIPE_INIT;
 __device__ const uint8_t kBatchSubkeyBits[2][48][48] = TDES_SUBKEY_INIT;
 
 __device__ __forceinline__ uint32_t bswap32d(uint32_t x) { return __byte_perm(x, 0u, 0x0123); }
 
 // ---------------------------------------------------------------- key table
+__device__ __forceinline__ bool same_des_key(const uint8_t* a, const uint8_t* b) {
+    uint32_t d = 0;
+    for (int i = 0; i < 8; ++i) d |= (uint32_t)(a[i] ^ b[i]) & 0xFEu;  // parity bits ignored
+    return d == 0;
+}
+
 // Thread per (key, word): bitsliced tables of both directions, then the
-// scalar groups of both directions.
+// scalar groups of both directions.  A triple with K1 = K2 (EDE3 = E_K3) or
+// K2 = K3 (EDE3 = E_K1) gets single-DES tables under that key: the one-pass
+// bitsliced table, and the scalar groups of EDE3 under (K, K, K), whose first
+// 16 rounds are those of DES_K in both directions.
 __global__ void tdes_keytable_kernel(const uint8_t* __restrict__ keys, uint32_t count,
-                                     uint32_t* __restrict__ tabs, uint8_t* __restrict__ chunks) {
+                                     uint32_t* __restrict__ tabs, uint8_t* __restrict__ chunks,
+                                     uint8_t* __restrict__ stages) {
     const uint64_t per_key = (uint64_t)kPerKeyWords + kPerKeyChunks;
     const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= per_key * count) return;
     const uint32_t key = (uint32_t)(e / per_key);
     const uint32_t w = (uint32_t)(e % per_key);
     const uint8_t* k = keys + 24ull * key;
+    const uint8_t* single = same_des_key(k, k + 8) ? k + 16 : same_des_key(k + 8, k + 16) ? k : nullptr;
+    uint8_t eff[24];
+    for (int i = 0; i < 24; ++i) eff[i] = single ? single[i % 8] : k[i];
+    if (w == 0) stages[key] = single ? 1 : 3;
     if (w < kPerKeyWords) {
         const int dir = w / TDES_TABLE_WORDS, i = w % TDES_TABLE_WORDS;
-        tabs[(uint64_t)key * kPerKeyWords + w] = tdes_table_word(k, kBatchRecipe[dir][i]);
+        uint32_t v = 0;
+        if (!single) v = tdes_table_word(eff, kBatchRecipe[dir][i]);
+        else if (i < TDES1_TABLE_WORDS) v = tdes_table_word(eff, kBatchRecipe1[dir][i]);
+        tabs[(uint64_t)key * kPerKeyWords + w] = v;
     } else {
         const int f = w - kPerKeyWords;
         const int dir = f / TDES_SUBKEY_WORDS, c = f % TDES_SUBKEY_WORDS;
         chunks[(uint64_t)key * kPerKeyChunks + f] =
-            tdes_subkey_chunk(k, &kBatchSubkeyBits[dir][c / 8][6 * (c % 8)]);
+            tdes_subkey_chunk(eff, &kBatchSubkeyBits[dir][c / 8][6 * (c % 8)]);
     }
 }
 
@@ -100,7 +118,8 @@ __device__ __forceinline__ void store_be(uint8_t* p, uint64_t i, uint64_t v) {
 // registers across them (the 64 planes need the register file).
 __device__ __forceinline__ void batch_bs_tile(const BatchMsg* __restrict__ mp, uint64_t tile,
                                               uint64_t gtile, const uint32_t* __restrict__ tab,
-                                              const uint64_t* __restrict__ halo, uint32_t lane) {
+                                              const uint64_t* __restrict__ halo, uint32_t lane,
+                                              bool one_pass) {
     const uint64_t b0 = tile * kTileBlocks;
     uint32_t A0[32], A1[32];
     {
@@ -143,7 +162,7 @@ __device__ __forceinline__ void batch_bs_tile(const BatchMsg* __restrict__ mp, u
             }
     }
     }
-    tdes_process32(A0, A1, tab);
+    tdes_process32_rt(A0, A1, tab, one_pass);
     const BatchMsg m = *mp;
     const uint64_t n = m.nblocks;
     const bool full = b0 + kTileBlocks <= n;
@@ -249,7 +268,7 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
     if (msg != 0xFFFFFFFFu) {
         uint64_t y = tdes_block_scalar_nib(
             x, st.sp, reinterpret_cast<const uint32_t*>(warp_smem + TDES_SUBKEY_WORDS * lane),
-            st.ipn, st.fpn);
+            st.ipn, st.fpn, p.keystages[m.key] == 1 ? 16 : 48);
         if (m.mode == TDES_MODE_CTR || m.mode == TDES_MODE_CBC_DECRYPT) y ^= prev;
         store_be(m.out, blk, y);
     }
@@ -283,12 +302,13 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
         c.ip_lo = kBatchLaneIP[lane][1];
         c.fp_hi = kBatchLaneFP[lane][0];
         c.fp_lo = kBatchLaneFP[lane][1];
+        const int rounds = p.keystages[m.key] == 1 ? 16 : 48;
         uint64_t prev = m.iv;
         uint64_t next = load_be(m.in, 0);
         for (uint64_t i = 0; i < m.nblocks; ++i) {
             const uint64_t x = next ^ prev;
             if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
-            prev = tdes_block_warp(x, c, warp_smem);
+            prev = tdes_block_warp(x, c, warp_smem, rounds);
             if (lane == 0) store_be(m.out, i, prev);
         }
         __syncwarp();
@@ -302,13 +322,14 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
         stage_chunks(ch, p.keychunks + (uint64_t)m.key * kPerKeyChunks);
         // the next block is loaded one iteration ahead (its latency hides
         // behind the current block's rounds)
+        const int rounds = p.keystages[m.key] == 1 ? 16 : 48;
         uint64_t prev = m.iv;
         uint64_t next = load_be(m.in, 0);
         for (uint64_t i = 0; i < m.nblocks; ++i) {
             const uint64_t x = next ^ prev;
             if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
             prev = tdes_block_scalar_nib(x, st.sp, reinterpret_cast<const uint32_t*>(ch), st.ipn,
-                                         st.fpn);
+                                         st.fpn, rounds);
             store_be(m.out, i, prev);
         }
     }
@@ -338,29 +359,26 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
         }
         item -= p.n_c_items;
         if (item < p.n_b_chunks) {
-            // a run of b_chunk consecutive tiles: one message search for the
-            // run, then a step forward at each message boundary
+            // a run of b_chunk consecutive tiles; the plan maps each tile to
+            // its message entry
             const uint64_t t0 = item * p.b_chunk;
-            uint32_t lo = 0, hi = p.n_b;  // b_prefix[lo] <= t0 < b_prefix[hi]
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (p.b_prefix[mid] <= t0) lo = mid; else hi = mid;
-            }
             for (uint64_t t = t0; t < min(t0 + p.b_chunk, p.n_b_tiles); ++t) {
-                while (t >= p.b_prefix[lo + 1]) ++lo;
+                const uint32_t lo = p.b_tile[t];
                 const BatchMsg* mp = p.msgs + p.b_msg[lo];
                 const uint32_t key = mp->key, dir = (uint32_t)dir_of(mp->mode);
                 const uint32_t want = (key << 1) | dir;
+                const bool one_pass = p.keystages[key] == 1;
                 if (want != staged) {
                     __syncwarp();
                     const uint4* src = reinterpret_cast<const uint4*>(
                         p.keytab + (uint64_t)key * kPerKeyWords + TDES_TABLE_WORDS * dir);
-                    for (int i = lane; i < TDES_TABLE_WORDS / 4; i += 32)
+                    const int n4 = (one_pass ? TDES1_TABLE_WORDS : TDES_TABLE_WORDS) / 4;
+                    for (int i = lane; i < n4; i += 32)
                         reinterpret_cast<uint4*>(wtab)[i] = __ldg(src + i);
                     __syncwarp();
                     staged = want;
                 }
-                batch_bs_tile(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane);
+                batch_bs_tile(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane, one_pass);
             }
             continue;
         }
@@ -375,11 +393,7 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
 __global__ void tdes_batch_halo_kernel(BatchParams p) {
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= p.n_b_tiles) return;
-    uint32_t lo = 0, hi = p.n_b;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (p.b_prefix[mid] <= t) lo = mid; else hi = mid;
-    }
+    const uint32_t lo = p.b_tile[t];
     const BatchMsg m = p.msgs[p.b_msg[lo]];
     const uint64_t k = t - p.b_prefix[lo];
     if (m.mode == TDES_MODE_CBC_DECRYPT && m.in == m.out && k >= 1)
@@ -460,6 +474,7 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     h->o_c = take(c_list.size() * 4);
     h->o_bm = take(b_msg.size() * 4);
     h->o_bp = take(b_prefix.size() * 8);
+    h->o_bt = take(h->n_b_tiles * 4);
     h->o_sl = take(s_list.size() * 4);
     h->o_si = take(s_items.size() * sizeof(uint2));
     h->o_halo = take(h->needs_halo ? h->n_b_tiles * 8 : 0);
@@ -472,6 +487,9 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     put(h->o_c, c_list.data(), c_list.size() * 4);
     put(h->o_bm, b_msg.data(), b_msg.size() * 4);
     put(h->o_bp, b_prefix.data(), b_prefix.size() * 8);
+    uint32_t* bt = reinterpret_cast<uint32_t*>(h->image.data() + h->o_bt);
+    for (uint32_t i = 0; i < h->n_b; ++i)
+        std::fill(bt + b_prefix[i], bt + b_prefix[i + 1], i);
     put(h->o_sl, s_list.data(), s_list.size() * 4);
     put(h->o_si, s_items.data(), s_items.size() * sizeof(uint2));
 }
@@ -482,12 +500,14 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
     p.msgs = reinterpret_cast<const BatchMsg*>(base + h.o_msgs);
     p.keytab = kt->tabs;
     p.keychunks = kt->chunks;
+    p.keystages = kt->stages;
     p.c_list = reinterpret_cast<const uint32_t*>(base + h.o_c);
     p.n_c = h.n_c;
     p.n_c_items = h.n_c_items;
     p.n_c_solo = h.n_c_solo;
     p.b_msg = reinterpret_cast<const uint32_t*>(base + h.o_bm);
     p.b_prefix = reinterpret_cast<const uint64_t*>(base + h.o_bp);
+    p.b_tile = reinterpret_cast<const uint32_t*>(base + h.o_bt);
     p.n_b = h.n_b;
     p.n_b_tiles = h.n_b_tiles;
     p.s_list = reinterpret_cast<const uint32_t*>(base + h.o_sl);
@@ -612,8 +632,9 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
     const size_t tab_bytes = (size_t)count * tdes::kPerKeyWords * 4;
     const size_t chunk_bytes = tdes::align16((size_t)count * tdes::kPerKeyChunks);
     const size_t key_bytes = tdes::align16((size_t)count * 24);
+    const size_t stage_bytes = tdes::align16(count);
     void* mem = nullptr;
-    e = cudaMalloc(&mem, tab_bytes + chunk_bytes + key_bytes);
+    e = cudaMalloc(&mem, tab_bytes + chunk_bytes + key_bytes + stage_bytes);
     if (e != cudaSuccess) return bcuda(e, "cudaMalloc(key table)");
     tdes_keytable_t* kt = new (std::nothrow) tdes_keytable_t;
     if (kt == nullptr) {
@@ -626,14 +647,15 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
     kt->tabs = static_cast<uint32_t*>(mem);
     kt->chunks = static_cast<uint8_t*>(mem) + tab_bytes;
     uint8_t* dkeys = kt->chunks + chunk_bytes;
+    kt->stages = dkeys + key_bytes;
     cudaStream_t s = nullptr;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dkeys, keys, (size_t)count * 24, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const uint64_t n = (uint64_t)count * (tdes::kPerKeyWords + tdes::kPerKeyChunks);
-        tdes::tdes_keytable_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dkeys, count,
-                                                                              kt->tabs, kt->chunks);
+        tdes::tdes_keytable_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            dkeys, count, kt->tabs, kt->chunks, kt->stages);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(dkeys, 0, (size_t)count * 24, s);  // keys not kept

@@ -14,6 +14,7 @@ struct tdes_keytable {
     void* mem;
     uint32_t* tabs;   // [key][dir][3328] bitsliced round-constant tables
     uint8_t* chunks;  // [key][dir][384] scalar round-key words
+    uint8_t* stages;  // [key] DES passes: 3, or 1 for a triple that reduces to single DES
 };
 
 namespace tdes {
@@ -31,11 +32,13 @@ struct BatchParams {
     const BatchMsg* msgs;
     const uint32_t* keytab;    // [key][dir][TDES_TABLE_WORDS]
     const uint8_t* keychunks;  // [key][dir][TDES_SUBKEY_WORDS]
+    const uint8_t* keystages;  // [key] 3 (EDE3) or 1 (single DES: a one-pass table)
     const uint32_t* c_list;    // CBC-enc message indices, longest first
     uint32_t n_c, n_c_items;
     uint32_t n_c_solo;         // the first n_c_solo chains run one per warp
     const uint32_t* b_msg;     // large message index per B entry
     const uint64_t* b_prefix;  // exclusive prefix of tiles, n_b + 1 entries
+    const uint32_t* b_tile;    // per B tile: its B entry (index into b_msg / b_prefix)
     uint32_t n_b;
     uint64_t n_b_tiles;
     const uint32_t* s_list;    // small message indices
@@ -51,7 +54,8 @@ struct BatchParams {
 // A batch laid out on the host as the byte image of its device buffer.
 struct PlanHost {
     std::vector<uint8_t> image;
-    size_t o_msgs = 0, o_c = 0, o_bm = 0, o_bp = 0, o_sl = 0, o_si = 0, o_halo = 0, o_ctr = 0;
+    size_t o_msgs = 0, o_c = 0, o_bm = 0, o_bp = 0, o_bt = 0, o_sl = 0, o_si = 0, o_halo = 0,
+           o_ctr = 0;
     uint32_t n_c = 0, n_c_solo = 0, n_c_items = 0, n_b = 0, n_s_items = 0;
     uint64_t n_b_tiles = 0, total_items = 0;
     bool needs_halo = false;

@@ -148,6 +148,39 @@ TDES_HD void tdes_rounds(uint32_t (&Lh)[32], uint32_t (&Rh)[32], const uint32_t*
     TDES_KEY_PASS(TDES_EPI, TDES_TABLE_EPI);
 }
 
+// The same with the pass count chosen at run time (the batch kernel, whose
+// key tables mix EDE3 and single-DES schedules): the prologue and epilogue
+// of the two table layouts touch the same halves, so the one-pass case only
+// skips the re-keyings and the last two passes and takes its own epilogue.
+static_assert(TDES_PRO_HALF_R == TDES1_PRO_HALF_R && TDES_EPI_HALF_R == TDES1_EPI_HALF_R,
+              "runtime pass count assumes matching prologue and epilogue halves");
+TDES_HD void tdes_rounds_rt(uint32_t (&Lh)[32], uint32_t (&Rh)[32], const uint32_t* __restrict__ tab,
+                            bool one_pass) {
+    TDES_KEY_PASS(TDES_PRO, TDES_TABLE_PRO);
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it));
+        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it + 1));
+    }
+    if (one_pass) {
+        TDES_KEY_PASS(TDES_EPI, TDES1_TABLE_EPI);
+        return;
+    }
+    TDES_KEY_PASS(TDES_REKEY16, TDES_TABLE_REKEY16);
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (16 + 2 * it));
+        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (17 + 2 * it));
+    }
+    TDES_KEY_PASS(TDES_REKEY32, TDES_TABLE_REKEY32);
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (32 + 2 * it));
+        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (33 + 2 * it));
+    }
+    TDES_KEY_PASS(TDES_EPI, TDES_TABLE_EPI);
+}
+
 // 32 blocks: A0[s], A1[s] are the first and second little-endian 32-bit
 // words of block s on entry and of its result on return.
 template <int STAGES = 3>
@@ -157,6 +190,18 @@ TDES_HD void tdes_process32(uint32_t (&A0)[32], uint32_t (&A1)[32], const uint32
     uint32_t Lh[32], Rh[32];
     tdes_ip(A0, A1, Lh, Rh);
     tdes_rounds<STAGES>(Lh, Rh, tab);
+    tdes_fp(Lh, Rh, A0, A1);
+    transpose32(A0);
+    transpose32(A1);
+}
+
+TDES_HD void tdes_process32_rt(uint32_t (&A0)[32], uint32_t (&A1)[32],
+                               const uint32_t* __restrict__ tab, bool one_pass) {
+    transpose32(A0);
+    transpose32(A1);
+    uint32_t Lh[32], Rh[32];
+    tdes_ip(A0, A1, Lh, Rh);
+    tdes_rounds_rt(Lh, Rh, tab, one_pass);
     tdes_fp(Lh, Rh, A0, A1);
     transpose32(A0);
     transpose32(A1);
@@ -231,20 +276,19 @@ TDES_HD uint64_t permute64_nib(uint64_t v, const uint64_t* __restrict__ tab) {
 // tables (ipn/fpn: 16 x 16 words each) instead of bit loops.  The 16 rounds
 // of a DES pass are unrolled by two so that the halves alternate in place,
 // and each round's key words are loaded one round ahead, off the chain of
-// dependent operations that sets the latency of a block.  ROUNDS = 16 runs
+// dependent operations that sets the latency of a block.  rounds = 16 runs
 // single DES on the first 16 rounds' key words.
-template <int ROUNDS = 48>
 TDES_HD uint64_t tdes_block_scalar_nib(uint64_t v, const uint32_t* __restrict__ sp,
                                        const uint32_t* __restrict__ keys,
                                        const uint64_t* __restrict__ ipn,
-                                       const uint64_t* __restrict__ fpn) {
+                                       const uint64_t* __restrict__ fpn, int rounds = 48) {
     v = permute64_nib(v, ipn);
     uint32_t L = (uint32_t)(v >> 32), R = (uint32_t)v;
     uint32_t ke = keys[0], ko = keys[1];
-    for (int r = 0; r < ROUNDS; r += 2) {
+    for (int r = 0; r < rounds; r += 2) {
         const uint32_t ke1 = keys[2 * r + 2], ko1 = keys[2 * r + 3];
         L ^= tdes_f_scalar(R, ke, ko, sp);
-        const int rn = r + 2 < ROUNDS ? r + 2 : r;  // the last prefetch rereads the last pair
+        const int rn = r + 2 < rounds ? r + 2 : r;  // the last prefetch rereads the last pair
         ke = keys[2 * rn];
         ko = keys[2 * rn + 1];
         R ^= tdes_f_scalar(L, ke1, ko1, sp);
@@ -274,16 +318,16 @@ __device__ __forceinline__ uint32_t lane_bit(uint64_t v, uint32_t src) {
     return (uint32_t)(v >> (63u - src)) & 1u;
 }
 
-// ROUNDS = 16 runs single DES on the first 16 rounds' key words.
-template <int ROUNDS = 48>
+// rounds = 16 runs single DES on the first 16 rounds' key words.
 __device__ __forceinline__ uint64_t tdes_block_warp(uint64_t v, const LaneConsts& c,
-                                                    const uint8_t* __restrict__ keys) {
+                                                    const uint8_t* __restrict__ keys,
+                                                    int rounds = 48) {
     uint32_t L = __ballot_sync(0xFFFFFFFFu, lane_bit(v, c.ip_hi));
     uint32_t R = __ballot_sync(0xFFFFFFFFu, lane_bit(v, c.ip_lo));
     uint32_t k = keys[c.keypos];
 #pragma unroll 2
-    for (int r = 0; r < ROUNDS; ++r) {
-        const uint32_t kn = keys[8 * (r + 1 < ROUNDS ? r + 1 : r) + c.keypos];
+    for (int r = 0; r < rounds; ++r) {
+        const uint32_t kn = keys[8 * (r + 1 < rounds ? r + 1 : r) + c.keypos];
         const uint32_t x = ((rotr32(R, (int)c.rot) & 63u) ^ k);
         const uint32_t w = (x & 32u) ? c.mhi : c.mlo;
         const uint32_t f = __ballot_sync(0xFFFFFFFFu, (w >> (x & 31u)) & 1u);

@@ -83,9 +83,8 @@ int main(int argc, char** argv) {
                 v = tdes_block_scalar_nib(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks),
                                           &kIPN[0][0], &kFPN[0][0]);
             else if (argv[1][1] == '1')
-                v = tdes_block_scalar_nib<16>(v, &kSP[0][0],
-                                              reinterpret_cast<const uint32_t*>(chunks),
-                                              &kIPN[0][0], &kFPN[0][0]);
+                v = tdes_block_scalar_nib(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks),
+                                          &kIPN[0][0], &kFPN[0][0], 16);
             else
                 v = tdes_block_scalar(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks), kIP,
                                       kFP);

@@ -243,3 +243,36 @@ def test_plans_with_different_shapes_coexist(mix):
         b.launch()
         for i, (got, w) in enumerate(zip(outputs(arena, msgs), want)):
             assert (got == w).all(), f"message {i}"
+
+
+def test_key_tables_with_single_des_triples(cuda_lib):
+    """Triples with K1 = K2 or K2 = K3 (parity bits ignored) get single-DES
+    tables in a key table; every path of the batch kernel (bitsliced tiles,
+    small messages, packed and one-per-warp CBC-encryption chains) gives the
+    oracle's EDE3 result for them, next to ordinary triples."""
+    T = cuda_lib
+    t = synth.key_triples(31, 3)
+    a, b, c = t[0].tobytes()[:8], t[1].tobytes()[8:16], t[2].tobytes()[16:]
+    flip = bytes(x ^ 1 for x in a)
+    triples = [a + a + b, a + b + b, c + c + c, a + flip + c, a + b + c, t[1].tobytes()]
+    keys = np.frombuffer(b"".join(triples), dtype=np.uint8).reshape(-1, 24).copy()
+    kt = T.KeyTable(keys)
+    msgs, off = [], 0
+    for k in range(len(triples)):
+        for mode in range(5):
+            for nb in (20, 700, 1500 + 7 * k):
+                data = synth.random_bytes(3100 + 97 * k + 13 * mode + nb, 8 * nb)
+                iv = int(synth.words(31, 100 * k + 10 * mode + nb % 7, 1, synth.STREAM_IV)[0])
+                if mode == 2:
+                    iv &= 0xFFFFFFFF00000000
+                msgs.append(dict(mode=mode, key=k, iv=iv, nb=nb, in_off=off, out_off=off + 8 * nb,
+                                 data=data))
+                off += 16 * nb
+    arena = torch.zeros(off + 64, dtype=torch.uint8, device="cuda")
+    restage(arena, msgs)
+    b = T.Batch(kt, entries_for(arena, msgs))
+    assert (b.status == 0).all()
+    b.launch()
+    for i, (got, m) in enumerate(zip(outputs(arena, msgs), msgs)):
+        want = oracle_msg(m["mode"], triples[m["key"]], m["iv"], m["data"])
+        assert (got == want).all(), f"message {i}: key {m['key']} mode {m['mode']} {m['nb']} blocks"
