@@ -30,6 +30,7 @@
 #include "tdes_batch_internal.h"
 #include "tdes_internal.h"
 #include "tdes_keysched.cuh"
+#include "tdes_scalar.cuh"
 
 namespace tdes {
 
@@ -169,7 +170,18 @@ __device__ __forceinline__ void batch_bs_tile(const BatchMsg* __restrict__ mp, u
     const bool vec = full && (((reinterpret_cast<uintptr_t>(m.in) |
                                 reinterpret_cast<uintptr_t>(m.out)) & 15u) == 0);
     const uint2* c = reinterpret_cast<const uint2*>(m.in);
-    if (m.mode == TDES_MODE_CTR) {
+    if (m.mode == TDES_MODE_CTR && vec) {  // full 16-byte-aligned tile: 128-bit loads
+        const uint4* p = reinterpret_cast<const uint4*>(m.in) + (b0 >> 1) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint4 v = __ldcs(p + 32 * j);
+            A0[2 * j] ^= v.x;
+            A1[2 * j] ^= v.y;
+            A0[2 * j + 1] ^= v.z;
+            A1[2 * j + 1] ^= v.w;
+        }
+        __syncwarp();  // in place: every lane has read its data before any lane writes
+    } else if (m.mode == TDES_MODE_CTR) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
 #pragma unroll
@@ -266,9 +278,10 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
     }
     __syncwarp();  // every read of the item's messages precedes every write (in place)
     if (msg != 0xFFFFFFFFu) {
-        uint64_t y = tdes_block_scalar_nib(
-            x, st.sp, reinterpret_cast<const uint32_t*>(warp_smem + TDES_SUBKEY_WORDS * lane),
-            st.ipn, st.fpn, p.keystages[m.key] == 1 ? 16 : 48);
+        const uint32_t* ks = reinterpret_cast<const uint32_t*>(warp_smem + TDES_SUBKEY_WORDS * lane);
+        uint64_t y = p.keystages[m.key] == 1
+                         ? tdes_block_scalar_nib<16>(x, st.sp, ks, st.ipn, st.fpn)
+                         : tdes_block_scalar_nib<48>(x, st.sp, ks, st.ipn, st.fpn);
         if (m.mode == TDES_MODE_CTR || m.mode == TDES_MODE_CBC_DECRYPT) y ^= prev;
         store_be(m.out, blk, y);
     }
@@ -278,6 +291,36 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
 __device__ const uint32_t kBatchLaneSbox[32][4] = TDES_LANE_SBOX_INIT;
 __device__ const uint32_t kBatchLaneIP[32][2] = TDES_LANE_IP_INIT;
 __device__ const uint32_t kBatchLaneFP[32][2] = TDES_LANE_FP_INIT;
+
+// One CBC-encryption chain walked by the whole warp; the next plaintext block
+// is loaded one block ahead.
+template <int ROUNDS>
+__device__ __forceinline__ void warp_chain(const BatchMsg& m, const LaneConsts& c,
+                                           const uint8_t* keys, uint32_t lane) {
+    uint64_t prev = m.iv;
+    uint64_t next = load_be(m.in, 0);
+    for (uint64_t i = 0; i < m.nblocks; ++i) {
+        const uint64_t x = next ^ prev;
+        if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
+        prev = tdes_block_warp<ROUNDS>(x, c, keys);
+        if (lane == 0) store_be(m.out, i, prev);
+    }
+}
+
+// One short CBC-encryption chain per lane (scalar round); the next block is
+// loaded one iteration ahead, so its latency hides behind the current block.
+template <int ROUNDS>
+__device__ __forceinline__ void lane_chain(const BatchMsg& m, const SharedTables& st,
+                                           const uint32_t* keys) {
+    uint64_t prev = m.iv;
+    uint64_t next = load_be(m.in, 0);
+    for (uint64_t i = 0; i < m.nblocks; ++i) {
+        const uint64_t x = next ^ prev;
+        if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
+        prev = tdes_block_scalar_nib<ROUNDS>(x, st.sp, keys, st.ipn, st.fpn);
+        store_be(m.out, i, prev);
+    }
+}
 
 // C item: CBC-encryption chains.  The first n_c_solo items (the longest
 // chains) hold one chain each, walked by the whole warp (tdes_block_warp: a
@@ -302,15 +345,10 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
         c.ip_lo = kBatchLaneIP[lane][1];
         c.fp_hi = kBatchLaneFP[lane][0];
         c.fp_lo = kBatchLaneFP[lane][1];
-        const int rounds = p.keystages[m.key] == 1 ? 16 : 48;
-        uint64_t prev = m.iv;
-        uint64_t next = load_be(m.in, 0);
-        for (uint64_t i = 0; i < m.nblocks; ++i) {
-            const uint64_t x = next ^ prev;
-            if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
-            prev = tdes_block_warp(x, c, warp_smem, rounds);
-            if (lane == 0) store_be(m.out, i, prev);
-        }
+        if (p.keystages[m.key] == 1)
+            warp_chain<16>(m, c, warp_smem, lane);
+        else
+            warp_chain<48>(m, c, warp_smem, lane);
         __syncwarp();
         return;
     }
@@ -320,18 +358,11 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
         const BatchMsg m = p.msgs[p.c_list[idx]];
         uint8_t* ch = warp_smem + TDES_SUBKEY_WORDS * lane;
         stage_chunks(ch, p.keychunks + (uint64_t)m.key * kPerKeyChunks);
-        // the next block is loaded one iteration ahead (its latency hides
-        // behind the current block's rounds)
-        const int rounds = p.keystages[m.key] == 1 ? 16 : 48;
-        uint64_t prev = m.iv;
-        uint64_t next = load_be(m.in, 0);
-        for (uint64_t i = 0; i < m.nblocks; ++i) {
-            const uint64_t x = next ^ prev;
-            if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
-            prev = tdes_block_scalar_nib(x, st.sp, reinterpret_cast<const uint32_t*>(ch), st.ipn,
-                                         st.fpn, rounds);
-            store_be(m.out, i, prev);
-        }
+        const uint32_t* ks = reinterpret_cast<const uint32_t*>(ch);
+        if (p.keystages[m.key] == 1)
+            lane_chain<16>(m, st, ks);
+        else
+            lane_chain<48>(m, st, ks);
     }
     __syncwarp();
 }

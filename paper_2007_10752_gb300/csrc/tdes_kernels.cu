@@ -13,6 +13,7 @@
 
 #include "tdes_internal.h"
 #include "tdes_keysched.cuh"
+#include "tdes_scalar.cuh"
 
 namespace tdes {
 
@@ -461,7 +462,7 @@ __global__ void tdes_cbc_enc_kernel(const uint8_t* __restrict__ chunks_g, uint64
     for (uint64_t i = 0; i < nblocks; ++i) {
         const uint64_t x = bswap64(next) ^ prev;
         if (i + 1 < nblocks) next = p[i + 1];
-        prev = tdes_block_warp(x, c, keys, ROUNDS);
+        prev = tdes_block_warp<ROUNDS>(x, c, keys);
         if (lane == 0) q[i] = bswap64(prev);
     }
 }

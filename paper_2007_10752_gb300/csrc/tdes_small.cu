@@ -13,6 +13,7 @@
 
 #include "tdes_internal.h"
 #include "tdes_keysched.cuh"
+#include "tdes_scalar.cuh"
 
 namespace tdes {
 
@@ -62,7 +63,7 @@ tdes_small_kernel(const uint8_t* __restrict__ chunks, int mode, uint64_t iv, con
     }
     __syncthreads();  // tables staged; every read of this CTA precedes its writes
     if (b < nblocks) {
-        uint64_t y = tdes_block_scalar_nib(x, st.sp, st.keys, st.ipn, st.fpn, ROUNDS);
+        uint64_t y = tdes_block_scalar_nib<ROUNDS>(x, st.sp, st.keys, st.ipn, st.fpn);
         if (mode != kSmallEcb) y ^= prev;
         reinterpret_cast<uint64_t*>(out)[b] = bswap64(y);
     }

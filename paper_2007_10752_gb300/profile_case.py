@@ -7,6 +7,7 @@ captures, whose commands are recorded beside their summaries in profiles/.
 
   python -m paper_2007_10752_gb300.profile_case --kernel ecb --mib 256 --launches 3
   python -m paper_2007_10752_gb300.profile_case --kernel batch --launches 3
+  python -m paper_2007_10752_gb300.profile_case --kernel batch_ctr --mib 256   (one CTR message as a batch)
   python -m paper_2007_10752_gb300.profile_case --kernel ecb --des   (single-DES schedule)
 """
 from __future__ import annotations
@@ -22,7 +23,8 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec", "cbc_enc", "batch"],
+    ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec", "cbc_enc", "batch",
+                                         "batch_ctr"],
                     default="ecb")
     ap.add_argument("--mib", type=int, default=256)
     ap.add_argument("--kib", type=int, default=0, help="size in KiB (overrides --mib)")
@@ -49,6 +51,17 @@ def main():
         return
     n = (args.kib << 10) if args.kib else (args.mib << 20)
     keys = synth.key_triple(2)
+    if args.kernel == "batch_ctr":
+        # the single-key CTR stream of the large streaming workload, at this size
+        import numpy as np
+        x = torch.from_numpy(synth.random_bytes(2, n)).cuda()
+        kt = tdes.KeyTable(np.frombuffer(keys, dtype=np.uint8).reshape(1, 24))
+        b = tdes.Batch(kt, [(tdes.MODE_CTR, 0, 1 << 32, x.data_ptr(), x.data_ptr(), n)])
+        for _ in range(args.launches):
+            b.launch()
+        torch.cuda.synchronize()
+        print(f"batch_ctr: {args.launches} launches on {n >> 20} MiB done")
+        return
     x = torch.from_numpy(synth.random_bytes(2, n)).cuda()
     y = torch.empty_like(x)
     ks = tdes.KeySchedule.des(keys[:8]) if args.des else tdes.KeySchedule.from_triple(keys)

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../paper_2007_10752_gb300/csrc/tdes_keysched.cuh"
+#include "../../paper_2007_10752_gb300/csrc/tdes_scalar.cuh"
 
 static const uint8_t kRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
 static const uint8_t kRecipe1[2][TDES1_TABLE_WORDS][3] = TDES1_RECIPE_INIT;
@@ -83,8 +84,9 @@ int main(int argc, char** argv) {
                 v = tdes_block_scalar_nib(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks),
                                           &kIPN[0][0], &kFPN[0][0]);
             else if (argv[1][1] == '1')
-                v = tdes_block_scalar_nib(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks),
-                                          &kIPN[0][0], &kFPN[0][0], 16);
+                v = tdes_block_scalar_nib<16>(v, &kSP[0][0],
+                                              reinterpret_cast<const uint32_t*>(chunks),
+                                              &kIPN[0][0], &kFPN[0][0]);
             else
                 v = tdes_block_scalar(v, &kSP[0][0], reinterpret_cast<const uint32_t*>(chunks), kIP,
                                       kFP);
