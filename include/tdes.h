@@ -28,7 +28,8 @@
  *     descriptors, trust the caller.  Pointers must be 8-byte aligned;
  *     16-byte aligned buffers take the fastest load path.
  *     `nbytes` must be a multiple of 8 (the paper's input consists of whole
- *     64-bit blocks); 0 is a valid empty call.  in == out (in place) is
+ *     64-bit blocks); 0 is a valid empty call; one call takes less than
+ *     2^31 tiles of 8 KiB (16 TiB), far above any GPU's memory.  in == out (in place) is
  *     allowed; any other overlap of the two ranges returns TDES_EINVAL.
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *     default stream) unless stated otherwise; the caller synchronises.
@@ -184,18 +185,23 @@ typedef struct {
 } tdes_desc_t;
 
 typedef struct {
-    uint32_t n_cbc_enc_messages; /* serial chains, one GPU lane each */
+    uint32_t n_cbc_enc_messages; /* serial chains, one GPU lane or warp each */
     uint64_t n_tiles;            /* bitsliced 1024-block tiles of large messages */
-    uint32_t n_small_items;      /* warp items of small (<= 32-block) messages */
+    uint32_t n_small_items;      /* warp items of small (<= 32-block) messages, one block
+                                    per lane (batches with few small messages) */
     int warps_per_cta;
     int ctas_per_sm;
     uint64_t bytes_per_mode[5];  /* payload bytes, indexed by TDES_MODE_* */
+    uint64_t n_mixed_tiles;      /* bitsliced tiles of small messages under up to 32 keys
+                                    (batches with 8192 or more small-message blocks) */
 } tdes_batch_info_t;
 
 /* Key schedules (Sec. III-A) of `count` triples (keys: count x 24 bytes,
- * K1||K2||K3 each) computed by one key-schedule kernel and kept in device
- * memory (27392 bytes per triple) on the current device.  Synchronous.  The
- * raw keys are not kept.  Free with tdes_keytable_free(). */
+ * K1||K2||K3 each) computed by the key-schedule kernels and kept in device
+ * memory (28225 bytes per triple: the bitsliced tables of both directions,
+ * their one-bit-per-word copies for tiles that mix keys, and the scalar
+ * round-key groups) on the current device.  Synchronous.  The raw keys are
+ * not kept.  Free with tdes_keytable_free(). */
 int tdes_keytable_create(const uint8_t *keys, uint32_t count, tdes_keytable_t **out);
 void tdes_keytable_free(tdes_keytable_t *kt);
 

@@ -39,6 +39,7 @@ def _inputs():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
     files += [os.path.join(CSRC, "generated", "tdes_generated.cuh"),
               os.path.join(CSRC, "generated", "tdes_generated_scalar.cuh"),
+              os.path.join(CSRC, "generated", "tdes_generated_mixed.cuh"),
               os.path.join(ROOT, "include", "tdes.h")]
     gen = os.path.join(HERE, "gen")
     files += [os.path.join(gen, f) for f in ("des_tables.py", "emit_cuda.py", "sbox_lop3.json")]

@@ -62,8 +62,8 @@ int check_call(const tdes_ks_t* ks, const void* in, const void* out, size_t nbyt
     if (nbytes % 8 != 0) return fail(TDES_EINVAL, "nbytes = %zu is not a multiple of 8", nbytes);
     *nblocks = nbytes / 8;
     if (nbytes == 0) return TDES_OK;
-    if (*nblocks / tdes::kTileBlocks >= (1ull << 32) - 1)
-        return fail(TDES_EINVAL, "a call is limited to 2^32 - 1 tiles of 8 KiB");
+    if (*nblocks / tdes::kTileBlocks >= (1ull << 31))
+        return fail(TDES_EINVAL, "a call is limited to 2^31 tiles of 8 KiB (16 TiB)");
     if (in == nullptr || out == nullptr) return fail(TDES_EINVAL, "NULL data pointer");
     const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
     if ((a | b) & 7u) return fail(TDES_EINVAL, "data pointers must be 8-byte aligned");

@@ -30,11 +30,16 @@
 #include "tdes_batch_internal.h"
 #include "tdes_internal.h"
 #include "tdes_keysched.cuh"
+#include "tdes_mixed.cuh"
 #include "tdes_scalar.cuh"
 
 namespace tdes {
 
 constexpr int kSmallBlocks = 32;                          // S messages: nblocks <= this
+// Small messages go to mixed-key tiles when the batch has at least this many
+// of their blocks (8 tiles' worth); fewer run one block per lane (S items),
+// which finish sooner alone.
+constexpr uint64_t kMixedMinBlocks = 8 * 1024;
 constexpr uint64_t kSoloChainBlocks = 512;                // longer CBC-enc chains: one per warp
 constexpr int kPerKeyWords = 2 * TDES_TABLE_WORDS;        // enc + dec bitsliced tables
 constexpr int kPerKeyChunks = 2 * TDES_SUBKEY_WORDS;      // enc + dec scalar groups
@@ -87,6 +92,25 @@ __global__ void tdes_keytable_kernel(const uint8_t* __restrict__ keys, uint32_t 
         chunks[(uint64_t)key * kPerKeyChunks + f] =
             tdes_subkey_chunk(eff, &kBatchSubkeyBits[dir][c / 8][6 * (c % 8)]);
     }
+}
+
+// Thread per (key, direction, packed word q): bit j of the word is the low
+// bit of word 32q + j of the three-pass table of the triple (EDE3 under
+// (K, K, K) for a triple that reduces: the same cipher), the form the
+// mixed-key tiles gather from.
+__global__ void tdes_keytable_pack_kernel(const uint8_t* __restrict__ keys, uint32_t count,
+                                          uint32_t* __restrict__ packed) {
+    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (uint64_t)count * 2 * kPackedWords) return;
+    const uint32_t key = (uint32_t)(e / (2 * kPackedWords));
+    const int dir = (int)(e / kPackedWords % 2), q = (int)(e % kPackedWords);
+    const uint8_t* k = keys + 24ull * key;
+    const uint8_t* single = same_des_key(k, k + 8) ? k + 16 : same_des_key(k + 8, k + 16) ? k : nullptr;
+    uint8_t eff[24];
+    for (int i = 0; i < 24; ++i) eff[i] = single ? single[i % 8] : k[i];
+    uint32_t w = 0;
+    for (int j = 0; j < 32; ++j) w |= (tdes_table_word(eff, kBatchRecipe[dir][32 * q + j]) & 1u) << j;
+    packed[e] = w;
 }
 
 // ------------------------------------------------------------ batch kernel
@@ -288,6 +312,87 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
     __syncwarp();
 }
 
+// Lane `lane` of slice sl: its message (index into msgs) and block, or false.
+__device__ __forceinline__ bool mixed_slot(const BatchParams& p, const MSlice& sl, uint32_t lane,
+                                           uint32_t* msg, uint32_t* blk) {
+    if (lane >= sl.nvalid) return false;
+    const uint32_t upto = sl.starts & (0xFFFFFFFFu >> (31u - lane));  // starts at lanes <= lane
+    *msg = p.m_list[sl.msg0 + (uint32_t)__popc(upto) - 1u];
+    *blk = lane - (31u - (uint32_t)__clz(upto));
+    return true;
+}
+
+// One mixed-key tile of small messages (ECB, CTR, CBC decryption).  Slice s
+// (bit position s of every plane) carries up to 32 blocks under its own key
+// and direction, one per lane; its table bits come from the key table's
+// packed copy, lane s loading slice s's row, and a transpose across the lanes
+// turns 32 rows into 32 table words.
+__device__ __forceinline__ void batch_mixed_tile(const BatchParams& p, uint32_t tile,
+                                                 uint32_t warp, uint32_t lane) {
+    uint32_t* wtab = reinterpret_cast<uint32_t*>(g_dyn + (size_t)warp * kWarpSmemBytes);
+    const MSlice* sl = p.m_slices + 32ull * tile;
+    {
+        const uint32_t kd = sl[lane].keydir;
+        const uint32_t* row = p.keypacked + ((uint64_t)(kd >> 1) * 2 + (kd & 1u)) * kPackedWords;
+        __syncwarp();
+#pragma unroll 1
+        for (int q = 0; q < kPackedWords; ++q)
+            wtab[32 * q + lane] = transpose_lanes32(__ldg(row + q), lane);
+        __syncwarp();
+    }
+    uint32_t A0[32], A1[32];
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+        uint32_t mi, b;
+        A0[s] = 0u;
+        A1[s] = 0u;
+        if (mixed_slot(p, sl[s], lane, &mi, &b)) {
+            const BatchMsg m = p.msgs[mi];
+            if (m.mode == TDES_MODE_CTR) {
+                A0[s] = bswap32d((uint32_t)(m.iv >> 32));
+                A1[s] = bswap32d((uint32_t)m.iv + b);
+            } else {
+                const uint2 v = reinterpret_cast<const uint2*>(m.in)[b];
+                A0[s] = v.x;
+                A1[s] = v.y;
+            }
+        }
+    }
+    tdes_process32_mixed(A0, A1, wtab);
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+        uint32_t mi, b;
+        const bool ok = mixed_slot(p, sl[s], lane, &mi, &b);
+        BatchMsg m;
+        if (ok) {
+            m = p.msgs[mi];
+            const uint2* c = reinterpret_cast<const uint2*>(m.in);
+            if (m.mode == TDES_MODE_CTR) {
+                const uint2 v = c[b];
+                A0[s] ^= v.x;
+                A1[s] ^= v.y;
+            } else if (m.mode == TDES_MODE_CBC_DECRYPT) {
+                const uint2 v = b ? c[b - 1]
+                                  : make_uint2(bswap32d((uint32_t)(m.iv >> 32)), bswap32d((uint32_t)m.iv));
+                A0[s] ^= v.x;
+                A1[s] ^= v.y;
+            }
+        }
+        __syncwarp();  // in place: every read of this slice's messages precedes its writes
+        if (ok) reinterpret_cast<uint2*>(m.out)[b] = make_uint2(A0[s], A1[s]);
+    }
+}
+
+// The mixed-key tiles of a plan, in a kernel of their own launched just
+// before the persistent kernel: inside it, their code slowed the persistent
+// kernel's other paths by 4% (alternating A/B runs on the 4096-message batch,
+// which has no mixed-key tiles).  Warps stride over the tiles.
+__global__ void __launch_bounds__(256, 2) tdes_batch_mixed_kernel(BatchParams p) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    for (uint32_t t = blockIdx.x * warps + warp; t < p.n_m_tiles; t += gridDim.x * warps)
+        batch_mixed_tile(p, t, warp, lane);
+}
+
 __device__ const uint32_t kBatchLaneSbox[32][4] = TDES_LANE_SBOX_INIT;
 __device__ const uint32_t kBatchLaneIP[32][2] = TDES_LANE_IP_INIT;
 __device__ const uint32_t kBatchLaneFP[32][2] = TDES_LANE_FP_INIT;
@@ -484,6 +589,42 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     }
     std::stable_sort(c_list.begin(), c_list.end(),
                      [&](uint32_t x, uint32_t y) { return msgs[x].nblocks > msgs[y].nblocks; });
+    // Many small messages: mixed-key tiles.  Sorted by (key, direction),
+    // they fill slices of up to 32 blocks under one key and direction (a
+    // message never splits), and 32 slices make a tile.
+    std::vector<uint32_t> m_list;
+    std::vector<MSlice> m_slices;
+    uint64_t small_blocks = 0;
+    for (uint32_t mi : s_list) small_blocks += msgs[mi].nblocks;
+    if (small_blocks >= kMixedMinBlocks) {
+        auto keydir = [&](uint32_t mi) {
+            const uint32_t dir = (msgs[mi].mode == TDES_MODE_ECB_DECRYPT ||
+                                  msgs[mi].mode == TDES_MODE_CBC_DECRYPT) ? 1u : 0u;
+            return (msgs[mi].key << 1) | dir;
+        };
+        std::stable_sort(s_list.begin(), s_list.end(),
+                         [&](uint32_t x, uint32_t y) { return keydir(x) < keydir(y); });
+        MSlice cur = {0, 0, 0, 0};
+        bool open = false;
+        for (uint32_t mi : s_list) {
+            const uint32_t kd = keydir(mi), nb = (uint32_t)msgs[mi].nblocks;
+            if (open && (cur.keydir != kd || cur.nvalid + nb > 32u)) {
+                m_slices.push_back(cur);
+                open = false;
+            }
+            if (!open) {
+                cur = {(uint32_t)m_list.size(), 0u, 0u, kd};
+                open = true;
+            }
+            cur.starts |= 1u << cur.nvalid;
+            cur.nvalid += nb;
+            m_list.push_back(mi);
+        }
+        if (open) m_slices.push_back(cur);
+        while (m_slices.size() % 32) m_slices.push_back({0u, 0u, 0u, 0u});  // empty slices
+        h->n_m_tiles = (uint32_t)(m_slices.size() / 32);
+        s_list.clear();
+    }
     for (uint32_t i = 0; i < s_list.size();) {  // small messages packed whole, <= 32 blocks
         const uint32_t first = i;
         uint32_t blocks = 0;
@@ -498,7 +639,7 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     h->n_b = (uint32_t)b_msg.size();
     h->n_b_tiles = b_prefix.back();
     h->n_s_items = (uint32_t)s_items.size();
-    h->total_items = (uint64_t)h->n_c_items + h->n_b_tiles + h->n_s_items;
+    h->total_items = (uint64_t)h->n_c_items + h->n_b_tiles + h->n_m_tiles + h->n_s_items;
     size_t off = 0;
     auto take = [&](size_t n) { const size_t o = align16(off); off = o + n; return o; };
     h->o_msgs = take(msgs.size() * sizeof(BatchMsg));
@@ -506,6 +647,8 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     h->o_bm = take(b_msg.size() * 4);
     h->o_bp = take(b_prefix.size() * 8);
     h->o_bt = take(h->n_b_tiles * 4);
+    h->o_ml = take(m_list.size() * 4);
+    h->o_ms = take(m_slices.size() * sizeof(MSlice));
     h->o_sl = take(s_list.size() * 4);
     h->o_si = take(s_items.size() * sizeof(uint2));
     h->o_halo = take(h->needs_halo ? h->n_b_tiles * 8 : 0);
@@ -521,6 +664,8 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     uint32_t* bt = reinterpret_cast<uint32_t*>(h->image.data() + h->o_bt);
     for (uint32_t i = 0; i < h->n_b; ++i)
         std::fill(bt + b_prefix[i], bt + b_prefix[i + 1], i);
+    put(h->o_ml, m_list.data(), m_list.size() * 4);
+    put(h->o_ms, m_slices.data(), m_slices.size() * sizeof(MSlice));
     put(h->o_sl, s_list.data(), s_list.size() * 4);
     put(h->o_si, s_items.data(), s_items.size() * sizeof(uint2));
 }
@@ -541,6 +686,10 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
     p.b_tile = reinterpret_cast<const uint32_t*>(base + h.o_bt);
     p.n_b = h.n_b;
     p.n_b_tiles = h.n_b_tiles;
+    p.keypacked = kt->packed;
+    p.m_list = reinterpret_cast<const uint32_t*>(base + h.o_ml);
+    p.m_slices = reinterpret_cast<const MSlice*>(base + h.o_ms);
+    p.n_m_tiles = h.n_m_tiles;
     p.s_list = reinterpret_cast<const uint32_t*>(base + h.o_sl);
     p.s_items = reinterpret_cast<const uint2*>(base + h.o_si);
     p.n_s_items = h.n_s_items;
@@ -556,6 +705,9 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
     cudaError_t e = cudaFuncSetAttribute(tdes_batch_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8 * kWarpSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tdes_batch_mixed_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kWarpSmemBytes);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_batch_kernel, 32 * warps, dyn);
@@ -585,6 +737,13 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
         tdes_batch_halo_kernel<<<(unsigned)((p.n_b_tiles + 255) / 256), 256, 0, s>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (p.n_m_tiles) {  // small messages of their own keys: disjoint from the rest
+        const uint64_t want = (p.n_m_tiles + warps - 1) / (uint64_t)warps;
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
+        tdes_batch_mixed_kernel<<<grid, 32 * warps, dyn_smem, s>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (total_items == 0) return cudaSuccess;
     const uint64_t want = (total_items + warps - 1) / (uint64_t)warps;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
     tdes_batch_kernel<<<grid, 32 * warps, dyn_smem, s>>>(p);
@@ -664,8 +823,9 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
     const size_t chunk_bytes = tdes::align16((size_t)count * tdes::kPerKeyChunks);
     const size_t key_bytes = tdes::align16((size_t)count * 24);
     const size_t stage_bytes = tdes::align16(count);
+    const size_t packed_bytes = (size_t)count * 2 * tdes::kPackedWords * 4;
     void* mem = nullptr;
-    e = cudaMalloc(&mem, tab_bytes + chunk_bytes + key_bytes + stage_bytes);
+    e = cudaMalloc(&mem, tab_bytes + chunk_bytes + key_bytes + stage_bytes + packed_bytes);
     if (e != cudaSuccess) return bcuda(e, "cudaMalloc(key table)");
     tdes_keytable_t* kt = new (std::nothrow) tdes_keytable_t;
     if (kt == nullptr) {
@@ -679,6 +839,7 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
     kt->chunks = static_cast<uint8_t*>(mem) + tab_bytes;
     uint8_t* dkeys = kt->chunks + chunk_bytes;
     kt->stages = dkeys + key_bytes;
+    kt->packed = reinterpret_cast<uint32_t*>(kt->stages + stage_bytes);
     cudaStream_t s = nullptr;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess)
@@ -688,6 +849,12 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
         tdes::tdes_keytable_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
             dkeys, count, kt->tabs, kt->chunks, kt->stages);
         e = cudaGetLastError();
+        const uint64_t np = (uint64_t)count * 2 * tdes::kPackedWords;
+        if (e == cudaSuccess) {
+            tdes::tdes_keytable_pack_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
+                dkeys, count, kt->packed);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(dkeys, 0, (size_t)count * 24, s);  // keys not kept
     if (s) {
@@ -805,6 +972,7 @@ int tdes_batch_info(const tdes_batch_t* b, tdes_batch_info_t* info) {
     info->n_cbc_enc_messages = b->params.n_c;
     info->n_tiles = b->params.n_b_tiles;
     info->n_small_items = b->params.n_s_items;
+    info->n_mixed_tiles = b->params.n_m_tiles;
     info->warps_per_cta = b->warps;
     info->ctas_per_sm = b->ctas_per_sm;
     for (int i = 0; i < 5; ++i) info->bytes_per_mode[i] = b->bytes[i];

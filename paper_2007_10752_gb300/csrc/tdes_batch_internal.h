@@ -15,9 +15,21 @@ struct tdes_keytable {
     uint32_t* tabs;   // [key][dir][3328] bitsliced round-constant tables
     uint8_t* chunks;  // [key][dir][384] scalar round-key words
     uint8_t* stages;  // [key] DES passes: 3, or 1 for a triple that reduces to single DES
+    uint32_t* packed; // [key][dir][104] three-pass tables, one bit per word (mixed-key tiles)
 };
 
 namespace tdes {
+
+constexpr int kPackedWords = 104;  // 3328 table words at one bit each
+
+// One slice (bit position) of a mixed-key tile: up to 32 blocks of small
+// messages under one key and direction, one block per lane.
+struct MSlice {
+    uint32_t msg0;    // first of the slice's messages in m_list
+    uint32_t starts;  // bit l set where a message begins at lane l
+    uint32_t nvalid;  // lanes [0, nvalid) hold blocks
+    uint32_t keydir;  // key << 1 | direction (1: decryption table)
+};
 
 struct BatchMsg {
     const uint8_t* in;
@@ -41,6 +53,10 @@ struct BatchParams {
     const uint32_t* b_tile;    // per B tile: its B entry (index into b_msg / b_prefix)
     uint32_t n_b;
     uint64_t n_b_tiles;
+    const uint32_t* keypacked; // [key][dir][kPackedWords]
+    const uint32_t* m_list;    // small messages in mixed-key tiles, in slice order
+    const MSlice* m_slices;    // 32 per mixed-key tile
+    uint32_t n_m_tiles;
     const uint32_t* s_list;    // small message indices
     const uint2* s_items;      // (first, count) into s_list, whole messages, <= 32 blocks
     uint32_t n_s_items;
@@ -54,9 +70,9 @@ struct BatchParams {
 // A batch laid out on the host as the byte image of its device buffer.
 struct PlanHost {
     std::vector<uint8_t> image;
-    size_t o_msgs = 0, o_c = 0, o_bm = 0, o_bp = 0, o_bt = 0, o_sl = 0, o_si = 0, o_halo = 0,
-           o_ctr = 0;
-    uint32_t n_c = 0, n_c_solo = 0, n_c_items = 0, n_b = 0, n_s_items = 0;
+    size_t o_msgs = 0, o_c = 0, o_bm = 0, o_bp = 0, o_bt = 0, o_ml = 0, o_ms = 0, o_sl = 0,
+           o_si = 0, o_halo = 0, o_ctr = 0;
+    uint32_t n_c = 0, n_c_solo = 0, n_c_items = 0, n_b = 0, n_m_tiles = 0, n_s_items = 0;
     uint64_t n_b_tiles = 0, total_items = 0;
     bool needs_halo = false;
     uint64_t bytes_per_mode[5] = {0, 0, 0, 0, 0};

@@ -266,28 +266,46 @@ def emit(path: str = OUT) -> str:
     L.append("")
     L.append("// Needs TDES_HD and lop3<LUT>(a, b, c) from tdes_bitslice.cuh.")
     L.append("")
-    L.append("// One round: T ^= f(S, round key).  S and T hold keyed planes; k points at")
-    L.append("// this round's 64 constants (per S-box: 4 update masks, 2 masks of the")
-    L.append("// doubled expansion inputs, 2 multipliers = mask | 1), in shared memory.")
-    L.append("TDES_HD void tdes_round(uint32_t (&T)[32], const uint32_t (&S)[32],")
-    L.append("                        const uint32_t* __restrict__ k) {")
-    for g in range(8):
-        circ = sboxes[g]
-        L.append(f"    {{  // S-box {g + 1}")
-        L.append(f"    const uint4 kd = *reinterpret_cast<const uint4*>(k + {8 * g + 4});")
-        for u in range(6):
-            j = 6 * g + u
-            i = T.E[j] - 1
-            if u == 0:
-                L.append(f"    const uint32_t x0 = S[{i}] * kd.z + kd.x;  // second copy: XOR by multiply-add")
-            elif u == 1:
-                L.append(f"    const uint32_t x1 = S[{i}] * kd.w + kd.y;")
-            else:
-                L.append(f"    const uint32_t x{u} = S[{i}];")
-        outs = emit_sbox(L, g, circ, P_INV[4 * g:4 * g + 4])
-        L.append("    }")
-    L.append("}")
-    L.append("")
+    mixed_lines = []
+    for mixed in (False, True):
+        if mixed:  # into its own header: only the batch kernel's mixed-key tiles use it
+            main_lines, L = L, mixed_lines
+        if not mixed:
+            L.append("// One round: T ^= f(S, round key).  S and T hold keyed planes; k points at")
+            L.append("// this round's 64 constants (per S-box: 4 update masks, 2 masks of the")
+            L.append("// doubled expansion inputs, 2 multipliers = mask | 1), in shared memory.")
+            L.append("TDES_HD void tdes_round(uint32_t (&T)[32], const uint32_t (&S)[32],")
+            L.append("                        const uint32_t* __restrict__ k) {")
+        else:
+            L.append("// The same round for tables whose masks differ from bit to bit (one key")
+            L.append("// per bit position: tiles of small messages under many keys).  The")
+            L.append("// multiply-add form of a masked XOR holds only for all-0 or all-1 masks,")
+            L.append("// so the doubled expansion inputs take a plain XOR; the multipliers are")
+            L.append("// not read.")
+            L.append("TDES_HD void tdes_round_mixed(uint32_t (&T)[32], const uint32_t (&S)[32],")
+            L.append("                              const uint32_t* __restrict__ k) {")
+        for g in range(8):
+            circ = sboxes[g]
+            L.append(f"    {{  // S-box {g + 1}")
+            L.append(f"    const uint4 kd = *reinterpret_cast<const uint4*>(k + {8 * g + 4});")
+            for u in range(6):
+                j = 6 * g + u
+                i = T.E[j] - 1
+                if u == 0 and not mixed:
+                    L.append(f"    const uint32_t x0 = S[{i}] * kd.z + kd.x;  // second copy: XOR by multiply-add")
+                elif u == 1 and not mixed:
+                    L.append(f"    const uint32_t x1 = S[{i}] * kd.w + kd.y;")
+                elif u == 0:
+                    L.append(f"    const uint32_t x0 = S[{i}] ^ kd.x;  // second copy")
+                elif u == 1:
+                    L.append(f"    const uint32_t x1 = S[{i}] ^ kd.y;")
+                else:
+                    L.append(f"    const uint32_t x{u} = S[{i}];")
+            emit_sbox(L, g, circ, P_INV[4 * g:4 * g + 4])
+            L.append("    }")
+        L.append("}")
+        L.append("")
+    L = main_lines
     L.append("// Initial permutation: transposed words A0/A1 (bit position -> plane) to halves.")
     L.append("TDES_HD void tdes_ip(const uint32_t (&A0)[32], const uint32_t (&A1)[32],")
     L.append("                     uint32_t (&Lh)[32], uint32_t (&Rh)[32]) {")
@@ -322,6 +340,16 @@ def emit(path: str = OUT) -> str:
         L.append("}")
     text = "\n".join(L) + "\n"
     _write(path, text)
+    hdr = ["// GENERATED by paper_2007_10752_gb300/gen/emit_cuda.py -- do not edit.",
+           "// Round of the bitsliced path for tables with a different key per bit",
+           "// position (from the S-box circuits in gen/sbox_lop3.json).",
+           "#pragma once",
+           "#include <cstdint>",
+           "",
+           "// Needs TDES_HD and lop3<LUT>(a, b, c) from tdes_bitslice.cuh.",
+           ""]
+    _write(os.path.join(os.path.dirname(path), "tdes_generated_mixed.cuh"),
+           "\n".join(hdr + mixed_lines) + "\n")
     L = []
     L.append("// GENERATED by paper_2007_10752_gb300/gen/emit_cuda.py -- do not edit.")
     L.append("// Tables of the scalar (one block per thread) 3DES path, from Appendix A.")

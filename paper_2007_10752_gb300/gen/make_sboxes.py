@@ -1,9 +1,10 @@
 """Search LOP3 circuits for the eight DES S-boxes and store the smallest found.
 
-Compiles ``sbox_search.c`` with gcc, runs one search process per S-box in
-parallel, checks every returned circuit exhaustively (all 64 inputs) against
-the S-box table of ``des_tables.py``, and rewrites ``sbox_lop3.json`` for any
-S-box where the new circuit has fewer gates than the stored one.
+Compiles ``sbox_search.c`` and ``resub_sboxes.c`` with gcc, runs one search
+process per S-box in parallel, passes each returned circuit through the
+resubstitution post-pass, checks every circuit exhaustively (all 64 inputs)
+against the S-box table of ``des_tables.py``, and rewrites ``sbox_lop3.json``
+for any S-box where the new circuit has fewer gates than the stored one.
 
 Run:  python -m paper_2007_10752_gb300.gen.make_sboxes [iterations] [seed] [extra args]
 """
@@ -77,6 +78,19 @@ def parse(text: str):
     return {"gates": gates, "outputs": outs}
 
 
+def to_text(circ) -> str:
+    """A circuit in the text format of sbox_search.c (input of resub_sboxes.c)."""
+    lines = [f"g {6 + i} {a} {b} {c} {lut}" for i, (a, b, c, lut) in enumerate(circ["gates"])]
+    lines += [f"out {t} {gid} {neg}" for t, (gid, neg) in enumerate(circ["outputs"])]
+    return "\n".join(lines) + "\n"
+
+
+def resub(exe: str, circ):
+    """The circuit after the resubstitution post-pass (or unchanged if it fails)."""
+    r = subprocess.run([exe], input=to_text(circ), capture_output=True, text=True)
+    return parse(r.stdout) if r.returncode == 0 else circ
+
+
 def load():
     if os.path.exists(JSON_PATH):
         with open(JSON_PATH) as f:
@@ -88,8 +102,11 @@ def main(argv):
     iters = argv[0] if argv else "30"
     seed = argv[1] if len(argv) > 1 else "1"
     extra = argv[2:] if len(argv) > 2 else ["0", "1", "99"]
-    exe = os.path.join(tempfile.mkdtemp(prefix="sbox_search_"), "sbox_search")
+    tmp = tempfile.mkdtemp(prefix="sbox_search_")
+    exe = os.path.join(tmp, "sbox_search")
+    rexe = os.path.join(tmp, "resub_sboxes")
     subprocess.check_call(["gcc", "-O3", "-o", exe, os.path.join(HERE, "sbox_search.c")])
+    subprocess.check_call(["gcc", "-O3", "-o", rexe, os.path.join(HERE, "resub_sboxes.c")])
     procs = []
     for g in range(8):
         tts = des_tables.sbox_truth_tables(g)
@@ -106,6 +123,9 @@ def main(argv):
         circ = parse(out)
         if not verify(g, circ):
             raise SystemExit(f"S{g + 1}: search returned a wrong circuit")
+        small = resub(rexe, circ)
+        if verify(g, small) and len(small["gates"]) < len(circ["gates"]):
+            circ = small
         old = store["sboxes"][g]
         n_new, n_old = len(circ["gates"]), (len(old["gates"]) if old else None)
         print(f"S{g + 1}: {n_new} gates (stored: {n_old})")

@@ -79,7 +79,8 @@ class BatchInfo(ctypes.Structure):
     """tdes_batch_info_t"""
     _fields_ = [("n_cbc_enc_messages", ctypes.c_uint32), ("n_tiles", ctypes.c_uint64),
                 ("n_small_items", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int), ("bytes_per_mode", ctypes.c_uint64 * 5)]
+                ("ctas_per_sm", ctypes.c_int), ("bytes_per_mode", ctypes.c_uint64 * 5),
+                ("n_mixed_tiles", ctypes.c_uint64)]
 
 _lib = None
 
@@ -385,7 +386,8 @@ class Batch:
         _check(load().tdes_batch_info(self.handle, ctypes.byref(bi)))
         return {"n_cbc_enc_messages": bi.n_cbc_enc_messages, "n_tiles": bi.n_tiles,
                 "n_small_items": bi.n_small_items, "warps_per_cta": bi.warps_per_cta,
-                "ctas_per_sm": bi.ctas_per_sm, "bytes_per_mode": list(bi.bytes_per_mode)}
+                "ctas_per_sm": bi.ctas_per_sm, "bytes_per_mode": list(bi.bytes_per_mode),
+                "n_mixed_tiles": bi.n_mixed_tiles}
 
     def free(self):
         if self.handle:

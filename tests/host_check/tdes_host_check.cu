@@ -10,6 +10,8 @@
 //   b1_*: the single-DES (one-pass) bitsliced tables and rounds under K1.
 //   s1_*: the 16-round scalar round on the key words of (K1, K1, K1), as the
 //         library builds them for a single-DES schedule.
+//   mx_*: the mixed-key round (tdes_process32_mixed): block b of each group
+//         of 32 is slot b, under the triple whose K1 has byte 0 XOR (2 * b).
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -17,6 +19,7 @@
 
 #include "../../paper_2007_10752_gb300/csrc/tdes_keysched.cuh"
 #include "../../paper_2007_10752_gb300/csrc/tdes_scalar.cuh"
+#include "../../paper_2007_10752_gb300/csrc/tdes_mixed.cuh"
 
 static const uint8_t kRecipe[2][TDES_TABLE_WORDS][3] = TDES_RECIPE_INIT;
 static const uint8_t kRecipe1[2][TDES1_TABLE_WORDS][3] = TDES1_RECIPE_INIT;
@@ -40,6 +43,7 @@ int main(int argc, char** argv) {
         memcpy(keys + 16, keys, 8);
     }
     const bool bitsliced = argv[1][0] == 'b';
+    const bool mixed = strncmp(argv[1], "mx", 2) == 0;
     const bool one_pass = strncmp(argv[1], "b1", 2) == 0;
     std::vector<uint8_t> data;
     uint8_t buf[1 << 16];
@@ -49,7 +53,33 @@ int main(int argc, char** argv) {
     const size_t n = data.size() / 8;
     std::vector<uint8_t> out(data.size());
 
-    if (bitsliced) {
+    if (mixed) {
+        alignas(16) static uint32_t tab[TDES_TABLE_WORDS];
+        for (int e = 0; e < TDES_TABLE_WORDS; ++e) {
+            uint32_t w = 0;
+            for (int sl = 0; sl < 32; ++sl) {
+                uint8_t k[24];
+                memcpy(k, keys, 24);
+                k[0] ^= (uint8_t)(2 * sl);
+                w |= (tdes_table_word(k, kRecipe[dec][e]) & 1u) << sl;
+            }
+            tab[e] = w;
+        }
+        for (size_t g0 = 0; g0 < n; g0 += 32) {
+            uint32_t A0[32], A1[32];
+            for (int sl = 0; sl < 32; ++sl) {
+                uint32_t w[2] = {0, 0};
+                if (g0 + sl < n) memcpy(w, &data[8 * (g0 + sl)], 8);
+                A0[sl] = w[0];
+                A1[sl] = w[1];
+            }
+            tdes_process32_mixed(A0, A1, tab);
+            for (int sl = 0; sl < 32 && g0 + sl < n; ++sl) {
+                uint32_t w[2] = {A0[sl], A1[sl]};
+                memcpy(&out[8 * (g0 + sl)], w, 8);
+            }
+        }
+    } else if (bitsliced) {
         alignas(16) static uint32_t tab[TDES_TABLE_WORDS];
         if (one_pass)
             for (int e = 0; e < TDES1_TABLE_WORDS; ++e) tab[e] = tdes_table_word(keys, kRecipe1[dec][e]);

@@ -42,7 +42,7 @@ def test_sbox_circuits_match_oracle_exhaustively():
 def test_generated_headers_are_current(tmp_path):
     emit_cuda.emit(str(tmp_path / "tdes_generated.cuh"))
     gen_dir = os.path.join(ROOT, "paper_2007_10752_gb300", "csrc", "generated")
-    for name in ("tdes_generated.cuh", "tdes_generated_scalar.cuh"):
+    for name in ("tdes_generated.cuh", "tdes_generated_scalar.cuh", "tdes_generated_mixed.cuh"):
         assert open(tmp_path / name).read() == open(os.path.join(gen_dir, name)).read(), name
 
 
@@ -112,3 +112,62 @@ def test_generated_code_matches_oracle(host_check, name, mk, mode):
     else:
         want = oracle.tdes_ecb(keys, data, decrypt=mode.endswith("dec"))
     assert (got == want).all()
+
+
+def _plant_copy(circ):
+    """The circuit with a copy of a gate that has two or more readers, placed
+    right after it, and one reader moved onto the copy: the same function with
+    one redundant gate."""
+    gates, outs = circ["gates"], circ["outputs"]
+    readers = {}
+    for i, (a, b, c, _) in enumerate(gates):
+        for s_ in {a, b, c}:
+            readers.setdefault(s_, []).append(i)
+    src = next(i for i in range(len(gates)) if len(readers.get(6 + i, [])) >= 2)
+    moved_reader = readers[6 + src][-1]
+
+    def rn(s_):  # signals after the source gate move up by one
+        return s_ + 1 if s_ > 6 + src else s_
+    new = []
+    for i, (a, b, c, lut) in enumerate(gates):
+        x = [rn(a), rn(b), rn(c), lut]
+        if i == moved_reader:
+            x = [7 + src if v == 6 + src else v for v in x[:3]] + [lut]
+        new.append(x)
+        if i == src:
+            new.append([rn(a), rn(b), rn(c), lut])
+    return {"gates": new, "outputs": [[rn(gid), neg] for gid, neg in outs]}
+
+
+def test_resub_pass_keeps_function_and_removes_planted_redundancy(tmp_path):
+    """The resubstitution post-pass leaves every stored circuit's outputs
+    unchanged, and takes out a gate planted as a copy of another gate."""
+    exe = str(tmp_path / "resub")
+    subprocess.check_call(["gcc", "-O3", "-o", exe, os.path.join(GEN, "resub_sboxes.c")])
+    store = json.load(open(os.path.join(GEN, "sbox_lop3.json")))
+    for g, circ in enumerate(store["sboxes"]):
+        out = make_sboxes.resub(exe, circ)
+        assert make_sboxes.verify(g, out), g
+        assert len(out["gates"]) <= len(circ["gates"])
+        planted = _plant_copy(circ)
+        assert make_sboxes.verify(g, planted) and len(planted["gates"]) == len(circ["gates"]) + 1
+        small = make_sboxes.resub(exe, planted)
+        assert make_sboxes.verify(g, small), g
+        assert len(small["gates"]) <= len(circ["gates"]), g
+
+
+@pytest.mark.parametrize("name,mk", KEYSETS[:2], ids=[k[0] for k in KEYSETS[:2]])
+@pytest.mark.parametrize("mode", ["mx_enc", "mx_dec"])
+def test_mixed_key_round_matches_oracle(host_check, name, mk, mode):
+    """Tables whose 32 bit positions carry 32 different triples (the batch
+    kernel's tiles of small messages): block b of every group of 32 is
+    encrypted under its own triple."""
+    keys = bytearray(mk())
+    data = synth.random_bytes(len(name) * 17 + 3, 8 * 75)
+    got = _run(host_check, mode, bytes(keys), data)
+    for b in range(75):
+        k = bytearray(keys)
+        k[0] ^= 2 * (b % 32)
+        want = oracle.tdes_ecb(bytes(k), data[8 * b:8 * b + 8], decrypt=mode.endswith("dec"))
+        assert (got[8 * b:8 * b + 8] == want).all(), (mode, b)
+

@@ -276,3 +276,50 @@ def test_key_tables_with_single_des_triples(cuda_lib):
     for i, (got, m) in enumerate(zip(outputs(arena, msgs), msgs)):
         want = oracle_msg(m["mode"], triples[m["key"]], m["iv"], m["data"])
         assert (got == want).all(), f"message {i}: key {m['key']} mode {m['mode']} {m['nb']} blocks"
+
+
+def test_many_small_messages_share_mixed_key_tiles(cuda_lib):
+    """A batch with more than 8192 blocks of small (<= 32-block) messages
+    packs them into bitsliced tiles whose 32 bit positions carry different
+    key triples and directions: every message equals the oracle, for every
+    mode, ragged sizes, repeated and single-DES-reducing keys, in-place and
+    8-byte-aligned buffers."""
+    T = cuda_lib
+    rng = np.random.default_rng(41)
+    t = synth.key_triples(41, 40)
+    a = t[0].tobytes()[:8]
+    triples = [x.tobytes() for x in t]
+    triples[1] = a + a + t[1].tobytes()[16:]      # K1 = K2: single DES under K3
+    triples[2] = t[2].tobytes()[:8] * 3           # K1 = K2 = K3
+    keys = np.frombuffer(b"".join(triples), dtype=np.uint8).reshape(-1, 24).copy()
+    kt = T.KeyTable(keys)
+    msgs, off = [], 0
+    for i in range(1400):
+        nb = int(rng.integers(1, 33))
+        mode = int(rng.integers(0, 5))
+        key = int(rng.integers(0, len(triples)))
+        iv = int(synth.words(41, i, 1, synth.STREAM_IV)[0])
+        if mode == 2:
+            iv = (iv & 0xFFFFFFFF00000000) | int(rng.integers(0, 1 << 20))
+        in_place = rng.random() < 0.3
+        off = (off + 15) // 16 * 16 + (8 if rng.random() < 0.3 else 0)
+        in_off = off
+        off += 8 * nb
+        out_off = in_off if in_place else (off + 15) // 16 * 16
+        if not in_place:
+            off = out_off + 8 * nb
+        msgs.append(dict(mode=mode, key=key, iv=iv, nb=nb, in_off=in_off, out_off=out_off,
+                         data=synth.random_bytes(4100 + i, 8 * nb)))
+    arena = torch.zeros(off + 64, dtype=torch.uint8, device="cuda")
+    restage(arena, msgs)
+    b = T.Batch(kt, entries_for(arena, msgs))
+    assert (b.status == 0).all()
+    info = b.info()
+    assert info["n_mixed_tiles"] > 0 and info["n_small_items"] == 0
+    for shape in [(8, 0), (4, 0)]:
+        restage(arena, msgs)
+        b.configure(*shape)
+        b.launch_graph()
+        for i, (got, m) in enumerate(zip(outputs(arena, msgs), msgs)):
+            want = oracle_msg(m["mode"], triples[m["key"]], m["iv"], m["data"])
+            assert (got == want).all(), f"{shape} message {i}: mode {m['mode']} {m['nb']} blocks"
