@@ -24,7 +24,7 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec", "cbc_enc", "batch",
-                                         "batch_ctr"],
+                                         "batch_ctr", "batch_cbc_enc"],
                     default="ecb")
     ap.add_argument("--mib", type=int, default=256)
     ap.add_argument("--kib", type=int, default=0, help="size in KiB (overrides --mib)")
@@ -51,6 +51,18 @@ def main():
         return
     n = (args.kib << 10) if args.kib else (args.mib << 20)
     keys = synth.key_triple(2)
+    if args.kernel == "batch_cbc_enc":
+        # one CBC-encryption chain as a batch (walked by one warp)
+        import numpy as np
+        x = torch.from_numpy(synth.random_bytes(2, n)).cuda()
+        y = torch.empty_like(x)
+        kt = tdes.KeyTable(np.frombuffer(keys, dtype=np.uint8).reshape(1, 24))
+        b = tdes.Batch(kt, [(tdes.MODE_CBC_ENCRYPT, 0, 5, x.data_ptr(), y.data_ptr(), n)])
+        for _ in range(args.launches):
+            b.launch()
+        torch.cuda.synchronize()
+        print(f"batch_cbc_enc: {args.launches} launches on {n >> 10} KiB done")
+        return
     if args.kernel == "batch_ctr":
         # the single-key CTR stream of the large streaming workload, at this size
         import numpy as np
