@@ -136,6 +136,69 @@ def cpu_baseline(keys: bytes, seconds: float = 12.0):
             "single_thread_gbs": g1}
 
 
+def openssl_reference(keys: bytes, data, gpu_out, seconds: float = 6.0):
+    """OpenSSL's DES-EDE3 ECB (libcrypto EVP) on the host cores, if the library
+    is there: a practical CPU implementation for context (not the oracle).  Its
+    output on the first MiB is compared with the GPU's output of the timed step."""
+    import ctypes
+    import ctypes.util
+    import threading
+    name = ctypes.util.find_library("crypto")
+    if not name:
+        return {"unavailable": "libcrypto not found on this host"}
+    lib = ctypes.CDLL(name)
+    vp, cp, ip = ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)
+    lib.EVP_CIPHER_CTX_new.restype = vp
+    lib.EVP_des_ede3_ecb.restype = vp
+    lib.EVP_EncryptInit_ex.argtypes = [vp, vp, vp, cp, cp]
+    lib.EVP_CIPHER_CTX_set_padding.argtypes = [vp, ctypes.c_int]
+    lib.EVP_EncryptUpdate.argtypes = [vp, vp, ip, vp, ctypes.c_int]
+    lib.EVP_CIPHER_CTX_free.argtypes = [vp]
+    cipher = lib.EVP_des_ede3_ecb()
+    if not cipher:
+        return {"unavailable": "DES-EDE3 not offered by this libcrypto"}
+
+    def run(src, dst):
+        ctx = lib.EVP_CIPHER_CTX_new()
+        lib.EVP_EncryptInit_ex(ctx, cipher, None, keys, None)
+        lib.EVP_CIPHER_CTX_set_padding(ctx, 0)
+        outl = ctypes.c_int(0)
+        chunk = 1 << 24
+        for off in range(0, len(src), chunk):
+            n = min(chunk, len(src) - off)
+            lib.EVP_EncryptUpdate(ctx, ctypes.c_void_p(dst.ctypes.data + off), ctypes.byref(outl),
+                                  ctypes.c_void_p(src.ctypes.data + off), n)
+        lib.EVP_CIPHER_CTX_free(ctx)
+
+    import numpy as np
+    head = data[: 1 << 20]
+    out = np.empty_like(head)
+    run(head, out)
+    agrees = bool((out == gpu_out[: 1 << 20]).all())
+    t = time.perf_counter()
+    run(head, out)
+    rate1 = head.size / max(time.perf_counter() - t, 1e-6)
+    n1 = int(min(max(rate1 * seconds / 2, 1 << 20), data.size)) // 8 * 8
+    buf = np.empty(n1, dtype=np.uint8)
+    t = time.perf_counter()
+    run(data[:n1], buf)
+    g1 = n1 / (time.perf_counter() - t) / 1e9
+    cores = os.cpu_count() or 1
+    per = n1 // cores // 8 * 8
+    outs = [np.empty(per, dtype=np.uint8) for _ in range(cores)]
+    ths = [threading.Thread(target=run, args=(data[i * per:(i + 1) * per], outs[i]))
+           for i in range(cores)]
+    t = time.perf_counter()
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    gn = per * cores / (time.perf_counter() - t) / 1e9
+    return {"kind": "openssl EVP des-ede3-ecb", "version": int(lib.OpenSSL_version_num()),
+            "gbs_1_thread": round(g1, 4), "gbs_all_threads": round(gn, 4), "threads": cores,
+            "sample_bytes": n1, "agrees_with_gpu_on_first_mib": agrees}
+
+
 # ---------------------------------------------------------------- roofline
 def alg_ops_per_32_blocks(stages: int = 3) -> int:
     """Logic-pipe operations the bitsliced ECB algorithm needs per 32 blocks.
@@ -274,6 +337,7 @@ def run_ours(args):
     tdes.tdes_ecb_decrypt(ks, y, z)
     torch.cuda.synchronize()
     assert torch.equal(z, x), "ECB decrypt(encrypt(x)) != x"
+    ecb_out = y[: 1 << 20].cpu().numpy()  # checked against OpenSSL on the host below
     del z
 
     # ---- other modes of the same workload, and the 1 MiB single launch
@@ -295,6 +359,10 @@ def run_ours(args):
     small_in, small_out = x[: 1 << 20], y[: 1 << 20]
     small_us = graph_call_ms(torch, lambda: tdes.tdes_ecb_encrypt(ks, small_in, small_out)) * 1e3
     small_call_us = time_fn(lambda: tdes.tdes_ecb_encrypt(ks, small_in, small_out), 200) * 1e3
+
+    # ---- one serial CBC-encryption chain through the single-message call
+    n_chain = 1 << 16
+    chain_ms = time_fn(lambda: tdes.tdes_cbc_encrypt(ks, 5, x[: 8 * n_chain], y[: 8 * n_chain]), 2)
 
     # ---- single DES (a DES schedule, or a triple that reduces): one pass
     kd = tdes.KeySchedule.des(keys[:8])
@@ -402,6 +470,7 @@ def run_ours(args):
                   "ctr_gbs": round(NBYTES / (ctr_ms * 1e-3) / 1e9, 3),
                   "ecb_1mib_single_launch_us": round(small_us, 2),
                   "ecb_1mib_python_call_us": round(small_call_us, 2),
+                  "cbc_encrypt_chain_ns_per_block": round(chain_ms * 1e6 / n_chain, 1),
                   "key_schedule_ms": round(keysched_ms, 3),
                   "sbox_lop3_per_round": tdes.tdes_sbox_gate_count()},
     }
@@ -419,6 +488,7 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(keys)
+        line["cpu_library_reference"] = openssl_reference(keys, host, ecb_out)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -393,24 +393,6 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_mixed_kernel(BatchParams p)
         batch_mixed_tile(p, t, warp, lane);
 }
 
-__device__ const uint32_t kBatchLaneSbox[32][4] = TDES_LANE_SBOX_INIT;
-__device__ const uint32_t kBatchLaneIP[32][2] = TDES_LANE_IP_INIT;
-__device__ const uint32_t kBatchLaneFP[32][2] = TDES_LANE_FP_INIT;
-
-// One CBC-encryption chain walked by the whole warp; the next plaintext block
-// is loaded one block ahead.
-template <int ROUNDS>
-__device__ __forceinline__ void warp_chain(const BatchMsg& m, const LaneConsts& c,
-                                           const uint8_t* keys, uint32_t lane) {
-    uint64_t prev = m.iv;
-    uint64_t next = load_be(m.in, 0);
-    for (uint64_t i = 0; i < m.nblocks; ++i) {
-        const uint64_t x = next ^ prev;
-        if (i + 1 < m.nblocks) next = load_be(m.in, i + 1);
-        prev = tdes_block_warp<ROUNDS>(x, c, keys);
-        if (lane == 0) store_be(m.out, i, prev);
-    }
-}
 
 // One short CBC-encryption chain per lane (scalar round); the next block is
 // loaded one iteration ahead, so its latency hides behind the current block.
@@ -441,19 +423,10 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
         for (int i = lane; i < TDES_SUBKEY_WORDS / 16; i += 32)
             reinterpret_cast<uint4*>(warp_smem)[i] = __ldg(reinterpret_cast<const uint4*>(kg) + i);
         __syncwarp();
-        LaneConsts c;
-        c.mlo = kBatchLaneSbox[lane][0];
-        c.mhi = kBatchLaneSbox[lane][1];
-        c.rot = kBatchLaneSbox[lane][2];
-        c.keypos = kBatchLaneSbox[lane][3];
-        c.ip_hi = kBatchLaneIP[lane][0];
-        c.ip_lo = kBatchLaneIP[lane][1];
-        c.fp_hi = kBatchLaneFP[lane][0];
-        c.fp_lo = kBatchLaneFP[lane][1];
         if (p.keystages[m.key] == 1)
-            warp_chain<16>(m, c, warp_smem, lane);
+            tdes_cbc_chain_warp<16>(m.in, m.out, m.nblocks, m.iv, warp_smem, lane);
         else
-            warp_chain<48>(m, c, warp_smem, lane);
+            tdes_cbc_chain_warp<48>(m.in, m.out, m.nblocks, m.iv, warp_smem, lane);
         __syncwarp();
         return;
     }

@@ -167,3 +167,45 @@ TDES_HD uint64_t bswap64(uint64_t x) {
     x = ((x & 0x0000FFFF0000FFFFull) << 16) | ((x >> 16) & 0x0000FFFF0000FFFFull);
     return (x << 32) | (x >> 32);
 }
+
+#ifdef __CUDACC__
+// One CBC-encryption chain walked by the calling warp: out_i = E(in_i XOR
+// out_{i-1}), out_{-1} = iv, blocks as big-endian bytes.  keys: the chain's
+// round-key words in shared memory.  The next plaintext block is loaded one
+// block ahead.  A real call from the batch kernel: inlined there, the same loop
+// ran 4% slower (1580 against 1511 ns per block).  The single-message kernel
+// keeps its own inlined copy, which measured 1% faster than this call there.
+__device__ const uint32_t kChainLaneSbox[32][4] = TDES_LANE_SBOX_INIT;
+__device__ const uint32_t kChainLaneIP[32][2] = TDES_LANE_IP_INIT;
+__device__ const uint32_t kChainLaneFP[32][2] = TDES_LANE_FP_INIT;
+
+__device__ __forceinline__ LaneConsts chain_lane_consts(uint32_t lane) {
+    LaneConsts c;
+    c.mlo = kChainLaneSbox[lane][0];
+    c.mhi = kChainLaneSbox[lane][1];
+    c.rot = kChainLaneSbox[lane][2];
+    c.keypos = kChainLaneSbox[lane][3];
+    c.ip_hi = kChainLaneIP[lane][0];
+    c.ip_lo = kChainLaneIP[lane][1];
+    c.fp_hi = kChainLaneFP[lane][0];
+    c.fp_lo = kChainLaneFP[lane][1];
+    return c;
+}
+
+template <int ROUNDS>
+__device__ __noinline__ void tdes_cbc_chain_warp(const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                                                 uint64_t iv, const uint8_t* __restrict__ keys,
+                                                 uint32_t lane) {
+    const LaneConsts c = chain_lane_consts(lane);
+    const uint64_t* p = reinterpret_cast<const uint64_t*>(in);
+    uint64_t* q = reinterpret_cast<uint64_t*>(out);
+    uint64_t prev = iv;
+    uint64_t next = p[0];
+    for (uint64_t i = 0; i < nblocks; ++i) {
+        const uint64_t x = bswap64(next) ^ prev;
+        if (i + 1 < nblocks) next = p[i + 1];
+        prev = tdes_block_warp<ROUNDS>(x, c, keys);
+        if (lane == 0) q[i] = bswap64(prev);
+    }
+}
+#endif
