@@ -90,6 +90,7 @@ TDES_HD uint64_t tdes_block_scalar_nib(uint64_t v, const uint32_t* __restrict__ 
     v = permute64_nib(v, ipn);
     uint32_t L = (uint32_t)(v >> 32), R = (uint32_t)v;
     uint32_t ke = keys[0], ko = keys[1];
+#pragma unroll
     for (int r = 0; r < rounds; r += 2) {
         const uint32_t ke1 = keys[2 * r + 2], ko1 = keys[2 * r + 3];
         L ^= tdes_f_scalar(R, ke, ko, sp);
@@ -137,7 +138,7 @@ __device__ __forceinline__ uint64_t tdes_block_warp(uint64_t v, const LaneConsts
     // its low 5 bits count): R -> {bit test, select} || {rotate, XOR} ->
     // rotate -> ballot.
     const uint32_t b5 = 1u << ((c.rot + 5u) & 31u);
-#pragma unroll 2
+#pragma unroll
     for (int r = 0; r < rounds; ++r) {
         const uint32_t kn = keys[8 * (r + 1 < rounds ? r + 1 : r) + c.keypos];
         const uint32_t m0 = (k & 32u) ? c.mhi : c.mlo;
