@@ -40,6 +40,12 @@ constexpr int kSmallBlocks = 32;                          // S messages: nblocks
 // of their blocks (8 tiles' worth); fewer run one block per lane (S items),
 // which finish sooner alone.
 constexpr uint64_t kMixedMinBlocks = 8 * 1024;
+// Messages of 33..kSplitBlocks blocks (up to 4 KiB) run as pieces of 32
+// blocks in S items too, except in-place CBC decryption (a piece would read
+// the block before it after another warp wrote it): a block's 48 dependent
+// scalar rounds finish far sooner than a bitsliced tile, and a bitsliced tile
+// would spend its full 1024-block work on them anyway.
+constexpr uint64_t kSplitBlocks = 512;
 constexpr uint64_t kSoloChainBlocks = 512;                // longer CBC-enc chains: one per warp
 constexpr int kPerKeyWords = 2 * TDES_TABLE_WORDS;        // enc + dec bitsliced tables
 constexpr int kPerKeyChunks = 2 * TDES_SUBKEY_WORDS;      // enc + dec scalar groups
@@ -272,18 +278,17 @@ __device__ __noinline__ void batch_scalar_item(const BatchParams& p, uint2 item,
                                                uint32_t lane) {
     uint8_t* warp_smem = g_dyn + (size_t)warp * kWarpSmemBytes;
     const SharedTables& st = g_st;
-    // find this lane's (message, block): walk the item's messages in order
+    // find this lane's (message, block): walk the item's pieces in order
     uint32_t msg = 0xFFFFFFFFu;
     uint64_t blk = 0;
     uint32_t acc = 0;
     for (uint32_t i = 0; i < item.y; ++i) {
-        const uint32_t mi = p.s_list[item.x + i];
-        const uint32_t nb = (uint32_t)p.msgs[mi].nblocks;
-        if (lane >= acc && lane < acc + nb) {
-            msg = mi;
-            blk = lane - acc;
+        const SPiece pc = p.s_pieces[item.x + i];
+        if (lane >= acc && lane < acc + pc.n) {
+            msg = pc.msg;
+            blk = pc.first + (lane - acc);
         }
-        acc += nb;
+        acc += pc.n;
     }
     uint64_t x = 0, prev = 0;
     BatchMsg m;
@@ -532,6 +537,7 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
                 PlanHost* h) {
     std::vector<BatchMsg> msgs;
     std::vector<uint32_t> c_list, b_msg, s_list;
+    std::vector<SPiece> split, pieces;
     std::vector<uint64_t> b_prefix(1, 0);
     std::vector<uint2> s_items;
     *h = PlanHost();
@@ -554,6 +560,9 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
             c_list.push_back(mi);
         } else if (nb <= (uint64_t)kSmallBlocks) {
             s_list.push_back(mi);
+        } else if (nb <= kSplitBlocks && !(d.mode == TDES_MODE_CBC_DECRYPT && d.in == d.out)) {
+            for (uint32_t f = 0; f < nb; f += kSmallBlocks)
+                split.push_back({mi, f, (uint32_t)std::min<uint64_t>(kSmallBlocks, nb - f), 0u});
         } else {
             b_msg.push_back(mi);
             b_prefix.push_back(b_prefix.back() + (nb + kTileBlocks - 1) / kTileBlocks);
@@ -598,11 +607,15 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
         h->n_m_tiles = (uint32_t)(m_slices.size() / 32);
         s_list.clear();
     }
-    for (uint32_t i = 0; i < s_list.size();) {  // small messages packed whole, <= 32 blocks
+    // S items: whole small messages (unless in mixed-key tiles) and the
+    // pieces of medium ones, packed in order up to 32 blocks per item
+    for (uint32_t mi : s_list) pieces.push_back({mi, 0u, (uint32_t)msgs[mi].nblocks, 0u});
+    pieces.insert(pieces.end(), split.begin(), split.end());
+    for (uint32_t i = 0; i < pieces.size();) {
         const uint32_t first = i;
         uint32_t blocks = 0;
-        while (i < s_list.size() && blocks + msgs[s_list[i]].nblocks <= (uint64_t)kSmallBlocks)
-            blocks += (uint32_t)msgs[s_list[i++]].nblocks;
+        while (i < pieces.size() && blocks + pieces[i].n <= (uint32_t)kSmallBlocks)
+            blocks += pieces[i++].n;
         s_items.push_back(make_uint2(first, i - first));
     }
     h->n_c = (uint32_t)c_list.size();
@@ -622,7 +635,7 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     h->o_bt = take(h->n_b_tiles * 4);
     h->o_ml = take(m_list.size() * 4);
     h->o_ms = take(m_slices.size() * sizeof(MSlice));
-    h->o_sl = take(s_list.size() * 4);
+    h->o_sl = take(pieces.size() * sizeof(SPiece));
     h->o_si = take(s_items.size() * sizeof(uint2));
     h->o_halo = take(h->needs_halo ? h->n_b_tiles * 8 : 0);
     h->o_ctr = take(8);
@@ -639,7 +652,7 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
         std::fill(bt + b_prefix[i], bt + b_prefix[i + 1], i);
     put(h->o_ml, m_list.data(), m_list.size() * 4);
     put(h->o_ms, m_slices.data(), m_slices.size() * sizeof(MSlice));
-    put(h->o_sl, s_list.data(), s_list.size() * 4);
+    put(h->o_sl, pieces.data(), pieces.size() * sizeof(SPiece));
     put(h->o_si, s_items.data(), s_items.size() * sizeof(uint2));
 }
 
@@ -663,7 +676,7 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
     p.m_list = reinterpret_cast<const uint32_t*>(base + h.o_ml);
     p.m_slices = reinterpret_cast<const MSlice*>(base + h.o_ms);
     p.n_m_tiles = h.n_m_tiles;
-    p.s_list = reinterpret_cast<const uint32_t*>(base + h.o_sl);
+    p.s_pieces = reinterpret_cast<const SPiece*>(base + h.o_sl);
     p.s_items = reinterpret_cast<const uint2*>(base + h.o_si);
     p.n_s_items = h.n_s_items;
     p.halo = h.needs_halo ? reinterpret_cast<uint64_t*>(base + h.o_halo) : nullptr;

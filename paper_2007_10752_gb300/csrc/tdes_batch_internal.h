@@ -31,6 +31,15 @@ struct MSlice {
     uint32_t keydir;  // key << 1 | direction (1: decryption table)
 };
 
+// A run of consecutive blocks of one message, run one block per lane by the
+// scalar round (S items hold up to 32 blocks of such pieces).
+struct SPiece {
+    uint32_t msg;    // index into msgs
+    uint32_t first;  // first block of the piece
+    uint32_t n;      // blocks, 1..32
+    uint32_t pad;
+};
+
 struct BatchMsg {
     const uint8_t* in;
     uint8_t* out;
@@ -57,8 +66,8 @@ struct BatchParams {
     const uint32_t* m_list;    // small messages in mixed-key tiles, in slice order
     const MSlice* m_slices;    // 32 per mixed-key tile
     uint32_t n_m_tiles;
-    const uint32_t* s_list;    // small message indices
-    const uint2* s_items;      // (first, count) into s_list, whole messages, <= 32 blocks
+    const SPiece* s_pieces;    // pieces of small and medium messages
+    const uint2* s_items;      // (first, count) into s_pieces, <= 32 blocks per item
     uint32_t n_s_items;
     uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
     unsigned long long* counter;
