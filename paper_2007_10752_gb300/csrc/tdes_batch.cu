@@ -450,6 +450,17 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
     __syncwarp();
 }
 
+// SOLO_SLOTS: the plan has chains over 512 blocks, each walked by one warp.
+// They are latency-bound, and two on one SM sub-partition (SMSP) slow each
+// other down (a 4096-message batch: 865 against 517 ms), so each is taken
+// only by a warp that holds its SMSP's slot (%smid, %warpid: a placement hint
+// that correctness does not rely on).  A slot holder releases it after its
+// chain and claims again, so every such chain is taken: a warp leaves only
+// when the other items are gone and the chains are gone or its slot is held
+// by another warp, which will come back for them.  Without such chains the
+// kernel claims from one counter only (the slot logic measured 3% slower on
+// the other items even when unused).
+template <bool SOLO_SLOTS>
 __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
     for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) g_st.sp[i] = (&kBatchSP[0][0])[i];
     for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) {
@@ -461,13 +472,47 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
     uint32_t* wtab = reinterpret_cast<uint32_t*>(g_dyn + (size_t)warp * kWarpSmemBytes);
     uint32_t staged = ~0u;  // (key << 1 | dir) of the table in wtab
     const uint64_t total = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
+    uint32_t slot = 0;
+    bool solo_left = SOLO_SLOTS;
+    if (SOLO_SLOTS) {
+        uint32_t smid, wid;
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        asm("mov.u32 %0, %%warpid;" : "=r"(wid));
+        slot = (smid * 4u + (wid & 3u)) % (uint32_t)kChainSlots;
+    }
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(p.counter, 1ull);
-        item = __shfl_sync(0xFFFFFFFFu, item, 0);
-        if (item >= total) break;
+        bool slotted = false;
+        if (!SOLO_SLOTS) {
+            if (lane == 0) item = atomicAdd(p.counter, 1ull);
+            item = __shfl_sync(0xFFFFFFFFu, item, 0);
+            if (item >= total) break;
+        } else {
+            uint32_t gone = 0;
+            item = ~0ull;
+            if (lane == 0) {
+                if (solo_left && atomicCAS(&p.chain_slot[slot], 0u, 1u) == 0u) {
+                    const unsigned long long c = atomicAdd(p.c_counter, 1ull);
+                    if (c < p.n_c_solo) {
+                        item = c;
+                    } else {
+                        atomicExch(&p.chain_slot[slot], 0u);
+                        gone = 1;
+                    }
+                }
+                if (item == ~0ull) {  // packed chains, tiles, small items
+                    const unsigned long long o = atomicAdd(p.counter, 1ull);
+                    if (o < total - p.n_c_solo) item = p.n_c_solo + o;
+                }
+            }
+            item = __shfl_sync(0xFFFFFFFFu, item, 0);
+            if (__shfl_sync(0xFFFFFFFFu, gone, 0)) solo_left = false;
+            if (item == ~0ull) break;
+            slotted = item < p.n_c_solo;
+        }
         if (item < p.n_c_items) {
             batch_cbc_enc_item(p, (uint32_t)item, warp, lane);
+            if (SOLO_SLOTS && slotted && lane == 0) atomicExch(&p.chain_slot[slot], 0u);
             staged = ~0u;
             continue;
         }
@@ -638,7 +683,7 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     h->o_sl = take(pieces.size() * sizeof(SPiece));
     h->o_si = take(s_items.size() * sizeof(uint2));
     h->o_halo = take(h->needs_halo ? h->n_b_tiles * 8 : 0);
-    h->o_ctr = take(8);
+    h->o_ctr = take(16 + 4 * kChainSlots);  // counter, C counter, chain slots: zeroed together
     h->image.assign(align16(off), 0);
     auto put = [&](size_t o, const void* src, size_t n) {
         if (n) memcpy(h->image.data() + o, src, n);
@@ -681,6 +726,8 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
     p.n_s_items = h.n_s_items;
     p.halo = h.needs_halo ? reinterpret_cast<uint64_t*>(base + h.o_halo) : nullptr;
     p.counter = reinterpret_cast<unsigned long long*>(base + h.o_ctr);
+    p.c_counter = p.counter + 1;
+    p.chain_slot = reinterpret_cast<uint32_t*>(p.counter + 2);
     return p;
 }
 
@@ -688,15 +735,19 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
     const size_t dyn = (size_t)warps * kWarpSmemBytes;
     // The limit is a property of the kernel function shared by every plan, so
     // it is always set for the largest shape (8 warps) rather than this one.
-    cudaError_t e = cudaFuncSetAttribute(tdes_batch_kernel,
+    cudaError_t e = cudaFuncSetAttribute(tdes_batch_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8 * kWarpSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tdes_batch_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kWarpSmemBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tdes_batch_mixed_kernel,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kWarpSmemBytes);
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_batch_kernel, 32 * warps, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_batch_kernel<false>, 32 * warps,
+                                                      dyn);
     if (e != cudaSuccess) return e;
     *dyn_smem = dyn;
     *ctas_fit = n < 1 ? 1 : n;
@@ -704,7 +755,7 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
 }
 
 cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool needs_halo, int warps,
-                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s) {
+                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s, bool counter_fresh) {
     if (total_items == 0) return cudaSuccess;
     // Tiles per claim.  A claimed tile takes a warp tens of microseconds at
     // full occupancy, which already hides its message search and key staging
@@ -717,8 +768,11 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
     p.b_chunk = p.n_b_tiles > 256 * warps_total ? 4u : 1u;
     p.n_b_chunks = (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk;
     total_items = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
-    cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!counter_fresh) {
+        e = cudaMemsetAsync(p.counter, 0, 16 + 4 * kChainSlots, s);
+        if (e != cudaSuccess) return e;
+    }
     if (needs_halo && p.n_b_tiles) {
         tdes_batch_halo_kernel<<<(unsigned)((p.n_b_tiles + 255) / 256), 256, 0, s>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -732,7 +786,10 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
     if (total_items == 0) return cudaSuccess;
     const uint64_t want = (total_items + warps - 1) / (uint64_t)warps;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
-    tdes_batch_kernel<<<grid, 32 * warps, dyn_smem, s>>>(p);
+    if (p.n_c_solo)
+        tdes_batch_kernel<true><<<grid, 32 * warps, dyn_smem, s>>>(p);
+    else
+        tdes_batch_kernel<false><<<grid, 32 * warps, dyn_smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ struct tdes_keytable {
 namespace tdes {
 
 constexpr int kPackedWords = 104;  // 3328 table words at one bit each
+constexpr int kChainSlots = 1024;  // SM sub-partitions tracked for C items (4 per SM)
 
 // One slice (bit position) of a mixed-key tile: up to 32 blocks of small
 // messages under one key and direction, one block per lane.
@@ -70,7 +71,9 @@ struct BatchParams {
     const uint2* s_items;      // (first, count) into s_pieces, <= 32 blocks per item
     uint32_t n_s_items;
     uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
-    unsigned long long* counter;
+    unsigned long long* counter;   // claims of B and S items (and C items, see below)
+    unsigned long long* c_counter; // claims of C items by warps on an SMSP without one
+    uint32_t* chain_slot;          // [kChainSlots]: 1 while an SMSP runs a C item
     uint32_t b_chunk;          // B tiles per claimed item (set at launch)
     uint64_t n_b_chunks;       // ceil(n_b_tiles / b_chunk)
 };
@@ -97,8 +100,11 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
 // Sets the batch kernel's shared-memory limit for `warps` warps per CTA and
 // returns how many CTAs of that shape fit on an SM.
 cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit);
-// Counter reset, halo snapshot (if needed) and the persistent kernel on s.
+// Counter reset (unless the caller has just copied the plan image, whose
+// counter is zero), halo snapshot (if needed), the mixed-key kernel (if any)
+// and the persistent kernel on s.
 cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo, int warps,
-                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s);
+                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s,
+                          bool counter_fresh = false);
 
 }  // namespace tdes

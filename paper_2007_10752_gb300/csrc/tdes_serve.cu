@@ -179,10 +179,10 @@ struct tdes_server {
                     e = cudaMemcpyAsync(sl.dmem, sl.pinned, plan.image.size(),
                                         cudaMemcpyHostToDevice, sl.stream);
                 }
-                if (e == cudaSuccess) {
+                if (e == cudaSuccess) {  // the image just copied holds a zeroed claim counter
                     const tdes::BatchParams p = tdes::bind_plan(plan, sl.dmem, kt);
                     e = tdes::enqueue_batch(p, plan.total_items, plan.needs_halo,
-                                            cfg.warps_per_cta, dyn_smem, max_ctas, sl.stream);
+                                            cfg.warps_per_cta, dyn_smem, max_ctas, sl.stream, true);
                 }
                 if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
                 if (e != cudaSuccess) {
