@@ -356,6 +356,7 @@ def run_ours(args):
     nonce = synth.nonce32(SEED)
     dec_ms = time_fn(lambda: tdes.tdes_ecb_decrypt(ks, x, y), 50)
     ctr_ms = time_fn(lambda: tdes.tdes_ctr_crypt(ks, nonce, 0, x, y), 50)
+    cbc_dec_ms = time_fn(lambda: tdes.tdes_cbc_decrypt(ks, synth.iv64(SEED), x, y), 50)
     small_in, small_out = x[: 1 << 20], y[: 1 << 20]
     small_us = graph_call_ms(torch, lambda: tdes.tdes_ecb_encrypt(ks, small_in, small_out)) * 1e3
     small_call_us = time_fn(lambda: tdes.tdes_ecb_encrypt(ks, small_in, small_out), 200) * 1e3
@@ -468,6 +469,7 @@ def run_ours(args):
         "extra": {"kernel_ms_per_launch": round(per_launch_ms, 4),
                   "ecb_decrypt_gbs": round(NBYTES / (dec_ms * 1e-3) / 1e9, 3),
                   "ctr_gbs": round(NBYTES / (ctr_ms * 1e-3) / 1e9, 3),
+                  "cbc_decrypt_gbs": round(NBYTES / (cbc_dec_ms * 1e-3) / 1e9, 3),
                   "ecb_1mib_single_launch_us": round(small_us, 2),
                   "ecb_1mib_python_call_us": round(small_call_us, 2),
                   "cbc_encrypt_chain_ns_per_block": round(chain_ms * 1e6 / n_chain, 1),

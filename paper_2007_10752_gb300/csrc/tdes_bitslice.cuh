@@ -119,7 +119,7 @@ TDES_HD void xor_planes(uint32_t (&H)[32], const uint32_t* __restrict__ k) {
 template <int STAGES = 3>
 TDES_HD void tdes_rounds(uint32_t (&Lh)[32], uint32_t (&Rh)[32], const uint32_t* __restrict__ tab) {
     static_assert(STAGES == 1 || STAGES == 3, "one DES pass or EDE3");
-    if (STAGES == 1) {
+    if constexpr (STAGES == 1) {
         TDES_KEY_PASS(TDES1_PRO, TDES_TABLE_PRO);
     } else {
         TDES_KEY_PASS(TDES_PRO, TDES_TABLE_PRO);
@@ -129,23 +129,23 @@ TDES_HD void tdes_rounds(uint32_t (&Lh)[32], uint32_t (&Rh)[32], const uint32_t*
         tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it));
         tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (2 * it + 1));
     }
-    if (STAGES == 1) {
+    if constexpr (STAGES == 1) {
         TDES_KEY_PASS(TDES1_EPI, TDES1_TABLE_EPI);
-        return;
-    }
-    TDES_KEY_PASS(TDES_REKEY16, TDES_TABLE_REKEY16);
+    } else {
+        TDES_KEY_PASS(TDES_REKEY16, TDES_TABLE_REKEY16);
 #pragma unroll 1
-    for (int it = 0; it < 8; ++it) {  // second pass: the XOR target repeats at its start
-        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (16 + 2 * it));
-        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (17 + 2 * it));
-    }
-    TDES_KEY_PASS(TDES_REKEY32, TDES_TABLE_REKEY32);
+        for (int it = 0; it < 8; ++it) {  // second pass: the XOR target repeats at its start
+            tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (16 + 2 * it));
+            tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (17 + 2 * it));
+        }
+        TDES_KEY_PASS(TDES_REKEY32, TDES_TABLE_REKEY32);
 #pragma unroll 1
-    for (int it = 0; it < 8; ++it) {  // third pass
-        tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (32 + 2 * it));
-        tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (33 + 2 * it));
+        for (int it = 0; it < 8; ++it) {  // third pass
+            tdes_round(Lh, Rh, tab + TDES_TABLE_ROUND0 + 64 * (32 + 2 * it));
+            tdes_round(Rh, Lh, tab + TDES_TABLE_ROUND0 + 64 * (33 + 2 * it));
+        }
+        TDES_KEY_PASS(TDES_EPI, TDES_TABLE_EPI);
     }
-    TDES_KEY_PASS(TDES_EPI, TDES_TABLE_EPI);
 }
 
 // The same with the pass count chosen at run time (the batch kernel, whose

@@ -196,6 +196,10 @@ tdes_ecb_kernel(const uint32_t* __restrict__ table, const uint8_t* in, uint8_t* 
 template <bool VEC, int STAGES>
 __global__ void tdes_ctr_kernel(const uint32_t* __restrict__ table, uint32_t nonce, uint32_t ctr0,
                                 const uint8_t* in, uint8_t* out, uint64_t nblocks);
+template <bool VEC, int STAGES>
+__global__ void tdes_cbc_dec_kernel(const uint32_t* __restrict__ table, uint64_t iv,
+                                    const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                                    const uint64_t* __restrict__ halo);
 
 static std::atomic<bool> dyn_smem_ready[64];
 
@@ -212,6 +216,8 @@ static cudaError_t ensure_dyn_smem() {
         reinterpret_cast<const void*>(tdes_ctr_kernel<false, 3>),
         reinterpret_cast<const void*>(tdes_ctr_kernel<true, 1>),
         reinterpret_cast<const void*>(tdes_ctr_kernel<false, 1>),
+        reinterpret_cast<const void*>(tdes_cbc_dec_kernel<true, 3>),
+        reinterpret_cast<const void*>(tdes_cbc_dec_kernel<true, 1>),
     };
     for (const void* f : fns) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
@@ -379,18 +385,50 @@ __global__ void __launch_bounds__(256, 2)
 tdes_cbc_dec_kernel(const uint32_t* __restrict__ table, uint64_t iv, const uint8_t* in,
                     uint8_t* out, uint64_t nblocks, const uint64_t* __restrict__ halo) {
     __shared__ __align__(16) uint32_t tab[table_words<STAGES>()];
+    extern __shared__ __align__(16) uint4 cbc_data[];  // kCtrWarpBytes per warp (VEC only)
     stage_table<STAGES>(tab, table);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = blockDim.x >> 5;
-    const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
+    uint4* wbuf = cbc_data + (threadIdx.x >> 5) * (kCtrWarpBytes / 16);
+    // tile indices fit 32 bits: the host caps a call below 2^31 tiles (16 TiB)
+    const uint32_t ntiles = (uint32_t)((nblocks + kTileBlocks - 1) / kTileBlocks);
+    const uint32_t nfull = (uint32_t)(nblocks / kTileBlocks);  // tiles [0, nfull) are full
+    const uint32_t stride = gridDim.x * warps;
     const uint2 ivw = make_uint2(bswap32((uint32_t)(iv >> 32)), bswap32((uint32_t)iv));
     const uint2* c = reinterpret_cast<const uint2*>(in);
-    for (uint64_t t = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles;
-         t += (uint64_t)gridDim.x * warps) {
-        const uint64_t b0 = t * kTileBlocks;
+    uint32_t t = blockIdx.x * warps + (threadIdx.x >> 5);
+    if (VEC && t < nfull) {  // full tiles are prefetched one ahead, as in ECB
+        const uint4* p = reinterpret_cast<const uint4*>(in) + (uint64_t)t * (kTileBlocks / 2) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) cp_async16(wbuf + 32 * j + lane, p + 32 * j);
+        cp_async_commit();
+    }
+    for (; t < ntiles; t += stride) {
+        const uint64_t b0 = (uint64_t)t * kTileBlocks;
         uint32_t A0[32], A1[32];
-        load_tile<VEC>(in, b0, nblocks, lane, A0, A1);
+        const bool full = VEC && t < nfull;
+        if (full) {
+            cp_async_wait_all();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint4 v = wbuf[32 * j + lane];
+                A0[2 * j] = v.x;
+                A1[2 * j] = v.y;
+                A0[2 * j + 1] = v.z;
+                A1[2 * j + 1] = v.w;
+            }
+            const uint32_t tn = t + stride;
+            if (tn < nfull) {
+                const uint4* p =
+                    reinterpret_cast<const uint4*>(in) + (uint64_t)tn * (kTileBlocks / 2) + lane;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) cp_async16(wbuf + 32 * j + lane, p + 32 * j);
+                cp_async_commit();
+            }
+        } else {
+            load_tile<VEC>(in, b0, nblocks, lane, A0, A1);
+        }
         tdes_process32<STAGES>(A0, A1, tab);
         const uint2* ct = c + b0;  // this tile's ciphertext, 32-bit indices below
         const uint32_t nvalid = (uint32_t)min((uint64_t)kTileBlocks, nblocks - b0);
@@ -426,9 +464,10 @@ static void cbc_dec_launch(const uint32_t* tab_dec, uint64_t iv, const void* in,
                            uint64_t nblocks, const uint64_t* halo, bool vec16, Geometry g,
                            cudaStream_t s) {
     if (vec16)
-        tdes_cbc_dec_kernel<true, STAGES><<<g.grid, g.threads, 0, s>>>(
-            tab_dec, iv, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks,
-            halo);
+        tdes_cbc_dec_kernel<true, STAGES>
+            <<<g.grid, g.threads, (size_t)(g.threads / 32) * kCtrWarpBytes, s>>>(
+                tab_dec, iv, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out),
+                nblocks, halo);
     else
         tdes_cbc_dec_kernel<false, STAGES><<<g.grid, g.threads, 0, s>>>(
             tab_dec, iv, static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), nblocks,
@@ -438,6 +477,8 @@ static void cbc_dec_launch(const uint32_t* tab_dec, uint64_t iv, const void* in,
 cudaError_t launch_cbc_dec(const uint32_t* tab_dec, int stages, uint64_t iv, const void* in,
                            void* out, uint64_t nblocks, const uint64_t* halo, bool vec16,
                            Geometry g, cudaStream_t s) {
+    cudaError_t e = ensure_dyn_smem();
+    if (e != cudaSuccess) return e;
     if (stages == 1)
         cbc_dec_launch<1>(tab_dec, iv, in, out, nblocks, halo, vec16, g, s);
     else
@@ -517,8 +558,10 @@ int wide_ctas_per_sm(int kernel_id) {
                     &n, tdes_ctr_kernel<true, 3>, threads, kWideWarps * kCtrWarpBytes);
             break;
         default:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_cbc_dec_kernel<true, 3>,
-                                                              threads, 0);
+            e = ensure_dyn_smem();
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &n, tdes_cbc_dec_kernel<true, 3>, threads, kWideWarps * kCtrWarpBytes);
             break;
     }
     if (e != cudaSuccess || n < 1) return 1;
