@@ -375,6 +375,8 @@ def run_ours(args):
 
     # ---- large streaming: 32 GiB in place, CTR stream + 2^20 small messages
     streaming = None if args.no_stream else run_streaming(torch, tdes, synth, stream)
+    if streaming is not None:
+        streaming["uniform_reading"] = run_streaming_uniform(torch, tdes, synth)
 
     # ---- serving: Poisson arrivals at fractions of the measured peak
     serving = None if args.no_serve else run_serving(torch, tdes, synth, x)
@@ -661,6 +663,56 @@ def run_streaming(torch, tdes, synth, stream, reps=5):
             "ctr_stream_alone_gbps": round(STREAM_BYTES / (ctr_ms * 1e-3) / 1e9, 3),
             "tiles": info["n_tiles"], "small_items": info["n_small_items"],
             "cbc_encrypt_messages": info["n_cbc_enc_messages"]}
+
+
+UNIFORM_WORKLOAD = ("the same 32 GiB buffer in place: [0, 16 GiB) the single-key CTR stream, "
+                    "[16 GiB, 32 GiB) read as 2^28 messages of 64 B under 65536 seeded key "
+                    "triples (same mode mix; per-message key, mode and IV arrays drawn on the "
+                    "device); tdes_uniform_crypt (plan and run on the device) and the CTR call "
+                    "on two streams of one CUDA graph")
+
+
+def run_streaming_uniform(torch, tdes, synth, reps=3):
+    """Config 5, reading every byte of the second 16 GiB as a 64-byte message."""
+    from paper_2007_10752_gb300 import workloads as W
+    seed, n, n_keys = W.STREAM_SEED, W.STREAM_N_UNIFORM, W.STREAM_N_KEYS
+    buf = torch.empty(W.STREAM_TOTAL, dtype=torch.uint8, device="cuda")
+    synth.fill_device(buf, seed)
+    keys = synth.key_triples(seed, n_keys + 1)  # the last triple keys the CTR stream
+    kt = tdes.KeyTable(keys)
+    k, md, v = W.uniform_arrays_device(torch, seed, n, n_keys)
+    x_ctr, x_msg = buf[:W.STREAM_BYTES], buf[W.STREAM_BYTES:]
+    scratch = torch.empty(tdes.tdes_uniform_scratch_bytes(kt, n, 64), dtype=torch.uint8,
+                          device="cuda")
+    skipped = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ks = tdes.KeySchedule.from_triple(keys[-1].tobytes())
+    nonce = synth.nonce32(seed)
+    torch.cuda.synchronize()
+
+    def uniform():
+        tdes.tdes_uniform_crypt(kt, k, md, v, x_msg, x_msg, 64, scratch=scratch, skipped=skipped)
+
+    side = torch.cuda.Stream()
+
+    def both():
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            tdes.tdes_ctr_crypt(ks, nonce, 0, x_ctr, x_ctr)
+        uniform()
+        torch.cuda.current_stream().wait_stream(side)
+
+    uni_ms = graph_call_ms(torch, uniform, calls=1, reps=reps)
+    both_ms = graph_call_ms(torch, both, calls=1, reps=reps)
+    info = tdes.tdes_uniform_info(scratch)
+    out = {"workload": UNIFORM_WORKLOAD, "messages": n,
+           "messages_ms": round(uni_ms, 3),
+           "messages_gbps": round(n * 64 / (uni_ms * 1e-3) / 1e9, 3),
+           "processed_bytes": W.STREAM_TOTAL, "ms": round(both_ms, 3),
+           "gbps": round(W.STREAM_TOTAL / (both_ms * 1e-3) / 1e9, 3),
+           "skipped": int(skipped.item()), "plan": info}
+    del buf, x_ctr, x_msg, k, md, v, scratch
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- serving

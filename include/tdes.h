@@ -235,6 +235,59 @@ int tdes_batch_info(const tdes_batch_t *b, tdes_batch_info_t *info);
 void tdes_batch_free(tdes_batch_t *b);
 
 /* ------------------------------------------------------------------------
+ * Uniform messages: n_msgs messages of msg_bytes each, back to back (message
+ * i is bytes [i * msg_bytes, (i + 1) * msg_bytes) of in and of out), each
+ * under its own key triple and mode, planned and run on the device.  Not in
+ * the paper (one file under one triple in ECB, Sec. V); every message gets
+ * the same EDE3 (Sec. III-B) in the mode of TDES_MODE_*, as in a batch.
+ * Meant for very many small messages, where host-side descriptors
+ * (tdes_batch_plan) would not fit: messages are sorted by (key, mode class)
+ * on the device, full groups run in single-key bitsliced tiles, the rest in
+ * tiles that mix 32 keys, and CBC encryption runs 1024 (or 32 x 32) chains
+ * per tile, one bitsliced pass per block position.
+ * ------------------------------------------------------------------------ */
+
+#define TDES_UNIFORM_MAX_MSGS (1ull << 31)
+
+/* Device scratch the call needs for n_msgs messages of msg_bytes under the
+ * key table kt (about 4 bytes per message plus 20 bytes per key).
+ * TDES_EINVAL for a msg_bytes that is not a multiple of 8 in [8, 256] or
+ * n_msgs > TDES_UNIFORM_MAX_MSGS. */
+int tdes_uniform_scratch_bytes(const tdes_keytable_t *kt, uint64_t n_msgs, uint64_t msg_bytes,
+                               size_t *bytes);
+
+/* Encrypts or decrypts every message, asynchronously on `stream`; no host
+ * synchronisation and no allocation, so the call can be captured in a CUDA
+ * graph.  Device arrays of n_msgs entries: key_index (index into kt, 4-byte
+ * aligned), mode (TDES_MODE_*, one byte each), iv_or_ctr (8-byte aligned;
+ * CBC IV, or for CTR nonce << 32 | ctr0 as in tdes_desc_t).  in / out:
+ * device pointers, 8-byte aligned, equal (in place) or disjoint.  scratch:
+ * device memory of at least tdes_uniform_scratch_bytes(), 256-byte aligned,
+ * owned by the caller and not shared with a concurrent call; its contents
+ * need no initialisation.  Messages with a key index >= the table's count,
+ * a mode > TDES_MODE_CBC_ENCRYPT or a CTR counter that would pass 2^32 are
+ * skipped (their output bytes are not written); their number is written to
+ * *skipped (device memory, 8-byte aligned, nullable) by the end of the
+ * call's work.  Returns TDES_EINVAL for bad arguments before any work is
+ * queued. */
+int tdes_uniform_crypt(const tdes_keytable_t *kt, const uint32_t *key_index, const uint8_t *mode,
+                       const uint64_t *iv_or_ctr, const void *in, void *out, uint64_t msg_bytes,
+                       uint64_t n_msgs, void *scratch, size_t scratch_bytes,
+                       uint64_t *skipped, tdes_stream_t stream);
+
+typedef struct {
+    uint64_t skipped;          /* messages skipped (see tdes_uniform_crypt) */
+    uint32_t key_tiles;        /* single-key tiles of ECB / CTR / CBC-decrypt messages */
+    uint32_t mixed_slices;     /* mixed-key slices of such messages (32 per tile) */
+    uint32_t chain_key_tiles;  /* single-key tiles of 1024 CBC-encryption chains */
+    uint32_t chain_slices;     /* mixed-key slices of up to 32 CBC-encryption chains */
+} tdes_uniform_info_t;
+
+/* The plan of the last call that used `scratch`, read back synchronously
+ * (waits for the device). */
+int tdes_uniform_info(const void *scratch, tdes_uniform_info_t *info);
+
+/* ------------------------------------------------------------------------
  * Serving: continuous batching of individual requests.  Not in the paper.
  * ------------------------------------------------------------------------ */
 

@@ -30,7 +30,8 @@ EXPORTED = (
     "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_cbc_decrypt_noalloc",
     "tdes_ecb_crypt_host", "tdes_keytable_create", "tdes_keytable_free", "tdes_batch_plan",
     "tdes_batch_configure", "tdes_batch_launch", "tdes_batch_launch_graph", "tdes_batch_info",
-    "tdes_batch_free", "tdes_server_config_default", "tdes_server_create", "tdes_server_submit",
+    "tdes_batch_free", "tdes_uniform_scratch_bytes", "tdes_uniform_crypt", "tdes_uniform_info",
+    "tdes_server_config_default", "tdes_server_create", "tdes_server_submit",
     "tdes_server_poll", "tdes_server_wait", "tdes_server_destroy", "tdes_serve_loadtest",
     "tdes_sbox_gate_count", "tdes_set_small_cutoff", "tdes_strerror", "tdes_last_error",
 )
@@ -82,6 +83,13 @@ class BatchInfo(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int), ("bytes_per_mode", ctypes.c_uint64 * 5),
                 ("n_mixed_tiles", ctypes.c_uint64)]
 
+class UniformInfo(ctypes.Structure):
+    """tdes_uniform_info_t"""
+    _fields_ = [("skipped", ctypes.c_uint64), ("key_tiles", ctypes.c_uint32),
+                ("mixed_slices", ctypes.c_uint32), ("chain_key_tiles", ctypes.c_uint32),
+                ("chain_slices", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -125,6 +133,9 @@ def load(path: str = LIB_PATH):
     lib.tdes_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     lib.tdes_batch_free.argtypes = [vp]
     lib.tdes_batch_free.restype = None
+    lib.tdes_uniform_scratch_bytes.argtypes = [vp, u64, u64, ctypes.POINTER(sz)]
+    lib.tdes_uniform_crypt.argtypes = [vp, vp, vp, vp, vp, vp, u64, u64, vp, sz, vp, vp]
+    lib.tdes_uniform_info.argtypes = [vp, ctypes.POINTER(UniformInfo)]
     lib.tdes_server_config_default.argtypes = [ctypes.POINTER(ServerConfig)]
     lib.tdes_server_config_default.restype = None
     lib.tdes_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
@@ -399,6 +410,46 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+def tdes_uniform_scratch_bytes(kt: KeyTable, n_msgs: int, msg_bytes: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load().tdes_uniform_scratch_bytes(kt.handle, n_msgs, msg_bytes, ctypes.byref(n)))
+    return n.value
+
+
+def tdes_uniform_crypt(kt: KeyTable, key_index, mode, iv_or_ctr, inp, out, msg_bytes: int,
+                       scratch=None, skipped=None, stream=None, n_msgs=None):
+    """Messages of msg_bytes back to back in ``inp`` (device tensors; in place
+    when ``out is inp``); key_index (int32/uint32), mode (uint8) and iv_or_ctr
+    (int64/uint64) are device tensors of one entry per message.  ``scratch``
+    (a uint8 CUDA tensor of tdes_uniform_scratch_bytes) is allocated when
+    None; ``skipped`` (an int64 CUDA tensor of one element) receives the
+    number of skipped messages.  Returns the scratch tensor (it holds the plan
+    that tdes_uniform_info reads)."""
+    if n_msgs is None:
+        n_msgs = key_index.numel()
+    if mode.numel() < n_msgs or iv_or_ctr.numel() < n_msgs:
+        raise ValueError("mode and iv_or_ctr need one entry per message")
+    if _nbytes(inp) < n_msgs * msg_bytes or _nbytes(out) < n_msgs * msg_bytes:
+        raise ValueError("buffers shorter than n_msgs * msg_bytes")
+    need = tdes_uniform_scratch_bytes(kt, n_msgs, msg_bytes)
+    if scratch is None:
+        import torch
+        scratch = torch.empty(need + 256, dtype=torch.uint8, device=inp.device)
+        off = (-scratch.data_ptr()) % 256
+        scratch = scratch[off:off + need]
+    _check(load().tdes_uniform_crypt(kt.handle, _ptr(key_index), _ptr(mode), _ptr(iv_or_ctr),
+                                     _ptr(inp), _ptr(out), msg_bytes, n_msgs, _ptr(scratch),
+                                     _nbytes(scratch), _ptr(skipped), _stream(stream)))
+    return scratch
+
+
+def tdes_uniform_info(scratch) -> dict:
+    ui = UniformInfo()
+    _check(load().tdes_uniform_info(_ptr(scratch), ctypes.byref(ui)))
+    return {"skipped": ui.skipped, "key_tiles": ui.key_tiles, "mixed_slices": ui.mixed_slices,
+            "chain_key_tiles": ui.chain_key_tiles, "chain_slices": ui.chain_slices}
 
 
 class Server:

@@ -8,6 +8,10 @@ buffers plus batch descriptors (no cipher arithmetic here).
   single-key CTR stream at offset 0, then 2^20 messages of 64 bytes under
   65536 key triples with the same mode mix.  The payload is drawn on the
   device with the same SplitMix64 words as ``synth.random_bytes``.
+* ``uniform_arrays_device``: per-message key index, mode and IV arrays for
+  the second 16 GiB of that buffer read as 2^28 messages of 64 bytes, drawn
+  on the device with the same words as the host draws above (message i gets
+  word i of each stream, so the first 2^20 match ``build_streaming``).
 """
 from __future__ import annotations
 
@@ -21,6 +25,7 @@ STREAM_TOTAL = 32 << 30
 STREAM_BYTES = 16 << 30
 STREAM_N_SMALL = 1 << 20
 STREAM_N_KEYS = 65536
+STREAM_N_UNIFORM = 1 << 28  # the second 16 GiB as 64-byte messages
 MODE_MIX = (0.4, 0.3, 0.2, 0.1)  # ECB encrypt, CTR, CBC-decrypt, CBC-encrypt
 
 
@@ -71,3 +76,57 @@ def build_streaming(torch, tdes, seed=STREAM_SEED, total=STREAM_TOTAL, stream_by
     d["out_ptr"][1:] = np.uint64(base) + offs
     d["nbytes"][1:] = 64
     return buf, kt, d, keys, nonce
+
+
+def uniform_arrays_device(torch, seed, n, n_keys, first=0):
+    """(key_index int32, mode uint8, iv_or_ctr int64) CUDA tensors for messages
+    first .. first + n - 1: key pick = word % n_keys (n_keys a power of two,
+    so the low bits of the word), mode from MODE_MIX by the inverse CDF of the
+    word's top 53 bits (as ``synth.categorical``), IV = the word of the IV
+    stream (CTR keeps its nonce half, counter 0)."""
+    if n_keys & (n_keys - 1):
+        raise ValueError("device key picks need a power-of-two key count")
+
+    def words(stream):
+        w = torch.empty(n, dtype=torch.int64, device="cuda")
+        synth.fill_device(w.view(torch.uint8), seed, stream, 8 * first)
+        return w
+
+    key_index = uniform_key_index(torch, words(synth.STREAM_KEYPICK), n_keys)
+    mode = uniform_mode(torch, words(synth.STREAM_MODE))
+    return key_index, mode, uniform_iv(torch, words(synth.STREAM_IV), mode)
+
+
+def uniform_key_index(torch, w, n_keys):
+    return (w & (n_keys - 1)).to(torch.int32)
+
+
+def uniform_mode(torch, w):
+    u = ((w >> 11) & ((1 << 53) - 1)).to(torch.float64) * (1.0 / (1 << 53))
+    p = np.asarray(MODE_MIX, dtype=np.float64)
+    idx = torch.zeros(w.shape[0], dtype=torch.int64, device=w.device)
+    for c in np.cumsum(p / p.sum()):
+        idx += (u >= float(c)).to(torch.int64)
+    del u
+    idx.clamp_(max=len(p) - 1)
+    return torch.tensor([0, 2, 3, 4], dtype=torch.uint8, device=w.device)[idx]
+
+
+def uniform_iv(torch, w, mode):
+    return torch.where(mode == 2, w & -(1 << 32), w)
+
+
+def uniform_expected_fields(seed, i, n_keys):
+    """Host copy of message i's (key index, mode, iv_or_ctr) as drawn by
+    uniform_arrays_device."""
+    key = int(synth.u64s(seed, 1, synth.STREAM_KEYPICK, first=i)[0] % np.uint64(n_keys))
+    mode = int(_modes_at(seed, i))
+    iv = int(synth.u64s(seed, 1, synth.STREAM_IV, first=i)[0])
+    if mode == 2:
+        iv &= 0xFFFFFFFF00000000
+    return key, mode, iv
+
+
+def _modes_at(seed, i):
+    return np.array([0, 2, 3, 4], dtype=np.uint32)[
+        synth.categorical(seed, 1, list(MODE_MIX), synth.STREAM_MODE, first=i)][0]
