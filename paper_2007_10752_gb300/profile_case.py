@@ -9,6 +9,9 @@ captures, whose commands are recorded beside their summaries in profiles/.
   python -m paper_2007_10752_gb300.profile_case --kernel batch --launches 3
   python -m paper_2007_10752_gb300.profile_case --kernel batch_ctr --mib 256   (one CTR message as a batch)
   python -m paper_2007_10752_gb300.profile_case --kernel ecb --des   (single-DES schedule)
+  python -m paper_2007_10752_gb300.profile_case --kernel uniform --msgs 268435456 --keys 65536
+      (tdes_uniform_crypt: 64-byte messages in place, the second half of the
+       large streaming workload; every kernel of the call, --launches calls)
 """
 from __future__ import annotations
 
@@ -24,12 +27,14 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", choices=["ecb", "ecb_dec", "ctr", "cbc_dec", "cbc_enc", "batch",
-                                         "batch_ctr", "batch_cbc_enc"],
+                                         "batch_ctr", "batch_cbc_enc", "uniform"],
                     default="ecb")
     ap.add_argument("--mib", type=int, default=256)
     ap.add_argument("--kib", type=int, default=0, help="size in KiB (overrides --mib)")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--des", action="store_true", help="a single-DES schedule (one pass)")
+    ap.add_argument("--msgs", type=int, default=1 << 24, help="uniform: 64-byte messages")
+    ap.add_argument("--keys", type=int, default=4096, help="uniform: key triples (a power of two)")
     args = ap.parse_args()
 
     import torch
@@ -48,6 +53,21 @@ def main():
             b.launch()
         torch.cuda.synchronize()
         print(f"batch: {args.launches} launches of {int(np.sum(d['mode'] != 4))} messages done")
+        return
+    if args.kernel == "uniform":
+        from paper_2007_10752_gb300 import workloads as W
+        seed, n_msg = W.STREAM_SEED, args.msgs
+        buf = torch.empty(n_msg * 64, dtype=torch.uint8, device="cuda")
+        synth.fill_device(buf, seed, start_byte=W.STREAM_BYTES)
+        kt = tdes.KeyTable(synth.key_triples(seed, args.keys))
+        k, md, v = W.uniform_arrays_device(torch, seed, n_msg, args.keys)
+        scratch = torch.empty(tdes.tdes_uniform_scratch_bytes(kt, n_msg, 64), dtype=torch.uint8,
+                              device="cuda")
+        for _ in range(args.launches):
+            tdes.tdes_uniform_crypt(kt, k, md, v, buf, buf, 64, scratch=scratch)
+        torch.cuda.synchronize()
+        print(f"uniform: {args.launches} calls on {n_msg} messages done:",
+              tdes.tdes_uniform_info(scratch))
         return
     n = (args.kib << 10) if args.kib else (args.mib << 20)
     keys = synth.key_triple(2)
