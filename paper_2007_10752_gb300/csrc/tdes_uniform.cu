@@ -111,19 +111,27 @@ __device__ __forceinline__ uint32_t dir_of_mode(uint32_t md) {
     return (md == TDES_MODE_ECB_DECRYPT || md == TDES_MODE_CBC_DECRYPT) ? 1u : 0u;
 }
 
+// Lanes of a warp whose messages fall in the same group share one atomic
+// (the leader adds the group's lane count), so that a workload with few keys
+// does not serialise on a handful of counters; with many keys most groups
+// hold one lane.
 __global__ void uni_count_kernel(UniParams p) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31u;
     uint32_t bad = 0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n_msgs; i += stride) {
         const uint32_t g = uni_group(p, i);
-        if (g == ~0u)
-            ++bad;
-        else
-            atomicAdd(&p.counts[g], 1u);
+        const uint32_t peers = __match_any_sync(__activemask(), g);
+        if (lane == (uint32_t)(__ffs(peers) - 1)) {
+            if (g == ~0u)
+                bad += __popc(peers);
+            else
+                atomicAdd(&p.counts[g], (uint32_t)__popc(peers));
+        }
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) bad += __shfl_xor_sync(0xFFFFFFFFu, bad, o);
-    if ((threadIdx.x & 31u) == 0 && bad) atomicAdd(&p.hdr->skipped, (unsigned long long)bad);
+    if (lane == 0 && bad) atomicAdd(&p.hdr->skipped, (unsigned long long)bad);
 }
 
 struct Sums {
@@ -264,11 +272,19 @@ __global__ void uni_map_kernel(UniParams p) {
     }
 }
 
+// Lanes in the same group take consecutive positions from one atomic.
 __global__ void uni_scatter_kernel(UniParams p) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31u;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n_msgs; i += stride) {
         const uint32_t g = uni_group(p, i);
-        if (g != ~0u) p.order[atomicAdd(&p.cursor[g], 1u)] = (uint32_t)i;
+        const uint32_t act = __activemask();
+        const uint32_t peers = __match_any_sync(act, g);
+        const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+        uint32_t base = 0;
+        if (lane == leader && g != ~0u) base = atomicAdd(&p.cursor[g], (uint32_t)__popc(peers));
+        base = __shfl_sync(act, base, leader);
+        if (g != ~0u) p.order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
     }
 }
 

@@ -127,6 +127,29 @@ def test_uniform_cbc_encrypt_key_tiles(cuda_lib, msg_bytes):
         assert info["key_tiles"] == 0 and info["mixed_slices"] == 0
 
 
+def test_uniform_one_key_skewed(cuda_lib):
+    """Every message under one key: a handful of large groups (the planner's
+    per-group atomics are shared per warp), CBC-encryption key tiles of 1024
+    chains, and ECB messages checked as one concatenated ECB call."""
+    n, mb, seed = 100_000, 64, 9600
+    keys, key_index, mode, iv, data = make_case(seed, n, mb, 1)
+    kt = cuda_lib.KeyTable(keys)
+    got, skipped, info = run(cuda_lib, kt, key_index, mode, iv, data, mb, True)
+    assert skipped == 0
+    assert {k: info[k] for k in expected_plan(key_index, mode, 1, mb // 8)} == \
+        expected_plan(key_index, mode, 1, mb // 8)
+    assert info["chain_key_tiles"] > 0
+    k = keys[0].tobytes()
+    g = got.reshape(n, mb)
+    d = data.reshape(n, mb)
+    for md in (0, 1):
+        sel = np.nonzero(mode == md)[0]
+        want = oracle.tdes_ecb(k, d[sel].reshape(-1), decrypt=(md == 1)).reshape(-1, mb)
+        assert (g[sel] == want).all(), f"mode {md}"
+    for i in np.nonzero(mode >= 2)[0]:
+        assert (g[i] == oracle_msg(int(mode[i]), k, int(iv[i]), d[i])).all(), i
+
+
 def test_uniform_single_message_and_empty(cuda_lib):
     keys = synth.key_triples(9200, 4)
     kt = cuda_lib.KeyTable(keys)
