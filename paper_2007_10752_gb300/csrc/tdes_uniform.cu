@@ -8,7 +8,7 @@
 // plan is a counting sort on the device, with no host round trip, so a call
 // can be captured in a CUDA graph:
 //   1. count the messages of each group (mode, key);
-//   2. one CTA scans the counts.  Each group gets full single-key tiles
+//   2. scan the counts.  Each group gets full single-key tiles
 //      (1024 blocks of whole messages; for CBC encryption, 1024 chains) and,
 //      for what is left, mixed-key slices (one slice = one bit position of
 //      a tile: up to 32 blocks under one key, one block per lane);
@@ -183,56 +183,96 @@ __device__ Sums block_scan(Sums v, Sums* total) {
     return ex;
 }
 
-// Offsets of groups [g0, g1) (modes 0-3, or CBC encryption), starting from
-// `base`; *total gets the range's sums.
-__device__ void scan_groups(const UniParams& p, uint32_t g0, uint32_t g1, Sums base, Sums* total) {
-    const uint32_t n = g1 - g0;
-    const uint32_t per = (n + kScanThreads - 1) / kScanThreads;
-    const uint32_t a = g0 + min(n, threadIdx.x * per), b = g0 + min(n, (threadIdx.x + 1) * per);
-    Sums v = {0u, 0u, 0u};
-    for (uint32_t g = a; g < b; ++g) {
-        const uint32_t md = g / p.n_keys, c = p.counts[g];
-        const uint32_t M = per_tile_of(p, md), Q = per_slice_of(p, md);
-        const uint32_t u = c / M, r = c - u * M;
-        v.c += c;
-        v.t += u;
-        v.s += (r + Q - 1) / Q;
+// The scan over groups runs in blocks of kScanSpan groups: the first
+// scan_blocks_a() blocks cover modes 0-3, the rest CBC encryption (whose
+// slices start a tile of their own, so the two ranges are scanned apart).
+// Three kernels: block sums, a scan of the block sums (one CTA), and each
+// block's offsets from its base.
+constexpr uint32_t kScanPer = 4;                           // groups per thread
+constexpr uint32_t kScanSpan = kScanThreads * kScanPer;   // groups per block
+
+__host__ __device__ inline uint32_t scan_blocks_a(uint32_t K) {
+    return (TDES_MODE_CBC_ENCRYPT * K + kScanSpan - 1) / kScanSpan;
+}
+__host__ __device__ inline uint32_t scan_blocks(uint32_t K) {
+    return scan_blocks_a(K) + (K + kScanSpan - 1) / kScanSpan;
+}
+
+// This thread's groups [*a, *b) of scan block blk.
+__device__ __forceinline__ void scan_range(const UniParams& p, uint32_t blk, uint32_t* a,
+                                           uint32_t* b) {
+    const uint32_t K = p.n_keys, G4 = TDES_MODE_CBC_ENCRYPT * K, na = scan_blocks_a(K);
+    const uint32_t g0 = blk < na ? blk * kScanSpan : G4 + (blk - na) * kScanSpan;
+    const uint32_t g1 = min(blk < na ? G4 : G4 + K, g0 + kScanSpan);
+    *a = min(g1, g0 + threadIdx.x * kScanPer);
+    *b = min(g1, *a + kScanPer);
+}
+
+// A group's messages, single-key tiles and mixed-key slices.
+__device__ __forceinline__ Sums group_sums(const UniParams& p, uint32_t g) {
+    const uint32_t md = g / p.n_keys, c = p.counts[g];
+    const uint32_t M = per_tile_of(p, md), Q = per_slice_of(p, md);
+    const uint32_t u = c / M, r = c - u * M;
+    return {c, u, (r + Q - 1) / Q};
+}
+
+__device__ __forceinline__ Sums add(Sums x, Sums y) { return {x.c + y.c, x.t + y.t, x.s + y.s}; }
+
+__global__ void __launch_bounds__(kScanThreads) uni_scan_partial_kernel(UniParams p, Sums* part) {
+    uint32_t a, b;
+    scan_range(p, blockIdx.x, &a, &b);
+    Sums v = {0u, 0u, 0u}, tot;
+    for (uint32_t g = a; g < b; ++g) v = add(v, group_sums(p, g));
+    block_scan(v, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// Exclusive scan of part[b0, b1) into base[], from `carry`; returns the end.
+__device__ Sums scan_parts(const Sums* part, Sums* base, uint32_t b0, uint32_t b1, Sums carry) {
+    for (uint32_t c0 = b0; c0 < b1; c0 += kScanThreads) {
+        const uint32_t b = c0 + threadIdx.x;
+        const Sums v = b < b1 ? part[b] : Sums{0u, 0u, 0u};
+        Sums tot;
+        const Sums ex = block_scan(v, &tot);
+        if (b < b1) base[b] = add(carry, ex);
+        carry = add(carry, tot);
     }
-    const Sums ex = block_scan(v, total);
-    Sums run = {base.c + ex.c, base.t + ex.t, base.s + ex.s};
+    return carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) uni_scan_top_kernel(UniParams p, const Sums* part,
+                                                                    Sums* base) {
+    const uint32_t na = scan_blocks_a(p.n_keys), nb = scan_blocks(p.n_keys);
+    const Sums t01 = scan_parts(part, base, 0u, na, {0u, 0u, 0u});
+    const uint32_t s2 = (t01.s + 31u) & ~31u;  // CBC-encryption slices start a tile of their own
+    const Sums end = scan_parts(part, base, na, nb, {t01.c, t01.t, s2});
+    if (threadIdx.x == 0) {
+        p.hdr->kind_tiles[kKindEcb] = 0u;
+        p.hdr->kind_tiles[kKindCbcEnc] = t01.t;
+        p.hdr->kind_tiles[kKindCbcEnc + 1] = end.t;
+        p.hdr->tiles[0] = t01.t;
+        p.hdr->tiles[1] = end.t - t01.t;
+        p.hdr->slices[0] = t01.s;
+        p.hdr->slices[1] = end.s - s2;
+        p.hdr->slice2_base = s2;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) uni_scan_final_kernel(UniParams p, const Sums* base) {
+    uint32_t a, b;
+    scan_range(p, blockIdx.x, &a, &b);
+    Sums v = {0u, 0u, 0u}, tot;
+    for (uint32_t g = a; g < b; ++g) v = add(v, group_sums(p, g));
+    Sums run = add(base[blockIdx.x], block_scan(v, &tot));
+    const uint32_t g_ctr = TDES_MODE_CTR * p.n_keys, g_cbc = TDES_MODE_CBC_DECRYPT * p.n_keys;
     for (uint32_t g = a; g < b; ++g) {
-        const uint32_t md = g / p.n_keys, c = p.counts[g];
-        const uint32_t M = per_tile_of(p, md), Q = per_slice_of(p, md);
-        const uint32_t u = c / M, r = c - u * M;
         p.msg_off[g] = run.c;
         p.cursor[g] = run.c;  // the scatter's next position in the group
         p.tile_off[g] = run.t;
         p.slice_off[g] = run.s;
-        run.c += c;
-        run.t += u;
-        run.s += (r + Q - 1) / Q;
-    }
-}
-
-__global__ void __launch_bounds__(kScanThreads) uni_scan_kernel(UniParams p) {
-    const uint32_t K = p.n_keys;
-    const uint32_t G4 = TDES_MODE_CBC_ENCRYPT * K;  // groups of modes 0-3
-    Sums t01, t2;
-    scan_groups(p, 0u, G4, {0u, 0u, 0u}, &t01);
-    const uint32_t s2 = (t01.s + 31u) & ~31u;  // CBC-encryption slices start a tile of their own
-    scan_groups(p, G4, G4 + K, {t01.c, t01.t, s2}, &t2);
-    __syncthreads();  // tile_off[] of other threads' groups is read below
-    if (threadIdx.x == 0) {
-        p.hdr->kind_tiles[kKindEcb] = 0u;
-        p.hdr->kind_tiles[kKindCtr] = p.tile_off[TDES_MODE_CTR * K];
-        p.hdr->kind_tiles[kKindCbcDec] = p.tile_off[TDES_MODE_CBC_DECRYPT * K];
-        p.hdr->kind_tiles[kKindCbcEnc] = t01.t;
-        p.hdr->kind_tiles[kKindCbcEnc + 1] = t01.t + t2.t;
-        p.hdr->tiles[0] = t01.t;
-        p.hdr->tiles[1] = t2.t;
-        p.hdr->slices[0] = t01.s;
-        p.hdr->slices[1] = t2.s;
-        p.hdr->slice2_base = s2;
+        if (g == g_ctr) p.hdr->kind_tiles[kKindCtr] = run.t;
+        if (g == g_cbc) p.hdr->kind_tiles[kKindCbcDec] = run.t;
+        run = add(run, group_sums(p, g));
     }
 }
 
@@ -640,7 +680,7 @@ size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 // Scratch layout: header, five per-group arrays, order, tile and slice maps.
 struct UniLayout {
     size_t groups, max_tiles, max_slices;
-    size_t o_counts, o_cursor, o_msg, o_tile, o_slice, o_order, o_tg, o_sg, total;
+    size_t o_counts, o_cursor, o_msg, o_tile, o_slice, o_order, o_tg, o_sg, o_part, o_base, total;
 };
 
 UniLayout layout_for(uint64_t n_msgs, uint32_t m, uint32_t n_keys) {
@@ -658,7 +698,9 @@ UniLayout layout_for(uint64_t n_msgs, uint32_t m, uint32_t n_keys) {
     L.o_order = L.o_slice + g4;
     L.o_tg = L.o_order + al256(n_msgs * 4);
     L.o_sg = L.o_tg + al256(L.max_tiles * 4);
-    L.total = L.o_sg + al256(L.max_slices * 4);
+    L.o_part = L.o_sg + al256(L.max_slices * 4);
+    L.o_base = L.o_part + al256((size_t)scan_blocks(n_keys) * sizeof(Sums));
+    L.total = L.o_base + al256((size_t)scan_blocks(n_keys) * sizeof(Sums));
     return L;
 }
 
@@ -804,7 +846,12 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
     if (e == cudaSuccess) {
         what = "planning kernels";
         uni_count_kernel<<<grid, 256, 0, s>>>(p);
-        uni_scan_kernel<<<1, kScanThreads, 0, s>>>(p);
+        Sums* part = reinterpret_cast<Sums*>(base + L.o_part);
+        Sums* bases = reinterpret_cast<Sums*>(base + L.o_base);
+        const unsigned nblk = scan_blocks(kt->count);
+        uni_scan_partial_kernel<<<nblk, kScanThreads, 0, s>>>(p, part);
+        uni_scan_top_kernel<<<1, kScanThreads, 0, s>>>(p, part, bases);
+        uni_scan_final_kernel<<<nblk, kScanThreads, 0, s>>>(p, bases);
         uni_map_kernel<<<grid, 256, 0, s>>>(p);
         uni_scatter_kernel<<<grid, 256, 0, s>>>(p);
         e = cudaGetLastError();
