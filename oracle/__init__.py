@@ -28,5 +28,6 @@ from .oracle import (  # noqa: F401
     tdes_cbc_encrypt,
     tdes_ctr,
     tdes_ecb,
+    tdes_messages,
     tdes_parallel,
 )

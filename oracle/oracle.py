@@ -103,6 +103,10 @@ class Oracle:
                                              ctypes.c_uint32, u8p, u8p, ctypes.c_uint64,
                                              ctypes.c_int]
         lib.oracle_tdes_parallel.restype = ctypes.c_int
+        vp = ctypes.c_void_p
+        lib.oracle_tdes_messages.argtypes = [vp, ctypes.c_uint32, vp, vp, vp, vp, vp, vp, vp,
+                                             ctypes.c_uint64, ctypes.c_int]
+        lib.oracle_tdes_messages.restype = ctypes.c_int
         self.lib = lib
         self.path = path
 
@@ -210,6 +214,33 @@ class Oracle:
         return out
 
 
+    def tdes_messages(self, keys, key_index, mode, iv_or_ctr, offset, nblocks, data,
+                      threads: int = 1) -> np.ndarray:
+        """Independent messages under their own triples and modes (see
+        oracle_tdes_messages); returns a copy of ``data`` with every message
+        replaced by its result."""
+        k = np.ascontiguousarray(np.asarray(keys, dtype=np.uint8).reshape(-1, 24))
+        ki = np.ascontiguousarray(key_index, dtype=np.uint32)
+        md = np.ascontiguousarray(mode, dtype=np.uint8)
+        iv = np.ascontiguousarray(np.asarray(iv_or_ctr).astype(np.uint64))
+        off = np.ascontiguousarray(offset, dtype=np.uint64)
+        nb = np.ascontiguousarray(nblocks, dtype=np.uint64)
+        d = np.ascontiguousarray(data, dtype=np.uint8)
+        n = ki.size
+        if not (md.size == iv.size == off.size == nb.size == n):
+            raise ValueError("one key index, mode, IV, offset and length per message")
+        if n and int((off + 8 * nb).max()) > d.size:
+            raise ValueError("a message extends past the buffer")
+        out = d.copy()
+        rc = self.lib.oracle_tdes_messages(k.ctypes.data, k.shape[0], ki.ctypes.data,
+                                           md.ctypes.data, iv.ctypes.data, off.ctypes.data,
+                                           nb.ctypes.data, d.ctypes.data, out.ctypes.data, n,
+                                           int(threads))
+        if rc != 0:
+            raise ValueError("bad message for oracle_tdes_messages")
+        return out
+
+
 def default() -> Oracle:
     global _default
     with _lock:
@@ -252,6 +283,11 @@ def tdes_cbc_decrypt(keys, iv, data):
 
 def tdes_parallel(keys, data, mode="ecb_enc", nonce=0, ctr0=0, threads=1):
     return default().tdes_parallel(keys, data, mode, nonce, ctr0, threads)
+
+
+def tdes_messages(keys, key_index, mode, iv_or_ctr, offset, nblocks, data, threads=1):
+    return default().tdes_messages(keys, key_index, mode, iv_or_ctr, offset, nblocks, data,
+                                   threads)
 
 
 def des_ecb(key, data, decrypt=False):

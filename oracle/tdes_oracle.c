@@ -438,3 +438,64 @@ int oracle_tdes_parallel(const uint8_t keys[24], int mode, uint32_t nonce, uint3
         if (jobs[t].k != NULL) pthread_join(tid[t], NULL);
     return 0;
 }
+
+/* ---- many messages, each under its own triple and mode (batch checks) ---- */
+
+typedef struct {
+    const uint8_t *keys;
+    const uint32_t *key_index;
+    const uint8_t *mode;
+    const uint64_t *iv;
+    const uint64_t *offset, *nblocks;
+    const uint8_t *in;
+    uint8_t *out;
+    uint64_t first, end;
+} msg_job;
+
+static void *msg_worker(void *arg) {
+    msg_job *j = (msg_job *)arg;
+    for (uint64_t i = j->first; i < j->end; ++i) {
+        const uint8_t *k = j->keys + 24 * (uint64_t)j->key_index[i];
+        const uint8_t *in = j->in + j->offset[i];
+        uint8_t *out = j->out + j->offset[i];
+        const uint64_t nb = j->nblocks[i], iv = j->iv[i];
+        switch (j->mode[i]) {
+        case 0: oracle_tdes_ecb(k, 0, in, out, nb); break;
+        case 1: oracle_tdes_ecb(k, 1, in, out, nb); break;
+        case 2: oracle_tdes_ctr(k, (uint32_t)(iv >> 32), (uint32_t)iv, in, out, nb); break;
+        case 3: oracle_tdes_cbc_decrypt(k, iv, in, out, nb); break;
+        default: oracle_tdes_cbc_encrypt(k, iv, in, out, nb); break;
+        }
+    }
+    return NULL;
+}
+
+int oracle_tdes_messages(const uint8_t *keys, uint32_t n_keys, const uint32_t *key_index,
+                         const uint8_t *mode, const uint64_t *iv_or_ctr, const uint64_t *offset,
+                         const uint64_t *nblocks, const uint8_t *in, uint8_t *out, uint64_t n,
+                         int nthreads) {
+    if (nthreads < 1 || nthreads > 1024) return -1;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (key_index[i] >= n_keys || mode[i] > 4) return -1;
+        if (mode[i] == 2 && (iv_or_ctr[i] & 0xFFFFFFFFull) + nblocks[i] > ((uint64_t)1 << 32))
+            return -1;
+    }
+    pthread_t tid[1024];
+    msg_job jobs[1024];
+    const uint64_t per_thread = (n + (uint64_t)nthreads - 1) / (uint64_t)nthreads;
+    int started = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        uint64_t first = per_thread * (uint64_t)t, end = first + per_thread;
+        if (first >= n) break;
+        if (end > n) end = n;
+        jobs[t] = (msg_job){keys, key_index, mode, iv_or_ctr, offset, nblocks, in, out, first, end};
+        if (pthread_create(&tid[t], NULL, msg_worker, &jobs[t]) != 0) {
+            msg_worker(&jobs[t]); /* run inline if a thread cannot start */
+            jobs[t].keys = NULL;
+        }
+        started = t + 1;
+    }
+    for (int t = 0; t < started; ++t)
+        if (jobs[t].keys != NULL) pthread_join(tid[t], NULL);
+    return 0;
+}

@@ -58,6 +58,20 @@ void oracle_des_cbc_decrypt(const uint8_t key[8], uint64_t iv, const uint8_t *in
 int oracle_tdes_parallel(const uint8_t keys[24], int mode, uint32_t nonce, uint32_t ctr0,
                          const uint8_t *in, uint8_t *out, uint64_t nblocks, int nthreads);
 
+/* Many independent messages, each under its own triple and mode, for
+ * checking whole batches: message i is the nblocks[i] blocks at byte offset
+ * offset[i] of in, written at the same offset of out, under the triple
+ * keys[24 * key_index[i] ..] (n_keys triples) in mode[i]: 0 ECB encrypt,
+ * 1 ECB decrypt, 2 CTR (iv_or_ctr[i] = nonce << 32 | ctr0), 3 CBC decrypt,
+ * 4 CBC encrypt (iv_or_ctr[i] = IV).  Each message is computed by the mode
+ * functions above; messages are split into contiguous ranges over nthreads
+ * host threads.  Returns -1 and writes nothing if any message has a key
+ * index >= n_keys, a mode > 4 or a CTR counter that would pass 2^32. */
+int oracle_tdes_messages(const uint8_t *keys, uint32_t n_keys, const uint32_t *key_index,
+                         const uint8_t *mode, const uint64_t *iv_or_ctr, const uint64_t *offset,
+                         const uint64_t *nblocks, const uint8_t *in, uint8_t *out, uint64_t n,
+                         int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

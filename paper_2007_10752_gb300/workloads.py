@@ -119,14 +119,22 @@ def uniform_iv(torch, w, mode):
 def uniform_expected_fields(seed, i, n_keys):
     """Host copy of message i's (key index, mode, iv_or_ctr) as drawn by
     uniform_arrays_device."""
-    key = int(synth.u64s(seed, 1, synth.STREAM_KEYPICK, first=i)[0] % np.uint64(n_keys))
-    mode = int(_modes_at(seed, i))
-    iv = int(synth.u64s(seed, 1, synth.STREAM_IV, first=i)[0])
-    if mode == 2:
-        iv &= 0xFFFFFFFF00000000
+    k, m, v = uniform_expected_arrays(seed, np.array([i], dtype=np.uint64), n_keys)
+    return int(k[0]), int(m[0]), int(v[0])
+
+
+def uniform_expected_arrays(seed, idx, n_keys):
+    """(key index, mode, iv_or_ctr) arrays of the messages at indices ``idx``
+    (any order), as drawn by uniform_arrays_device: word idx of each stream."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    key = (synth.splitmix64_at(synth.substream(seed, synth.STREAM_KEYPICK), idx)
+           % np.uint64(n_keys)).astype(np.uint32)
+    u = (synth.splitmix64_at(synth.substream(seed, synth.STREAM_MODE), idx)
+         >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    p = np.asarray(MODE_MIX, dtype=np.float64)
+    cat = np.minimum(np.searchsorted(np.cumsum(p / p.sum()), u, side="right"), len(p) - 1)
+    mode = np.array([0, 2, 3, 4], dtype=np.uint8)[cat]
+    iv = synth.splitmix64_at(synth.substream(seed, synth.STREAM_IV), idx)
+    iv = np.where(mode == 2, iv & np.uint64(0xFFFFFFFF00000000), iv)
     return key, mode, iv
 
-
-def _modes_at(seed, i):
-    return np.array([0, 2, 3, 4], dtype=np.uint32)[
-        synth.categorical(seed, 1, list(MODE_MIX), synth.STREAM_MODE, first=i)][0]

@@ -1,9 +1,12 @@
 """Large streaming, processed in place in one persistent launch: a 32 GiB
 seeded buffer whose first 16 GiB is one single-key CTR stream and whose next
 64 MiB are 2^20 messages of 64 bytes under 65536 key triples (modes
-ECB 40% / CTR 30% / CBC-decrypt 20% / CBC-encrypt 10%).  Sampled messages
-and CTR windows are recomputed by the oracle from inputs regenerated by the
-counter-based generator; bytes outside the processed ranges are unchanged."""
+ECB 40% / CTR 30% / CBC-decrypt 20% / CBC-encrypt 10%).  Every message, and
+2^20 seeded random blocks plus windows of the CTR stream, are recomputed by
+the oracle (on all host cores) from inputs regenerated by the counter-based
+generator; bytes outside the processed ranges are unchanged."""
+import os
+
 import numpy as np
 import pytest
 
@@ -35,7 +38,7 @@ def test_device_fill_matches_host_generator(cuda_lib):
     assert (t.cpu().numpy() == synth.random_bytes(77, t.numel(), start_byte=8 * 12345)).all()
 
 
-def test_large_streaming_sampled(cuda_lib):
+def test_large_streaming_every_message(cuda_lib):
     T = cuda_lib
     import torch as _t
     buf, kt, d, keys, nonce = build_streaming(_t, T)
@@ -44,15 +47,28 @@ def test_large_streaming_sampled(cuda_lib):
     b.launch_graph()
     torch.cuda.synchronize()
     rng = np.random.default_rng(SEED)
-    # 64-byte messages
-    pick = np.sort(rng.choice(N_SMALL, 3000, replace=False))
-    got = buf[STREAM_BYTES:STREAM_BYTES + 64 * N_SMALL].view(-1, 64)[torch.from_numpy(pick).cuda()]
-    got = got.cpu().numpy()
-    for row, i in enumerate(pick):
-        e = d[1 + i]
-        data = synth.random_bytes(SEED, 64, start_byte=STREAM_BYTES + 64 * int(i))
-        want = _oracle(int(e["mode"]), keys[int(e["key_index"])].tobytes(), int(e["iv_or_ctr"]), data)
-        assert (got[row] == want).all(), f"message {i} mode {e['mode']}"
+    threads = max(1, min(64, os.cpu_count() or 1))
+    # every 64-byte message
+    e = d[1:]
+    got = buf[STREAM_BYTES:STREAM_BYTES + 64 * N_SMALL].cpu().numpy()
+    want = oracle.tdes_messages(keys, e["key_index"], e["mode"].astype(np.uint8),
+                                e["iv_or_ctr"], 64 * np.arange(N_SMALL, dtype=np.uint64),
+                                np.full(N_SMALL, 8, dtype=np.uint64),
+                                synth.random_bytes(SEED, 64 * N_SMALL, start_byte=STREAM_BYTES),
+                                threads)
+    bad = np.nonzero((got != want).reshape(N_SMALL, 64).any(axis=1))[0]
+    assert bad.size == 0, f"{bad.size} messages differ, first {bad[:5]}"
+    # 2^20 seeded random blocks of the CTR stream, each a one-block CTR message
+    nblk = STREAM_BYTES // 8
+    pos = np.unique(rng.integers(0, nblk, 1 << 20, dtype=np.uint64))
+    gotb = buf.view(torch.int64)[torch.from_numpy(pos.astype(np.int64)).cuda()].cpu().numpy()
+    wantb = oracle.tdes_messages(keys, np.full(pos.size, N_KEYS, dtype=np.uint32),
+                                 np.full(pos.size, 2, dtype=np.uint8),
+                                 (np.uint64(nonce) << np.uint64(32)) | pos,
+                                 8 * np.arange(pos.size, dtype=np.uint64),
+                                 np.ones(pos.size, dtype=np.uint64),
+                                 synth.blocks_at(SEED, pos).reshape(-1), threads)
+    assert (gotb.view(np.uint8) == wantb).all(), "CTR stream block"
     # CTR stream windows (counter = block index from 0)
     kctr = keys[N_KEYS].tobytes()
     nblk = STREAM_BYTES // 8

@@ -261,8 +261,9 @@ def test_uniform_argument_errors(cuda_lib):
 
 def test_uniform_full_size_sampled(cuda_lib):
     """The second 16 GiB of the streaming workload read as 2^28 messages of 64
-    bytes under 65536 key triples (device-drawn arrays), in place; 3000
-    sampled messages against the oracle."""
+    bytes under 65536 key triples (device-drawn arrays), in place; 2^20
+    seeded random messages (and the first and last) against the oracle."""
+    import os
     seed, n, n_keys, mb = workloads.STREAM_SEED, workloads.STREAM_N_UNIFORM, 65536, 64
     keys = synth.key_triples(seed, n_keys)
     kt = cuda_lib.KeyTable(keys)
@@ -271,18 +272,22 @@ def test_uniform_full_size_sampled(cuda_lib):
     synth.fill_device(buf, seed, start_byte=start)
     k, md, v = workloads.uniform_arrays_device(torch, seed, n, n_keys)
     skipped = torch.full((1,), -1, dtype=torch.int64, device="cuda")
-    rng = np.random.default_rng(seed)
-    idx = np.concatenate([[0, 1, n - 1], rng.integers(0, n, 3000)])
     scratch = cuda_lib.tdes_uniform_crypt(kt, k, md, v, buf, buf, mb, skipped=skipped)
     torch.cuda.synchronize()
     assert skipped.item() == 0
     info = cuda_lib.tdes_uniform_info(scratch)
     assert info["key_tiles"] > 0 and info["mixed_slices"] > 0 and info["chain_slices"] > 0
-    for i in idx:
-        i = int(i)
-        key, mode, iv = workloads.uniform_expected_fields(seed, i, n_keys)
-        data = synth.random_bytes(seed, mb, start_byte=start + i * mb)
-        got = buf[i * mb:(i + 1) * mb].cpu().numpy()
-        assert (got == oracle_msg(mode, keys[key].tobytes(), iv, data)).all(), i
-    del buf, k, md, v, scratch
+    del k, md, v, scratch
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 1 << 20)])).astype(np.uint64)
+    key, mode, iv = workloads.uniform_expected_arrays(seed, idx, n_keys)
+    got = buf.view(-1, mb)[torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
+    blocks = (np.uint64(start // 8) + np.uint64(8) * idx)[:, None] + np.arange(8, dtype=np.uint64)
+    data = synth.blocks_at(seed, blocks.reshape(-1)).reshape(-1)
+    want = oracle.tdes_messages(keys, key, mode, iv, mb * np.arange(idx.size, dtype=np.uint64),
+                                np.full(idx.size, 8, dtype=np.uint64), data,
+                                max(1, min(64, os.cpu_count() or 1)))
+    bad = np.nonzero((got.reshape(-1) != want).reshape(-1, mb).any(axis=1))[0]
+    assert bad.size == 0, f"{bad.size} messages differ, first {idx[bad[:5]]} modes {mode[bad[:5]]}"
+    del buf
     torch.cuda.empty_cache()

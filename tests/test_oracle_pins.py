@@ -380,3 +380,45 @@ def test_planted_mistake_is_caught(name, old, new, mutant_dir):
 
 def test_real_oracle_passes_every_check():
     assert _run_all_checks(oracle.default()) == []
+
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_messages_entry_equals_per_message_calls(threads):
+    """oracle_tdes_messages is a loop over the pinned mode functions: every
+    message equals the same mode function called on it alone, whatever the
+    thread split; bytes between messages are copied through."""
+    rng = np.random.default_rng(41)
+    keys = synth.key_triples(41, 5)
+    n = 300
+    nblocks = rng.integers(0, 12, n).astype(np.uint64)
+    gaps = rng.integers(0, 3, n) * 8
+    offset = np.concatenate([[0], np.cumsum(8 * nblocks + gaps)])[:-1].astype(np.uint64)
+    data = synth.random_bytes(41, int(offset[-1] + 8 * nblocks[-1]) + 16)
+    key_index = rng.integers(0, 5, n).astype(np.uint32)
+    mode = rng.integers(0, 5, n).astype(np.uint8)
+    iv = synth.u64s(41, n, synth.STREAM_IV)
+    iv[mode == 2] &= np.uint64(0xFFFFFFFF000FFFFF)
+    got = oracle.tdes_messages(keys, key_index, mode, iv, offset, nblocks, data, threads)
+    want = data.copy()
+    for i in range(n):
+        k, s = keys[key_index[i]].tobytes(), slice(int(offset[i]), int(offset[i] + 8 * nblocks[i]))
+        v, d = int(iv[i]), data[s]
+        want[s] = [lambda: oracle.tdes_ecb(k, d), lambda: oracle.tdes_ecb(k, d, decrypt=True),
+                   lambda: oracle.tdes_ctr(k, v >> 32, v & 0xFFFFFFFF, d),
+                   lambda: oracle.tdes_cbc_decrypt(k, v, d),
+                   lambda: oracle.tdes_cbc_encrypt(k, v, d)][int(mode[i])]()
+    assert (got == want).all()
+
+
+def test_messages_entry_rejects_bad_messages():
+    keys = synth.key_triples(42, 2)
+    data = synth.random_bytes(42, 64)
+    one = dict(offset=[0], nblocks=[8], data=data)
+    with pytest.raises(ValueError):
+        oracle.tdes_messages(keys, [2], [0], [0], **one)             # key index out of range
+    with pytest.raises(ValueError):
+        oracle.tdes_messages(keys, [0], [5], [0], **one)             # no such mode
+    with pytest.raises(ValueError):
+        oracle.tdes_messages(keys, [0], [2], [0xFFFFFFFC], **one)    # counter passes 2^32
+    with pytest.raises(ValueError):
+        oracle.tdes_messages(keys, [0], [0], [0], [8], [8], data)    # past the buffer
