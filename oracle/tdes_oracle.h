@@ -5,6 +5,8 @@
  * Parallelization of 3DES Encryption on GPU", Sec. III: one byte per bit,
  * 1-indexed appendix tables.  Only tests, the smoke check and the CPU
  * baseline of the benchmark use it; the CUDA library shares nothing with it.
+ * Two helpers at the end split work over host threads (the CPU baseline's
+ * timing, and checks of whole batches); each thread runs the same code.
  *
  * Byte conventions: blocks and keys are 8-byte big-endian strings (bit 1 =
  * MSB of byte 0).  A key triple is 24 bytes K1||K2||K3.  Buffers hold
