@@ -401,7 +401,9 @@ __device__ __forceinline__ uint2 cbc_prev(const UniParams& p, uint32_t mi, uint3
 
 // One single-key tile of ECB, CTR or CBC-decryption messages.  VEC16: every
 // pair is one 16-byte-aligned piece of one message (m even, in and out
-// 16-byte aligned).
+// 16-byte aligned); that path has no branch per pair (an out-of-tile slot,
+// possible when m does not divide 1024, reads a clamped message and is
+// masked), so the loads of all 16 pairs are in flight together.
 template <int KIND, bool VEC16>
 __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
                                                const uint32_t* __restrict__ tab, uint32_t lane,
@@ -412,7 +414,22 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
     for (int j = 0; j < 16; ++j) {
         const PairSlots q = pair_slots(p, 64u * j + 2u * lane);
         uint2 v0, v1;
-        load_pair<KIND == kKindCtr, VEC16>(p, pos0, q, v0, v1);
+        if (VEC16) {
+            const bool ok = q.slot0 < p.per_tile;
+            const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
+            if (KIND == kKindCtr) {
+                const uint64_t c0 = p.iv[mi0];
+                v0 = ctr_words(c0, q.blk0);
+                v1 = ctr_words(c0, q.blk0 + 1u);
+            } else {
+                const uint4 w = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
+                v0 = make_uint2(w.x, w.y);
+                v1 = make_uint2(w.z, w.w);
+            }
+            if (!ok) v0 = v1 = make_uint2(0u, 0u);
+        } else {
+            load_pair<KIND == kKindCtr, false>(p, pos0, q, v0, v1);
+        }
         A0[2 * j] = v0.x;
         A1[2 * j] = v0.y;
         A0[2 * j + 1] = v1.x;
@@ -420,34 +437,39 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
     }
     tdes_process32_compact<false>(A0, A1, tab, one_pass);
     pos0 = tile_pos0(p, t);  // reloaded: nothing but the planes stays live across the rounds
-    if (KIND == kKindCtr) {
+    if (KIND == kKindCtr || KIND == kKindCbcDec) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const PairSlots q = pair_slots(p, 64u * j + 2u * lane);
-            uint2 v0, v1;
-            load_pair<false, VEC16>(p, pos0, q, v0, v1);
-            A0[2 * j] ^= v0.x;
-            A1[2 * j] ^= v0.y;
-            A0[2 * j + 1] ^= v1.x;
-            A1[2 * j + 1] ^= v1.y;
-        }
-    } else if (KIND == kKindCbcDec) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const PairSlots q = pair_slots(p, 64u * j + 2u * lane);
-            if (q.slot0 < p.per_tile) {
+            uint2 v0 = make_uint2(0u, 0u), v1 = make_uint2(0u, 0u);
+            if (VEC16) {
+                const bool ok = q.slot0 < p.per_tile;
+                const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
+                if (KIND == kKindCtr) {
+                    const uint4 w = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
+                    v0 = make_uint2(w.x, w.y);
+                    v1 = make_uint2(w.z, w.w);
+                } else {  // the block before blk0 (or the IV), and blk0 itself
+                    const uint2 b = msg_in(p, mi0)[q.blk0 ? q.blk0 - 1u : 0u];
+                    const uint2 iv = q.blk0 ? make_uint2(0u, 0u) : iv_words(p.iv[mi0]);
+                    v0 = q.blk0 ? b : iv;
+                    v1 = msg_in(p, mi0)[q.blk0];
+                }
+                if (!ok) v0 = v1 = make_uint2(0u, 0u);
+            } else if (KIND == kKindCtr) {
+                load_pair<false, false>(p, pos0, q, v0, v1);
+            } else if (q.slot0 < p.per_tile) {
                 const uint32_t mi0 = p.order[pos0 + q.slot0];
-                const uint2 v0 = cbc_prev(p, mi0, q.blk0);
-                uint2 v1 = make_uint2(0u, 0u);
+                v0 = cbc_prev(p, mi0, q.blk0);
                 if (q.slot1 == q.slot0)
                     v1 = msg_in(p, mi0)[q.blk0];
                 else if (q.slot1 < p.per_tile)
                     v1 = iv_words(p.iv[p.order[pos0 + q.slot1]]);  // blk1 = 0
-                A0[2 * j] ^= v0.x;
-                A1[2 * j] ^= v0.y;
-                A0[2 * j + 1] ^= v1.x;
-                A1[2 * j + 1] ^= v1.y;
             }
+            A0[2 * j] ^= v0.x;
+            A1[2 * j] ^= v0.y;
+            A0[2 * j + 1] ^= v1.x;
+            A1[2 * j + 1] ^= v1.y;
         }
     }
     __syncwarp();  // in place: every read of the tile's messages precedes its writes
