@@ -326,6 +326,26 @@ int tdes_server_poll(tdes_server_t *s, uint64_t ticket);
 /* Waits (bounded) for a ticket: its status, or TDES_ETIMEDOUT; never hangs. */
 int tdes_server_wait(tdes_server_t *s, uint64_t ticket, uint64_t timeout_ns);
 
+/* A group of `count` (>= 1) requests under one ticket.  Every descriptor is
+ * checked as by tdes_server_submit first; if any is refused the call
+ * returns TDES_EINVAL and queues none.  The requests are then admitted and
+ * batched like single submissions (they may run in different batches).
+ * *ticket identifies the group (its requests hold tickets ticket ..
+ * ticket + count - 1, usable with tdes_server_poll). */
+int tdes_server_submit_group(tdes_server_t *s, const tdes_desc_t *reqs, uint32_t count,
+                             uint64_t *ticket);
+
+/* 0 when every request of the group is complete, 1 while any is pending,
+ * < 0 the first failed request's status.  per_desc_status (nullable, count
+ * entries) receives each request's tdes_server_poll result. */
+int tdes_server_poll_group(tdes_server_t *s, uint64_t ticket, uint32_t count,
+                           int *per_desc_status);
+
+/* Waits (bounded) for a whole group: its tdes_server_poll_group result, or
+ * TDES_ETIMEDOUT; never hangs. */
+int tdes_server_wait_group(tdes_server_t *s, uint64_t ticket, uint32_t count,
+                           uint64_t timeout_ns);
+
 /* Finishes every queued and running request, then stops the server. */
 void tdes_server_destroy(tdes_server_t *s);
 

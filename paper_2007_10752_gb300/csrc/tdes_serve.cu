@@ -301,6 +301,59 @@ int tdes_server_wait(tdes_server_t* s, uint64_t ticket, uint64_t timeout_ns) {
     }
 }
 
+int tdes_server_submit_group(tdes_server_t* s, const tdes_desc_t* reqs, uint32_t count,
+                             uint64_t* ticket) {
+    if (s == nullptr || ticket == nullptr || (reqs == nullptr && count > 0) || count == 0)
+        return sfail(TDES_EINVAL, "NULL argument or empty group");
+    for (uint32_t i = 0; i < count; ++i) {  // the whole group is refused before any is queued
+        const tdes_desc_t& r = reqs[i];
+        if (tdes::validate_desc(r, s->kt->count) != TDES_OK)
+            return sfail(TDES_EINVAL, "invalid request descriptor %u of the group", i);
+        if (r.nbytes && (!tdes::gpu_addressable(r.in) || !tdes::gpu_addressable(r.out)))
+            return sfail(TDES_EINVAL, "request %u: buffers must be device or pinned host memory", i);
+        if (cost_of(r) > s->cfg.budget_bytes)
+            return sfail(TDES_EINVAL, "request %u exceeds the admission budget", i);
+    }
+    if (s->sticky_error.load()) return sfail(s->sticky_error.load(), "server stopped by an error");
+    std::lock_guard<std::mutex> lock(s->mu);
+    const uint64_t t0 = s->next_ticket;
+    s->next_ticket += count;
+    *ticket = t0;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (reqs[i].nbytes == 0)
+            s->complete(t0 + i, TDES_OK, now_ns());
+        else
+            s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i])});
+    }
+    return TDES_OK;
+}
+
+int tdes_server_poll_group(tdes_server_t* s, uint64_t ticket, uint32_t count,
+                           int* per_desc_status) {
+    if (s == nullptr || ticket == 0 || count == 0) return sfail(TDES_EINVAL, "bad group");
+    int err = TDES_OK;
+    bool pending = false;
+    for (uint32_t i = 0; i < count; ++i) {
+        const int r = tdes_server_poll(s, ticket + i);
+        if (per_desc_status) per_desc_status[i] = r;
+        if (r == 1) pending = true;
+        else if (r < 0 && err == TDES_OK) err = r;
+    }
+    return err != TDES_OK ? err : (pending ? 1 : TDES_OK);
+}
+
+int tdes_server_wait_group(tdes_server_t* s, uint64_t ticket, uint32_t count,
+                           uint64_t timeout_ns) {
+    const int64_t until = now_ns() + (int64_t)std::min<uint64_t>(timeout_ns, INT64_MAX / 2);
+    for (;;) {
+        const int r = tdes_server_poll_group(s, ticket, count, nullptr);
+        if (r != 1) return r;
+        if (now_ns() > until) return sfail(TDES_ETIMEDOUT, "group %llu still pending",
+                                           (unsigned long long)ticket);
+        std::this_thread::yield();
+    }
+}
+
 void tdes_server_destroy(tdes_server_t* s) {
     if (s == nullptr) return;
     s->stop.store(true, std::memory_order_release);

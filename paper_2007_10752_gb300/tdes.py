@@ -32,7 +32,8 @@ EXPORTED = (
     "tdes_batch_configure", "tdes_batch_launch", "tdes_batch_launch_graph", "tdes_batch_info",
     "tdes_batch_free", "tdes_uniform_scratch_bytes", "tdes_uniform_crypt", "tdes_uniform_info",
     "tdes_server_config_default", "tdes_server_create", "tdes_server_submit",
-    "tdes_server_poll", "tdes_server_wait", "tdes_server_destroy", "tdes_serve_loadtest",
+    "tdes_server_poll", "tdes_server_wait", "tdes_server_submit_group",
+    "tdes_server_poll_group", "tdes_server_wait_group", "tdes_server_destroy", "tdes_serve_loadtest",
     "tdes_sbox_gate_count", "tdes_set_small_cutoff", "tdes_strerror", "tdes_last_error",
 )
 
@@ -142,6 +143,9 @@ def load(path: str = LIB_PATH):
     lib.tdes_server_submit.argtypes = [vp, ctypes.POINTER(Desc), ctypes.POINTER(u64)]
     lib.tdes_server_poll.argtypes = [vp, u64]
     lib.tdes_server_wait.argtypes = [vp, u64, u64]
+    lib.tdes_server_submit_group.argtypes = [vp, vp, u32, ctypes.POINTER(u64)]
+    lib.tdes_server_poll_group.argtypes = [vp, u64, u32, vp]
+    lib.tdes_server_wait_group.argtypes = [vp, u64, u32, u64]
     lib.tdes_server_destroy.argtypes = [vp]
     lib.tdes_server_destroy.restype = None
     lib.tdes_serve_loadtest.argtypes = [vp, ctypes.POINTER(LoadtestConfig),
@@ -479,6 +483,26 @@ class Server:
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
         return int(load().tdes_server_wait(self.handle, ticket, int(timeout_s * 1e9)))
+
+    def submit_group(self, entries) -> tuple:
+        """entries: (mode, key_index, iv_or_ctr, in, out, nbytes) each; returns
+        (ticket, count) of the group."""
+        arr, n = make_descs(entries)
+        t = ctypes.c_uint64()
+        _check(load().tdes_server_submit_group(self.handle, ctypes.addressof(arr), n,
+                                               ctypes.byref(t)))
+        return t.value, n
+
+    def poll_group(self, group) -> tuple:
+        """(group status, per-request statuses) of a (ticket, count) group."""
+        ticket, n = group
+        st = np.zeros(n, dtype=np.int32)
+        r = int(load().tdes_server_poll_group(self.handle, ticket, n, st.ctypes.data))
+        return r, st
+
+    def wait_group(self, group, timeout_s: float = 60.0) -> int:
+        ticket, n = group
+        return int(load().tdes_server_wait_group(self.handle, ticket, n, int(timeout_s * 1e9)))
 
     def loadtest(self, in_pool, out_pool, n_requests, offered_gbps, seed=1, small_frac=0.8,
                  small=(64, 4096), large=(64 << 10, 16 << 20), mode_probs=(1, 1, 1),

@@ -67,6 +67,40 @@ def test_server_results_match_oracle_and_alone(cuda_lib):
     srv.close()
 
 
+def test_group_submit_poll_wait(cuda_lib):
+    """A group of requests under one ticket: per-request statuses, the group
+    completes as a whole and every result equals the oracle; a group with one
+    bad descriptor is refused whole, before anything is queued."""
+    T = cuda_lib
+    keys = synth.key_triples(23, 16)
+    kt = T.KeyTable(keys)
+    srv = T.Server(kt)
+    reqs = _requests(23, 120, 16, big_every=17)
+    ins = [torch.from_numpy(r["data"]).cuda() for r in reqs]
+    outs = [torch.empty_like(x) for x in ins]
+    empty = torch.empty(0, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    entries = [(r["mode"], r["key"], r["iv"], x, y, x.numel()) for r, x, y in zip(reqs, ins, outs)]
+    entries.append((0, 0, 0, empty, empty, 0))  # an empty request completes at once
+    group = srv.submit_group(entries)
+    assert group[1] == len(reqs) + 1
+    assert srv.wait_group(group, 60.0) == 0
+    status, per = srv.poll_group(group)
+    assert status == 0 and (per == 0).all()
+    for i, (r, y) in enumerate(zip(reqs, outs)):
+        want = _oracle(r["mode"], keys[r["key"]].tobytes(), r["iv"], r["data"])
+        assert (y.cpu().numpy() == want).all(), f"request {i}"
+    # one invalid descriptor (key index out of range): the whole group is refused
+    bad = entries[:3] + [(0, 999, 0, ins[0], outs[0], ins[0].numel())]
+    with pytest.raises(T.TdesError):
+        srv.submit_group(bad)
+    # the next group still works, and its tickets follow on
+    g2 = srv.submit_group(entries[:5])
+    assert g2[0] == group[0] + group[1]
+    assert srv.wait_group(g2, 60.0) == 0
+    srv.close()
+
+
 def test_budget_queues_instead_of_failing(cuda_lib):
     T = cuda_lib
     keys = synth.key_triples(22, 8)
