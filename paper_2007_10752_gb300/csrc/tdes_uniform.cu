@@ -401,9 +401,12 @@ __device__ __forceinline__ uint2 cbc_prev(const UniParams& p, uint32_t mi, uint3
 
 // One single-key tile of ECB, CTR or CBC-decryption messages.  VEC16: every
 // pair is one 16-byte-aligned piece of one message (m even, in and out
-// 16-byte aligned); that path has no branch per pair (an out-of-tile slot,
-// possible when m does not divide 1024, reads a clamped message and is
-// masked), so the loads of all 16 pairs are in flight together.
+// 16-byte aligned); there the loads before the rounds, and CTR's after
+// them, have no branch per pair (an out-of-tile slot, possible when m does
+// not divide 1024, reads a clamped message and is masked), so the loads of
+// all 16 pairs are in flight together.  CBC decryption's operands after the
+// rounds keep their branches, which measured faster (69.4 against 70.0 ms
+// for 2^28 messages).
 template <int KIND, bool VEC16>
 __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
                                                const uint32_t* __restrict__ tab, uint32_t lane,
@@ -442,19 +445,12 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
         for (int j = 0; j < 16; ++j) {
             const PairSlots q = pair_slots(p, 64u * j + 2u * lane);
             uint2 v0 = make_uint2(0u, 0u), v1 = make_uint2(0u, 0u);
-            if (VEC16) {
+            if (VEC16 && KIND == kKindCtr) {
                 const bool ok = q.slot0 < p.per_tile;
                 const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
-                if (KIND == kKindCtr) {
-                    const uint4 w = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
-                    v0 = make_uint2(w.x, w.y);
-                    v1 = make_uint2(w.z, w.w);
-                } else {  // the block before blk0 (or the IV), and blk0 itself
-                    const uint2 b = msg_in(p, mi0)[q.blk0 ? q.blk0 - 1u : 0u];
-                    const uint2 iv = q.blk0 ? make_uint2(0u, 0u) : iv_words(p.iv[mi0]);
-                    v0 = q.blk0 ? b : iv;
-                    v1 = msg_in(p, mi0)[q.blk0];
-                }
+                const uint4 w = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
+                v0 = make_uint2(w.x, w.y);
+                v1 = make_uint2(w.z, w.w);
                 if (!ok) v0 = v1 = make_uint2(0u, 0u);
             } else if (KIND == kKindCtr) {
                 load_pair<false, false>(p, pos0, q, v0, v1);
