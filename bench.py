@@ -633,7 +633,9 @@ def run_paper_context(torch, tdes, synth, x, y, ks, stream):
 # ------------------------------------------------------- large streaming
 STREAM_WORKLOAD = ("32 GiB seeded buffer in place: [0, 16 GiB) one single-key CTR stream, then "
                    "2^20 messages of 64 B under 65536 seeded key triples (ECB 40% / CTR 30% / "
-                   "CBC-decrypt 20% / CBC-encrypt 10%); one persistent launch (CUDA graph)")
+                   "CBC-decrypt 20% / CBC-encrypt 10%); one batch plan replayed as one CUDA "
+                   "graph (the stream through the single-key CTR kernel, the messages through "
+                   "the mixed-key and persistent batch kernels)")
 
 
 def run_streaming(torch, tdes, synth, stream, reps=5):
@@ -662,7 +664,8 @@ def run_streaming(torch, tdes, synth, stream, reps=5):
             "ctr_stream_alone_ms": round(ctr_ms, 3),
             "ctr_stream_alone_gbps": round(STREAM_BYTES / (ctr_ms * 1e-3) / 1e9, 3),
             "tiles": info["n_tiles"], "small_items": info["n_small_items"],
-            "cbc_encrypt_messages": info["n_cbc_enc_messages"]}
+            "cbc_encrypt_messages": info["n_cbc_enc_messages"],
+            "direct_messages": info["n_direct_messages"]}
 
 
 UNIFORM_WORKLOAD = ("the same 32 GiB buffer in place: [0, 16 GiB) the single-key CTR stream, "

@@ -194,6 +194,8 @@ typedef struct {
     uint64_t bytes_per_mode[5];  /* payload bytes, indexed by TDES_MODE_* */
     uint64_t n_mixed_tiles;      /* bitsliced tiles of small messages under up to 32 keys
                                     (batches with 8192 or more small-message blocks) */
+    uint32_t n_direct_messages;  /* messages of 64 MiB or more (ECB, CTR, out-of-place CBC
+                                    decryption) run by the single-key kernels */
 } tdes_batch_info_t;
 
 /* Key schedules (Sec. III-A) of `count` triples (keys: count x 24 bytes,
@@ -212,7 +214,10 @@ void tdes_keytable_free(tdes_keytable_t *kt);
  * Rejected descriptors are skipped; the call still returns TDES_OK with the
  * plan of the valid ones (tdes_last_error() then counts the rejections).
  * Messages are classified: CBC encryption (serial chains), large messages
- * (more than 32 blocks: bitsliced tiles) and small ones (scalar blocks). */
+ * (more than 32 blocks: bitsliced tiles) and small ones (scalar blocks).
+ * Messages of 64 MiB or more in ECB, CTR or out-of-place CBC decryption run
+ * through the single-key kernels, launched ahead of the batch kernels in
+ * the same launch (and the same CUDA graph). */
 int tdes_batch_plan(const tdes_keytable_t *kt, const tdes_desc_t *descs, uint32_t count,
                     int *per_desc_status, tdes_batch_t **out);
 

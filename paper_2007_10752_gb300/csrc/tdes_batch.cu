@@ -579,7 +579,7 @@ int validate_desc(const tdes_desc_t& d, uint32_t key_count) {
 static size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, int* status,
-                PlanHost* h) {
+                PlanHost* h, bool allow_direct) {
     std::vector<BatchMsg> msgs;
     std::vector<uint32_t> c_list, b_msg, s_list;
     std::vector<SPiece> split, pieces;
@@ -605,6 +605,11 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
             c_list.push_back(mi);
         } else if (nb <= (uint64_t)kSmallBlocks) {
             s_list.push_back(mi);
+        } else if (allow_direct && d.nbytes >= kDirectBytes &&
+                   !(d.mode == TDES_MODE_CBC_DECRYPT && d.in == d.out)) {
+            h->direct.push_back({d.mode, d.key_index, d.iv_or_ctr,
+                                 static_cast<const uint8_t*>(d.in), static_cast<uint8_t*>(d.out),
+                                 nb, 3});
         } else if (nb <= kSplitBlocks && !(d.mode == TDES_MODE_CBC_DECRYPT && d.in == d.out)) {
             for (uint32_t f = 0; f < nb; f += kSmallBlocks)
                 split.push_back({mi, f, (uint32_t)std::min<uint64_t>(kSmallBlocks, nb - f), 0u});
@@ -793,6 +798,30 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
     return cudaGetLastError();
 }
 
+cudaError_t enqueue_direct(const std::vector<DirectMsg>& direct, const tdes_keytable* kt,
+                           int device, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (const DirectMsg& m : direct) {
+        const uint32_t dir = (m.mode == TDES_MODE_ECB_DECRYPT || m.mode == TDES_MODE_CBC_DECRYPT);
+        const uint32_t* tab = kt->tabs + ((uint64_t)m.key * 2 + dir) * TDES_TABLE_WORDS;
+        const bool vec16 = ((reinterpret_cast<uintptr_t>(m.in) | reinterpret_cast<uintptr_t>(m.out)) &
+                            15u) == 0;
+        const uint64_t ntiles = (m.nblocks + kTileBlocks - 1) / kTileBlocks;
+        if (m.mode == TDES_MODE_CTR) {
+            e = launch_ctr(tab, m.stages, (uint32_t)(m.iv >> 32), (uint32_t)m.iv, m.in, m.out,
+                           m.nblocks, vec16, geometry_for(ntiles, kCtr, device), s);
+        } else if (m.mode == TDES_MODE_CBC_DECRYPT) {
+            e = launch_cbc_dec(tab, m.stages, m.iv, m.in, m.out, m.nblocks, nullptr, vec16,
+                               geometry_for(ntiles, kCbcDec, device), s);
+        } else {
+            e = launch_ecb(tab, m.stages, m.in, m.out, m.nblocks, vec16,
+                           geometry_for(ntiles, kEcb, device), s);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}
+
 }  // namespace tdes
 
 struct tdes_batch {
@@ -809,6 +838,7 @@ struct tdes_batch {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     uint64_t bytes[5];  // payload bytes per mode
+    std::vector<tdes::DirectMsg> direct;  // run by the single-key kernels
 };
 
 namespace {
@@ -846,6 +876,8 @@ int set_launch_config(tdes_batch_t* b, int warps, int ctas_per_sm) {
 }
 
 cudaError_t enqueue(tdes_batch_t* b, cudaStream_t s) {
+    cudaError_t e = tdes::enqueue_direct(b->direct, b->kt, b->device, s);
+    if (e != cudaSuccess || b->total_items == 0) return e;
     return tdes::enqueue_batch(b->params, b->total_items, b->needs_halo, b->warps, b->dyn_smem,
                                (uint64_t)b->sms * b->ctas_per_sm, s);
 }
@@ -934,7 +966,14 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
     if (dev != kt->device) return bfail(TDES_EINVAL, "key table lives on another device");
     tdes::PlanHost h;
-    tdes::build_plan(descs, count, kt->count, per_desc_status, &h);
+    tdes::build_plan(descs, count, kt->count, per_desc_status, &h, true);
+    for (tdes::DirectMsg& m : h.direct) {  // the key's DES passes, from the key table
+        uint8_t st = 3;
+        e = cudaMemcpy(&st, kt->stages + m.key, 1, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bcuda(e, "reading a key's pass count");
+        m.stages = st;
+    }
+    if (!h.direct.empty()) tdes::geometry_for(1, tdes::kEcb, dev);  // kernel set-up, outside any capture
     void* mem = nullptr;
     e = cudaMalloc(&mem, h.image.size());
     if (e != cudaSuccess) return bcuda(e, "cudaMalloc(batch plan)");
@@ -955,6 +994,7 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     b->total_items = h.total_items;
     b->needs_halo = h.needs_halo;
     memcpy(b->bytes, h.bytes_per_mode, sizeof b->bytes);
+    b->direct = h.direct;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     int rc = set_launch_config(b, tdes::kWideWarps, 0);
     if (rc != TDES_OK) {
@@ -975,14 +1015,14 @@ int tdes_batch_configure(tdes_batch_t* b, int warps_per_cta, int ctas_per_sm) {
 
 int tdes_batch_launch(tdes_batch_t* b, tdes_stream_t stream) {
     if (b == nullptr) return bfail(TDES_EINVAL, "batch is NULL");
-    if (b->total_items == 0) return TDES_OK;
+    if (b->total_items == 0 && b->direct.empty()) return TDES_OK;
     cudaError_t e = enqueue(b, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? TDES_OK : bcuda(e, "batch launch");
 }
 
 int tdes_batch_launch_graph(tdes_batch_t* b, tdes_stream_t stream) {
     if (b == nullptr) return bfail(TDES_EINVAL, "batch is NULL");
-    if (b->total_items == 0) return TDES_OK;
+    if (b->total_items == 0 && b->direct.empty()) return TDES_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     if (b->exec == nullptr) {
@@ -1016,6 +1056,7 @@ int tdes_batch_info(const tdes_batch_t* b, tdes_batch_info_t* info) {
     info->n_tiles = b->params.n_b_tiles;
     info->n_small_items = b->params.n_s_items;
     info->n_mixed_tiles = b->params.n_m_tiles;
+    info->n_direct_messages = (uint32_t)b->direct.size();
     info->warps_per_cta = b->warps;
     info->ctas_per_sm = b->ctas_per_sm;
     for (int i = 0; i < 5; ++i) info->bytes_per_mode[i] = b->bytes[i];

@@ -79,6 +79,19 @@ struct BatchParams {
 };
 
 
+// A message of at least kDirectBytes in ECB, CTR or out-of-place CBC
+// decryption: a batch plan runs it through the single-key kernels (their
+// shared-memory prefetch of each tile does not fit beside the batch kernel's
+// per-warp key table) instead of as batch tiles.
+struct DirectMsg {
+    uint32_t mode, key;
+    uint64_t iv;  // CBC: IV; CTR: first counter block
+    const uint8_t* in;
+    uint8_t* out;
+    uint64_t nblocks;
+    int stages;   // DES passes of the key (read from the key table at plan time)
+};
+
 // A batch laid out on the host as the byte image of its device buffer.
 struct PlanHost {
     std::vector<uint8_t> image;
@@ -89,12 +102,18 @@ struct PlanHost {
     bool needs_halo = false;
     uint64_t bytes_per_mode[5] = {0, 0, 0, 0, 0};
     int invalid = 0;
+    std::vector<DirectMsg> direct;  // only when the plan allows them
 };
+
+constexpr uint64_t kDirectBytes = 64ull << 20;
 
 // TDES_OK or TDES_EINVAL for one descriptor against a key table of key_count.
 int validate_desc(const tdes_desc_t& d, uint32_t key_count);
 // Validates and classifies n descriptors into `out` (status: nullable, n entries).
-void build_plan(const tdes_desc_t* d, uint32_t n, uint32_t key_count, int* status, PlanHost* out);
+// allow_direct: messages of kDirectBytes or more (not CBC encryption, not
+// in-place CBC decryption) go to out->direct instead of batch tiles.
+void build_plan(const tdes_desc_t* d, uint32_t n, uint32_t key_count, int* status, PlanHost* out,
+                bool allow_direct = false);
 // Kernel parameters of a plan whose image was copied to dev_base.
 BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt);
 // Sets the batch kernel's shared-memory limit for `warps` warps per CTA and
@@ -106,5 +125,9 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit);
 cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo, int warps,
                           size_t dyn_smem, uint64_t max_ctas, cudaStream_t s,
                           bool counter_fresh = false);
+// The single-key kernel launches of a plan's direct messages on s (before
+// its batch launches; each uses the whole GPU).
+cudaError_t enqueue_direct(const std::vector<DirectMsg>& direct, const tdes_keytable* kt,
+                           int device, cudaStream_t s);
 
 }  // namespace tdes

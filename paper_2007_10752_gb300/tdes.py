@@ -82,7 +82,7 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("n_cbc_enc_messages", ctypes.c_uint32), ("n_tiles", ctypes.c_uint64),
                 ("n_small_items", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("bytes_per_mode", ctypes.c_uint64 * 5),
-                ("n_mixed_tiles", ctypes.c_uint64)]
+                ("n_mixed_tiles", ctypes.c_uint64), ("n_direct_messages", ctypes.c_uint32)]
 
 class UniformInfo(ctypes.Structure):
     """tdes_uniform_info_t"""
@@ -402,7 +402,7 @@ class Batch:
         return {"n_cbc_enc_messages": bi.n_cbc_enc_messages, "n_tiles": bi.n_tiles,
                 "n_small_items": bi.n_small_items, "warps_per_cta": bi.warps_per_cta,
                 "ctas_per_sm": bi.ctas_per_sm, "bytes_per_mode": list(bi.bytes_per_mode),
-                "n_mixed_tiles": bi.n_mixed_tiles}
+                "n_mixed_tiles": bi.n_mixed_tiles, "n_direct_messages": bi.n_direct_messages}
 
     def free(self):
         if self.handle:

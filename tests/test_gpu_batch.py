@@ -308,3 +308,60 @@ def test_many_small_messages_share_mixed_key_tiles(cuda_lib):
         for i, (got, m) in enumerate(zip(outputs(arena, msgs), msgs)):
             want = oracle_msg(m["mode"], triples[m["key"]], m["iv"], m["data"])
             assert (got == want).all(), f"{shape} message {i}: mode {m['mode']} {m['nb']} blocks"
+
+
+def test_large_messages_run_direct(cuda_lib):
+    """Messages of 64 MiB or more (ECB both ways, CTR, out-of-place CBC
+    decryption) run through the single-key kernels inside the batch launch;
+    in-place CBC decryption and CBC encryption stay in the batch kernel.
+    Sampled windows of every large message against the oracle (a single-DES
+    triple included), every byte of the small ones, and graph replays equal
+    the plain launch."""
+    T = cuda_lib
+    seed, big = 31, 64 << 20
+    keys = synth.key_triples(seed, 4).copy()
+    keys[2, 8:16] = keys[2, 0:8]  # K1 = K2: one DES pass
+    specs = [(0, 0, big), (1, 1, big), (2, 2, big), (3, 3, big), (3, 0, big), (0, 1, 4096),
+             (2, 3, 8 * 1000), (4, 2, 8 * 300)]
+    inplace = {4}
+    ivs = synth.u64s(seed, len(specs), synth.STREAM_IV)
+    bufs, ents = [], []
+    for i, (mode, key, n) in enumerate(specs):
+        x = torch.from_numpy(synth.random_bytes(seed + i, n)).cuda()
+        y = x if i in inplace else torch.zeros_like(x)
+        iv = int(ivs[i]) & (0xFFFFFFFF00000000 if mode == 2 else 0xFFFFFFFFFFFFFFFF)
+        bufs.append((x.cpu().numpy() if i in inplace else None, x, y))
+        ents.append((mode, key, iv, x.data_ptr(), y.data_ptr(), n))
+    kt = T.KeyTable(keys)
+    b = T.Batch(kt, ents)
+    assert (b.status == 0).all()
+    assert b.info()["n_direct_messages"] == 4
+    b.launch()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    outs = []
+    for i, ((mode, key, n), (host_in, x, y)) in enumerate(zip(specs, bufs)):
+        hin = host_in if host_in is not None else x.cpu().numpy()
+        hy = y.cpu().numpy()
+        outs.append(hy.copy())
+        k, iv, nblk = keys[key].tobytes(), ents[i][2], n // 8
+        w = min(nblk, 1024)
+        for s in sorted({0, nblk - w, int(rng.integers(0, nblk - w + 1))}):
+            xs = hin[8 * s:8 * (s + w)]
+            if mode in (0, 1):
+                want = oracle.tdes_ecb(k, xs, decrypt=(mode == 1))
+            elif mode == 2:
+                want = oracle.tdes_ctr(k, iv >> 32, (iv & 0xFFFFFFFF) + s, xs)
+            elif mode == 3:
+                prev = iv if s == 0 else int.from_bytes(hin[8 * s - 8:8 * s].tobytes(), "big")
+                want = oracle.tdes_cbc_decrypt(k, prev, xs)
+            else:
+                prev = iv if s == 0 else int.from_bytes(hy[8 * s - 8:8 * s].tobytes(), "big")
+                want = oracle.tdes_cbc_encrypt(k, prev, xs)
+            assert (hy[8 * s:8 * (s + w)] == want).all(), f"message {i} mode {mode} window {s}"
+    # graph replays give the same bytes (the in-place message is restored first)
+    bufs[4][1].copy_(torch.from_numpy(bufs[4][0]).cuda())
+    b.launch_graph()
+    torch.cuda.synchronize()
+    for i, (_, x, y) in enumerate(bufs):
+        assert (y.cpu().numpy() == outs[i]).all(), f"message {i} graph replay"
