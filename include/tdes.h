@@ -132,7 +132,8 @@ int tdes_cbc_encrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out
  * library (8 bytes per tile, TDES_NOALLOC_MAX_TILES tiles = 1 MiB of device
  * memory, held on every device that loads the library until the process
  * exits); in-place calls larger than TDES_NOALLOC_MAX_BYTES return
- * TDES_EINVAL.  Out-of-place calls use no scratch and have no size limit.
+ * TDES_EINVAL.  Out-of-place calls use no scratch and have no size limit
+ * beyond the 2^31 tiles of every call.
  * The call never calls cudaMalloc, cudaFree or any allocating routine.
  * The first call on each device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

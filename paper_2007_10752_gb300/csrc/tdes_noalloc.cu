@@ -82,6 +82,8 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t* ks, uint64_t iv, const void* in, v
         return fail(TDES_EINVAL, "buffers must be device memory or pinned, mapped host memory");
     const uint64_t nblocks = nbytes / 8;
     const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+    if (nblocks / tdes::kTileBlocks >= (1ull << 31))
+        return fail(TDES_EINVAL, "a call is limited to 2^31 tiles of 8 KiB (16 TiB)");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint64_t* halo = nullptr;
     if (in == out && ntiles > 1) {
