@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 
 #include "../../include/tdes.h"
 #include "tdes_batch_internal.h"
@@ -740,6 +741,8 @@ struct UniLaunch {
 
 cudaError_t prepare(int device, UniLaunch* out) {
     static UniLaunch cache[64];
+    static std::mutex mu;  // calls from several host threads share the cache
+    std::lock_guard<std::mutex> lock(mu);
     if (device >= 0 && device < 64 && cache[device].device == device) {
         *out = cache[device];
         return cudaSuccess;
