@@ -367,9 +367,10 @@ __device__ __forceinline__ uint2 ctr_words(uint64_t c, uint32_t blk) {
     return make_uint2(bswap32u((uint32_t)(c >> 32)), bswap32u((uint32_t)c + blk));
 }
 
-// Blocks (blk0, blk1) of the lane's pair j: p.in's bytes for ECB and CBC
-// decryption (and the post-round XOR of CTR), counter blocks for CTR.
-template <bool COUNTER, bool VEC16>
+// Blocks (blk0, blk1) of the lane's pair j on the general path (any m, any
+// 8-byte alignment): p.in's bytes for ECB and CBC decryption (and the
+// post-round XOR of CTR), counter blocks for CTR.
+template <bool COUNTER>
 __device__ __forceinline__ void load_pair(const UniParams& p, uint32_t pos0, const PairSlots& q,
                                           uint2& v0, uint2& v1) {
     v0 = v1 = make_uint2(0u, 0u);
@@ -382,10 +383,6 @@ __device__ __forceinline__ void load_pair(const UniParams& p, uint32_t pos0, con
             v1 = ctr_words(c0, q.blk1);
         else if (q.slot1 < p.per_tile)
             v1 = ctr_words(p.iv[p.order[pos0 + q.slot1]], q.blk1);
-    } else if (VEC16) {  // m even: the pair is one aligned 16-byte piece of one message
-        const uint4 w = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
-        v0 = make_uint2(w.x, w.y);
-        v1 = make_uint2(w.z, w.w);
     } else {
         v0 = __ldcs(msg_in(p, mi0) + q.blk0);
         if (q.slot1 == q.slot0)
@@ -432,7 +429,7 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
             }
             if (!ok) v0 = v1 = make_uint2(0u, 0u);
         } else {
-            load_pair<KIND == kKindCtr, false>(p, pos0, q, v0, v1);
+            load_pair<KIND == kKindCtr>(p, pos0, q, v0, v1);
         }
         A0[2 * j] = v0.x;
         A1[2 * j] = v0.y;
@@ -454,7 +451,7 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
                 v1 = make_uint2(w.z, w.w);
                 if (!ok) v0 = v1 = make_uint2(0u, 0u);
             } else if (KIND == kKindCtr) {
-                load_pair<false, false>(p, pos0, q, v0, v1);
+                load_pair<false>(p, pos0, q, v0, v1);
             } else if (q.slot0 < p.per_tile) {
                 const uint32_t mi0 = p.order[pos0 + q.slot0];
                 v0 = cbc_prev(p, mi0, q.blk0);
