@@ -58,13 +58,12 @@ def expected_plan(key_index, mode, n_keys, m):
     single-key tiles of 1024 // m messages (1024 chains for CBC encryption),
     and slices of 32 // m messages (32 chains) for the rest."""
     counts = np.bincount(mode.astype(np.int64) * n_keys + key_index, minlength=5 * n_keys)
-    plan = {"key_tiles": 0, "mixed_slices": 0, "chain_key_tiles": 0, "chain_slices": 0}
-    for g, c in enumerate(counts):
-        chain = g >= 4 * n_keys
-        per_tile, per_slice = (1024, 32) if chain else (1024 // m, 32 // m)
-        u, r = divmod(int(c), per_tile)
-        plan["chain_key_tiles" if chain else "key_tiles"] += u
-        plan["chain_slices" if chain else "mixed_slices"] += -(-r // per_slice)
+    plan = {}
+    for name, c, per_tile, per_slice in (("", counts[:4 * n_keys], 1024 // m, 32 // m),
+                                         ("chain_", counts[4 * n_keys:], 1024, 32)):
+        u, r = np.divmod(c, per_tile)
+        plan[name + "key_tiles"] = int(u.sum())
+        plan[(name + "slices") if name else "mixed_slices"] = int((-(-r // per_slice)).sum())
     return plan
 
 
@@ -148,6 +147,26 @@ def test_uniform_one_key_skewed(cuda_lib):
         assert (g[sel] == want).all(), f"mode {md}"
     for i in np.nonzero(mode >= 2)[0]:
         assert (g[i] == oracle_msg(int(mode[i]), k, int(iv[i]), d[i])).all(), i
+
+
+def test_uniform_million_keys(cuda_lib):
+    """A key table of 2^20 triples: 5 x 2^20 groups, so the planner's scan of
+    block sums runs over more than one CTA-wide chunk; every message against
+    the oracle."""
+    import os
+    n, mb, n_keys, seed = 20000, 64, 1 << 20, 9700
+    keys, key_index, mode, iv, data = make_case(seed, n, mb, n_keys)
+    kt = cuda_lib.KeyTable(keys)
+    got, skipped, info = run(cuda_lib, kt, key_index, mode, iv, data, mb, False)
+    assert skipped == 0
+    assert {k: info[k] for k in expected_plan(key_index, mode, n_keys, mb // 8)} == \
+        expected_plan(key_index, mode, n_keys, mb // 8)
+    want = oracle.tdes_messages(keys, key_index, mode, iv, mb * np.arange(n, dtype=np.uint64),
+                                np.full(n, mb // 8, dtype=np.uint64), data,
+                                max(1, min(64, os.cpu_count() or 1)))
+    assert (got == want).all()
+    del kt
+    torch.cuda.empty_cache()
 
 
 def test_uniform_single_message_and_empty(cuda_lib):
