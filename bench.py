@@ -745,7 +745,8 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
                        "requests": r["requests"], "batches": r["batches"],
                        "duration_s": round(r["duration_s"], 3)})
     # host payloads: request buffers in pinned host memory, read and written by
-    # the kernels over the host link (no staging copies)
+    # the kernels over the host link (the server's default; its optional device
+    # staging measured lower closed-loop throughput)
     host_in = in_pool[: 1 << 30].cpu().pin_memory()
     host_out = torch.empty(2 << 30, dtype=torch.uint8).pin_memory()
     hpeak = srv.loadtest(host_in, host_out, n_peak, 0.0, seed=7)

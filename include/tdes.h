@@ -307,6 +307,15 @@ typedef struct {
     int warps_per_cta;       /* persistent-kernel shape, 1..8 */
     int reserve_ctas_per_sm; /* with slots > 1: CTAs per SM a batch leaves for the next one */
     uint32_t ring_entries;   /* completion records kept; older tickets read as complete */
+    uint64_t stage_bytes;    /* device staging per slot for requests in host memory (default
+                                0: none).  A request whose buffers are pinned host memory and
+                                that has at least stage_min_bytes is copied in, processed and
+                                copied out on its batch's stream, so the copies of one batch
+                                overlap the kernels of the others; smaller ones, and any that
+                                do not fit the slot's staging, are read and written by the
+                                kernels over the host link (which gave the higher closed-loop
+                                throughput on a GB300) */
+    uint64_t stage_min_bytes;
 } tdes_server_config_t;
 
 /* Defaults: 8 GiB budget, 4 slots, 16384 requests per batch, 4 warps per CTA,

@@ -24,6 +24,8 @@ void set_last_error(const char* msg);
 // (what cudaHostAlloc gives on a unified-address system).  Pageable host
 // memory is refused: a kernel access to it could fault.
 bool gpu_addressable(const void* p);
+// True for page-locked host memory (whether or not it is mapped).
+bool host_memory(const void* p);
 
 constexpr int kTileBlocks = 1024;  // blocks per warp tile: 32 lanes x 32 blocks
 constexpr int kWideWarps = 8;      // warps per CTA for large inputs

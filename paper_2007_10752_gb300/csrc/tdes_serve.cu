@@ -63,12 +63,21 @@ struct Slot {
     std::vector<uint64_t> tickets;
     uint64_t cost = 0;
     bool busy = false;
+    uint8_t* stage = nullptr;  // device staging for requests in host memory
+    size_t stage_cap = 0;
 };
 
 struct Pending {
     tdes_desc_t d;
     uint64_t ticket;
     uint64_t cost;
+    bool stage;  // host buffers, large enough to be staged through the device
+};
+
+struct StagedCopy {
+    void* dst;
+    const void* src;
+    size_t n;
 };
 
 struct Completion {
@@ -97,6 +106,11 @@ struct tdes_server {
     std::atomic<uint64_t> batches{0}, completed{0};
     std::atomic<int> sticky_error{0};
     uint64_t admitted = 0;  // dispatcher thread only
+
+    bool wants_stage(const tdes_desc_t& d) const {
+        return cfg.stage_bytes && d.nbytes >= cfg.stage_min_bytes && d.nbytes <= cfg.stage_bytes &&
+               tdes::host_memory(d.in) && tdes::host_memory(d.out);
+    }
 
     void complete(uint64_t ticket, int status, int64_t t) {
         Completion& c = ring[ticket % ring.size()];
@@ -132,6 +146,7 @@ struct tdes_server {
         cudaSetDevice(device);
         std::vector<Pending> take;
         std::vector<tdes_desc_t> descs;
+        std::vector<StagedCopy> copy_in, copy_out;
         tdes::PlanHost plan;
         const uint64_t reserve = cfg.slots > 1 ? (uint64_t)std::max(0, cfg.reserve_ctas_per_sm) : 0;
         const uint64_t per_sm = std::max<uint64_t>(1, (uint64_t)ctas_fit > reserve
@@ -170,10 +185,27 @@ struct tdes_server {
                 }
                 if (take.empty()) break;
                 descs.resize(take.size());
-                for (size_t i = 0; i < take.size(); ++i) descs[i] = take[i].d;
+                copy_in.clear();
+                copy_out.clear();
+                size_t staged = 0;
+                for (size_t i = 0; i < take.size(); ++i) {
+                    descs[i] = take[i].d;
+                    const size_t n = (size_t)take[i].d.nbytes;
+                    if (!take[i].stage || staged + n > sl.stage_cap) continue;
+                    // processed in place in the slot's staging, copied in and out
+                    uint8_t* dev = sl.stage + staged;
+                    copy_in.push_back({dev, take[i].d.in, n});
+                    copy_out.push_back({take[i].d.out, dev, n});
+                    descs[i].in = dev;
+                    descs[i].out = dev;
+                    staged += (n + 255) & ~(size_t)255;
+                }
                 tdes::build_plan(descs.data(), (uint32_t)descs.size(), kt->count, nullptr, &plan);
                 cudaError_t e = cudaSuccess;
                 if (!ensure_capacity(sl, plan.image.size())) e = cudaErrorMemoryAllocation;
+                for (const StagedCopy& c : copy_in)
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyHostToDevice, sl.stream);
                 if (e == cudaSuccess) {
                     memcpy(sl.pinned, plan.image.data(), plan.image.size());
                     e = cudaMemcpyAsync(sl.dmem, sl.pinned, plan.image.size(),
@@ -184,6 +216,9 @@ struct tdes_server {
                     e = tdes::enqueue_batch(p, plan.total_items, plan.needs_halo,
                                             cfg.warps_per_cta, dyn_smem, max_ctas, sl.stream, true);
                 }
+                for (const StagedCopy& c : copy_out)
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, sl.stream);
                 if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
                 if (e != cudaSuccess) {
                     sticky_error.store(TDES_ECUDA);
@@ -219,6 +254,8 @@ void tdes_server_config_default(tdes_server_config_t* cfg) {
     cfg->warps_per_cta = 4;
     cfg->reserve_ctas_per_sm = 1;
     cfg->ring_entries = 1u << 21;
+    cfg->stage_bytes = 0;  // host payloads zero-copy by default: measured faster
+    cfg->stage_min_bytes = 64ull << 10;
 }
 
 int tdes_server_create(const tdes_keytable_t* kt, const tdes_server_config_t* cfg_in,
@@ -247,6 +284,10 @@ int tdes_server_create(const tdes_keytable_t* kt, const tdes_server_config_t* cf
     for (Slot& sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess && cfg.stage_bytes) {
+            e = cudaMalloc(reinterpret_cast<void**>(&sl.stage), cfg.stage_bytes);
+            if (e == cudaSuccess) sl.stage_cap = cfg.stage_bytes;
+        }
     }
     if (e != cudaSuccess) {
         int rc = scuda(e, "server set-up");
@@ -277,7 +318,7 @@ int tdes_server_submit(tdes_server_t* s, const tdes_desc_t* req, uint64_t* ticke
         s->complete(t, TDES_OK, now_ns());
         return TDES_OK;
     }
-    s->queue.push_back({*req, t, cost});
+    s->queue.push_back({*req, t, cost, s->wants_stage(*req)});
     return TDES_OK;
 }
 
@@ -323,7 +364,7 @@ int tdes_server_submit_group(tdes_server_t* s, const tdes_desc_t* reqs, uint32_t
         if (reqs[i].nbytes == 0)
             s->complete(t0 + i, TDES_OK, now_ns());
         else
-            s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i])});
+            s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i]), s->wants_stage(reqs[i])});
     }
     return TDES_OK;
 }
@@ -364,6 +405,7 @@ void tdes_server_destroy(tdes_server_t* s) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.dmem) cudaFree(sl.dmem);
         if (sl.pinned) cudaFreeHost(sl.pinned);
+        if (sl.stage) cudaFree(sl.stage);
     }
     delete s;
 }

@@ -147,13 +147,16 @@ def test_loadtest_reports(cuda_lib):
     srv.close()
 
 
-def test_server_host_payloads(cuda_lib):
-    """Requests whose buffers are pinned host memory (the kernels work on them
-    over the host link); pageable host buffers are refused at submit."""
+@pytest.mark.parametrize("staged", [False, True], ids=["zero_copy", "staged"])
+def test_server_host_payloads(cuda_lib, staged):
+    """Requests whose buffers are pinned host memory: the kernels work on them
+    over the host link, or (staged) the large ones are copied through the
+    slot's device staging and processed there; pageable host buffers are
+    refused at submit."""
     T = cuda_lib
     keys = synth.key_triples(25, 16)
     kt = T.KeyTable(keys)
-    srv = T.Server(kt)
+    srv = T.Server(kt, stage_bytes=(1 << 20) if staged else 0, stage_min_bytes=64 << 10)
     reqs = _requests(25, 120, 16, big_every=40)
     ins = [torch.from_numpy(r["data"]).pin_memory() for r in reqs]
     outs = [torch.empty_like(x).pin_memory() for x in ins]
