@@ -256,7 +256,9 @@ void tdes_batch_free(tdes_batch_t *b);
 #define TDES_UNIFORM_MAX_MSGS (1ull << 31)
 
 /* Device scratch the call needs for n_msgs messages of msg_bytes under the
- * key table kt (about 4 bytes per message plus 20 bytes per key).
+ * key table kt: 4 to 8 bytes per message (more for longer messages, whose
+ * slices hold fewer messages) plus about 100 bytes per key triple (1.3 GB for
+ * 2^28 messages of 64 bytes under 65536 triples).
  * TDES_EINVAL for a msg_bytes that is not a multiple of 8 in [8, 256] or
  * n_msgs > TDES_UNIFORM_MAX_MSGS. */
 int tdes_uniform_scratch_bytes(const tdes_keytable_t *kt, uint64_t n_msgs, uint64_t msg_bytes,
