@@ -42,7 +42,9 @@ namespace {
 
 constexpr int kUniWarps = 8;                            // warps per CTA of the work kernels
 constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per warp
-constexpr int kChainWarpBytes = kUniTableBytes + 32 * 32 * 4;  // + the chains' message indices
+// CBC-encryption chains: a warp's table, its 1024 chains' message indices and
+// one held block per chain (25 KB; 8 warps per SM)
+constexpr int kChainWarpBytes = kUniTableBytes + 32 * 32 * 4 + 32 * 32 * 8;
 constexpr int kScanThreads = 1024;
 constexpr uint32_t kChainsPerTile = kTileBlocks;       // class 2: one chain per tile slot
 constexpr uint32_t kModes = 5;                         // groups per key: one per TDES_MODE_*
@@ -487,53 +489,102 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
     }
 }
 
+// The block passes of 1024 CBC-encryption chains: widx[32 s + lane] is the
+// message of the chain in bit plane word s (~0u: none).  After a pass the
+// planes are back in block order, so A holds C_i and the next pass starts
+// from A ^ P_{i+1}: only the plaintext is read.  When messages are 16-byte
+// aligned, passes go in pairs: one 16-byte load brings P_i and P_{i+1}, the
+// held block keeps P_{i+1} and then C_i, and one 16-byte store writes
+// C_i, C_{i+1}.  A sector is then read and written half as often (64-byte
+// messages: 2^28 of them under 65536 keys, 69.1 -> 66.2 ms per call; 2^22
+// CBC encryptions under two keys, 2.15 -> 1.59 ms).
+template <bool MIXED>
+__device__ __forceinline__ void uni_chain_passes(const UniParams& p, uint32_t (&A0)[32],
+                                                 uint32_t (&A1)[32], const uint32_t* __restrict__ tab,
+                                                 const uint32_t* widx, uint2* held, uint32_t lane,
+                                                 bool one_pass) {
+    const bool pair = p.m % 2u == 0u && (((uintptr_t)p.in | (uintptr_t)p.out) & 15u) == 0u;
+    for (uint32_t i = 0; i < p.m; ++i) {
+        const bool odd = (i & 1u) != 0u;
+        if (!pair) {
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const uint32_t mi = widx[32 * s + lane];
+                if (mi != ~0u) {
+                    const uint2 x = __ldcs(msg_in(p, mi) + i);
+                    A0[s] ^= x.x;
+                    A1[s] ^= x.y;
+                }
+            }
+        } else if (!odd) {
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const uint32_t mi = widx[32 * s + lane];
+                uint4 x = make_uint4(0u, 0u, 0u, 0u);
+                if (mi != ~0u) x = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi) + i));
+                A0[s] ^= x.x;
+                A1[s] ^= x.y;
+                held[32 * s + lane] = make_uint2(x.z, x.w);
+            }
+        }
+        tdes_process32_compact<MIXED>(A0, A1, tab, one_pass);
+        if (!pair) {
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const uint32_t mi = widx[32 * s + lane];
+                if (mi != ~0u) msg_out(p, mi)[i] = make_uint2(A0[s], A1[s]);
+            }
+        } else if (!odd) {  // hold C_i, start pass i + 1 from C_i ^ P_{i+1}
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const uint2 x = held[32 * s + lane];
+                held[32 * s + lane] = make_uint2(A0[s], A1[s]);
+                A0[s] ^= x.x;
+                A1[s] ^= x.y;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const uint32_t mi = widx[32 * s + lane];
+                const uint2 c = held[32 * s + lane];
+                if (mi != ~0u)
+                    *reinterpret_cast<uint4*>(msg_out(p, mi) + i - 1) = make_uint4(c.x, c.y, A0[s], A1[s]);
+            }
+        }
+    }
+    __syncwarp();  // widx and held are rewritten by the next tile
+}
+
 // One single-key tile of 1024 CBC-encryption chains (chain k = 64 j + 2 lane
-// + h), one bitsliced pass per block position.  After a pass the planes are
-// back in block order, so A holds C_i, and the next pass starts from
-// A ^ P_{i+1}: only the plaintext is read.
-__device__ __forceinline__ void uni_chain_tile(const UniParams& p, uint32_t t,
-                                               const uint32_t* __restrict__ tab, uint32_t lane,
-                                               bool one_pass) {
+// + h sits in plane word 2 j + h).  wsm holds the warp's table, then room for
+// the chains' message indices and held blocks.
+__device__ __forceinline__ void uni_chain_tile(const UniParams& p, uint32_t t, uint32_t* wsm,
+                                               uint32_t lane, bool one_pass) {
+    uint32_t* widx = wsm + TDES_TABLE_WORDS;
     uint32_t A0[32], A1[32];
-    uint32_t pos0 = tile_pos0(p, t);
+    const uint32_t pos0 = tile_pos0(p, t);
 #pragma unroll
     for (int j = 0; j < 16; ++j)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t mi = p.order[pos0 + 64u * j + 2u * lane + h];
+            widx[32 * (2 * j + h) + lane] = mi;
             const uint2 c = iv_words(p.iv[mi]);
             A0[2 * j + h] = c.x;
             A1[2 * j + h] = c.y;
         }
-    for (uint32_t i = 0; i < p.m; ++i) {
-        pos0 = tile_pos0(p, t);
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint2 x = __ldcs(msg_in(p, p.order[pos0 + 64u * j + 2u * lane + h]) + i);
-                A0[2 * j + h] ^= x.x;
-                A1[2 * j + h] ^= x.y;
-            }
-        tdes_process32_compact<false>(A0, A1, tab, one_pass);
-        pos0 = tile_pos0(p, t);
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t mi = p.order[pos0 + 64u * j + 2u * lane + h];
-                msg_out(p, mi)[i] = make_uint2(A0[2 * j + h], A1[2 * j + h]);
-            }
-    }
+    uni_chain_passes<false>(p, A0, A1, wsm, widx, reinterpret_cast<uint2*>(widx + 32 * 32), lane,
+                            one_pass);
 }
 
 // Single-key tiles of one kind, split evenly into one contiguous run per
 // warp: a group's tiles are consecutive, so a warp stages each table once
 // per run.
 template <int KIND, bool VEC16>
-__global__ void __launch_bounds__(32 * kUniWarps, 2) uni_tile_kernel(UniParams p) {
+__global__ void __launch_bounds__(32 * kUniWarps, KIND == kKindCbcEnc ? 1 : 2) uni_tile_kernel(UniParams p) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint32_t* wtab = reinterpret_cast<uint32_t*>(uni_smem + (size_t)warp * kUniTableBytes);
+    uint32_t* wtab = reinterpret_cast<uint32_t*>(
+        uni_smem + (size_t)warp * (KIND == kKindCbcEnc ? kChainWarpBytes : kUniTableBytes));
     const uint32_t first = p.hdr->kind_tiles[KIND];
     const uint32_t n = p.hdr->kind_tiles[KIND + 1] - first;
     const uint32_t W = gridDim.x * kUniWarps, w = blockIdx.x * kUniWarps + warp;
@@ -596,9 +647,7 @@ __global__ void __launch_bounds__(32 * kUniWarps, CHAIN ? 1 : 2) uni_mixed_kerne
             __syncwarp();
         }
         if (CHAIN) {
-            // lane l walks chain l of every slice; A carries C_i from pass to
-            // pass.  The chains' message indices are kept in shared memory
-            // (~0u: no chain) for all passes.
+            // lane l walks chain l of every slice
             uint32_t* widx = wtab + TDES_TABLE_WORDS;
             uint32_t A0[32], A1[32];
 #pragma unroll
@@ -615,24 +664,8 @@ __global__ void __launch_bounds__(32 * kUniWarps, CHAIN ? 1 : 2) uni_mixed_kerne
                 A0[s] = c.x;
                 A1[s] = c.y;
             }
-            for (uint32_t i = 0; i < p.m; ++i) {
-#pragma unroll
-                for (int s = 0; s < 32; ++s) {
-                    const uint32_t mi = widx[32 * s + lane];
-                    if (mi != ~0u) {
-                        const uint2 x = __ldcs(msg_in(p, mi) + i);
-                        A0[s] ^= x.x;
-                        A1[s] ^= x.y;
-                    }
-                }
-                tdes_process32_compact<true>(A0, A1, wtab, false);
-#pragma unroll
-                for (int s = 0; s < 32; ++s) {
-                    const uint32_t mi = widx[32 * s + lane];
-                    if (mi != ~0u) msg_out(p, mi)[i] = make_uint2(A0[s], A1[s]);
-                }
-            }
-            __syncwarp();  // widx is rewritten by the next tile
+            uni_chain_passes<true>(p, A0, A1, wtab, widx, reinterpret_cast<uint2*>(widx + 32 * 32),
+                                   lane, false);
         } else {
             // lane l holds block l % m of the slice's message l / m
             const uint32_t slot = (lane * p.magic) >> 16, blk = lane - slot * p.m;
@@ -752,13 +785,12 @@ cudaError_t prepare(int device, UniLaunch* out) {
         (const void*)uni_tile_kernel<kKindEcb, false>, (const void*)uni_tile_kernel<kKindEcb, true>,
         (const void*)uni_tile_kernel<kKindCtr, false>, (const void*)uni_tile_kernel<kKindCtr, true>,
         (const void*)uni_tile_kernel<kKindCbcDec, false>,
-        (const void*)uni_tile_kernel<kKindCbcDec, true>,
-        (const void*)uni_tile_kernel<kKindCbcEnc, false>};
+        (const void*)uni_tile_kernel<kKindCbcDec, true>};
     for (const void* f : fns)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(uni_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kUniWarps * kChainWarpBytes);
+    for (const void* f : {(const void*)uni_tile_kernel<kKindCbcEnc, false>, (const void*)uni_mixed_kernel<true>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kUniWarps * kChainWarpBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(uni_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     int fit = 0;
@@ -888,11 +920,12 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
         }
         uni_mixed_kernel<false><<<g, b, dyn, s>>>(p);
         // CBC-encryption chains: one CTA per SM, each warp with room for its
-        // chains' message indices (2^28 messages of 64 B: 75.2 -> 73.1 ms,
-        // alternating A/B runs).
+        // chains' message indices and held blocks (2^28 messages of 64 B:
+        // 75.2 -> 73.1 ms with the indices, alternating A/B runs).
         const dim3 g1(geo.sms);
-        uni_tile_kernel<kKindCbcEnc, false><<<g1, b, dyn, s>>>(p);
-        uni_mixed_kernel<true><<<g1, b, (size_t)kUniWarps * kChainWarpBytes, s>>>(p);
+        const size_t dyn_chain = (size_t)kUniWarps * kChainWarpBytes;
+        uni_tile_kernel<kKindCbcEnc, false><<<g1, b, dyn_chain, s>>>(p);
+        uni_mixed_kernel<true><<<g1, b, dyn_chain, s>>>(p);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && skipped != nullptr) {
