@@ -126,6 +126,39 @@ def test_uniform_cbc_encrypt_key_tiles(cuda_lib, msg_bytes):
         assert info["key_tiles"] == 0 and info["mixed_slices"] == 0
 
 
+@pytest.mark.parametrize("msg_bytes,n_keys,mix", [
+    (64, 2, (0, 0, 0, 0, 1.0)),  # 1024-chain single-key tiles and chain slices
+    (64, 300, MIX5),             # mixed-key slices of every mode
+    (16, 3, MIX5),
+], ids=["cbc_enc_key_tiles", "mixed_keys", "two_blocks"])
+def test_uniform_8_byte_aligned_buffers(cuda_lib, msg_bytes, n_keys, mix):
+    """Buffers 8 bytes past a 16-byte boundary: messages of an even number of
+    blocks then take the 8-byte loads and stores (CBC-encryption chains one
+    block per pass; block tiles without the 16-byte path)."""
+    n, seed = 2600, 9150 + msg_bytes + n_keys
+    keys, key_index, mode, iv, data = make_case(seed, n, msg_bytes, n_keys, mix=mix)
+    kt = cuda_lib.KeyTable(keys)
+    want = expected(keys, key_index, mode, iv, data, msg_bytes)
+    k = torch.from_numpy(key_index.view(np.int32)).cuda()
+    md = torch.from_numpy(mode).cuda()
+    v = torch.from_numpy(iv.view(np.int64)).cuda()
+    for in_place in (False, True):
+        xb = torch.zeros(n * msg_bytes + 32, dtype=torch.uint8, device="cuda")
+        x = xb[8 + (-xb.data_ptr()) % 16:][:n * msg_bytes]
+        assert x.data_ptr() % 16 == 8
+        x.copy_(torch.from_numpy(data))
+        if in_place:
+            y = x
+        else:
+            yb = torch.zeros_like(xb)
+            y = yb[8 + (-yb.data_ptr()) % 16:][:n * msg_bytes]
+        cuda_lib.tdes_uniform_crypt(kt, k, md, v, x, y, msg_bytes)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy()
+        bad = np.nonzero((got != want).reshape(n, msg_bytes).any(axis=1))[0]
+        assert bad.size == 0, f"{bad.size} messages differ, first {bad[:5]} (modes {mode[bad[:5]]})"
+
+
 def test_uniform_one_key_skewed(cuda_lib):
     """Every message under one key: a handful of large groups (the planner's
     per-group atomics are shared per warp), CBC-encryption key tiles of 1024
