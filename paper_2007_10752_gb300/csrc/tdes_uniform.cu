@@ -441,11 +441,27 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
     tdes_process32_compact<false>(A0, A1, tab, one_pass);
     pos0 = tile_pos0(p, t);  // reloaded: nothing but the planes stays live across the rounds
     if (KIND == kKindCtr || KIND == kKindCbcDec) {
+        uint2 carry = make_uint2(0u, 0u);  // CBC decryption: lane 31's second block of pair j - 1
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const PairSlots q = pair_slots(p, 64u * j + 2u * lane);
             uint2 v0 = make_uint2(0u, 0u), v1 = make_uint2(0u, 0u);
-            if (VEC16 && KIND == kKindCtr) {
+            if (VEC16 && KIND == kKindCbcDec) {
+                // The lane's own 16 bytes are C_b0 (v1's operand) and C_b0+1;
+                // C_b0-1 is the second block of the pair before, one lane
+                // down (lane 0: lane 31 of pair j - 1), in the same message
+                // unless b0 = 0, where the IV stands in.
+                const bool ok = q.slot0 < p.per_tile;
+                const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
+                const uint4 w = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
+                uint2 up = make_uint2(__shfl_up_sync(0xFFFFFFFFu, w.z, 1),
+                                      __shfl_up_sync(0xFFFFFFFFu, w.w, 1));
+                if (lane == 0) up = carry;
+                carry = make_uint2(__shfl_sync(0xFFFFFFFFu, w.z, 31), __shfl_sync(0xFFFFFFFFu, w.w, 31));
+                v0 = q.blk0 == 0u ? iv_words(p.iv[mi0]) : up;
+                v1 = make_uint2(w.x, w.y);
+                if (!ok) v0 = v1 = make_uint2(0u, 0u);
+            } else if (VEC16 && KIND == kKindCtr) {
                 const bool ok = q.slot0 < p.per_tile;
                 const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
                 const uint4 w = __ldcs(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
