@@ -114,10 +114,11 @@ def test_uniform_parity(cuda_lib, msg_bytes, n, n_keys, in_place):
 
 @pytest.mark.parametrize("msg_bytes", [8, 64, 136])
 def test_uniform_cbc_encrypt_key_tiles(cuda_lib, msg_bytes):
-    """CBC encryption only, two keys: 1024-chain single-key tiles plus chain slices."""
+    """CBC encryption only, two keys (key 0 reduces to single DES: the one-pass
+    table): 1024-chain single-key tiles plus chain slices."""
     n, n_keys, seed = 2600, 2, 9100 + msg_bytes
     keys, key_index, mode, iv, data = make_case(seed, n, msg_bytes, n_keys,
-                                                mix=(0, 0, 0, 0, 1.0))
+                                                mix=(0, 0, 0, 0, 1.0), reducing_key0=True)
     kt = cuda_lib.KeyTable(keys)
     for in_place in (False, True):
         got, skipped, info = run(cuda_lib, kt, key_index, mode, iv, data, msg_bytes, in_place)
