@@ -41,6 +41,7 @@ namespace tdes {
 namespace {
 
 constexpr int kUniWarps = 8;                            // warps per CTA of the work kernels
+constexpr int kKeyChainWarps = 9;                       // single-key CBC-encryption tiles: 9 x 25 KB
 constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per warp
 // CBC-encryption chains: a warp's table, its 1024 chains' message indices and
 // one held block per chain (25 KB; 8 warps per SM)
@@ -597,13 +598,15 @@ __device__ __forceinline__ void uni_chain_tile(const UniParams& p, uint32_t t, u
 // warp: a group's tiles are consecutive, so a warp stages each table once
 // per run.
 template <int KIND, bool VEC16>
-__global__ void __launch_bounds__(32 * kUniWarps, KIND == kKindCbcEnc ? 1 : 2) uni_tile_kernel(UniParams p) {
+__global__ void __launch_bounds__(KIND == kKindCbcEnc ? 32 * kKeyChainWarps : 32 * kUniWarps,
+                                  KIND == kKindCbcEnc ? 1 : 2) uni_tile_kernel(UniParams p) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t* wtab = reinterpret_cast<uint32_t*>(
         uni_smem + (size_t)warp * (KIND == kKindCbcEnc ? kChainWarpBytes : kUniTableBytes));
     const uint32_t first = p.hdr->kind_tiles[KIND];
     const uint32_t n = p.hdr->kind_tiles[KIND + 1] - first;
-    const uint32_t W = gridDim.x * kUniWarps, w = blockIdx.x * kUniWarps + warp;
+    const uint32_t nw = blockDim.x >> 5;
+    const uint32_t W = gridDim.x * nw, w = blockIdx.x * nw + warp;
     const uint32_t per = n / W, extra = n % W;
     const uint32_t a = w * per + min(w, extra), b = a + per + (w < extra ? 1u : 0u);
     uint32_t staged = ~0u;
@@ -804,9 +807,12 @@ cudaError_t prepare(int device, UniLaunch* out) {
         (const void*)uni_tile_kernel<kKindCbcDec, true>};
     for (const void* f : fns)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    for (const void* f : {(const void*)uni_tile_kernel<kKindCbcEnc, false>, (const void*)uni_mixed_kernel<true>})
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kUniWarps * kChainWarpBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(uni_tile_kernel<kKindCbcEnc, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kKeyChainWarps * kChainWarpBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(uni_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kUniWarps * kChainWarpBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(uni_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     int fit = 0;
@@ -937,11 +943,13 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
         uni_mixed_kernel<false><<<g, b, dyn, s>>>(p);
         // CBC-encryption chains: one CTA per SM, each warp with room for its
         // chains' message indices and held blocks (2^28 messages of 64 B:
-        // 75.2 -> 73.1 ms with the indices, alternating A/B runs).
+        // 75.2 -> 73.1 ms with the indices, alternating A/B runs).  Nine
+        // warps fit; they took 2^22 single-key chains of 64 B from 1.60 to
+        // 1.52 ms, and left the mixed-key chains unchanged.
         const dim3 g1(geo.sms);
-        const size_t dyn_chain = (size_t)kUniWarps * kChainWarpBytes;
-        uni_tile_kernel<kKindCbcEnc, false><<<g1, b, dyn_chain, s>>>(p);
-        uni_mixed_kernel<true><<<g1, b, dyn_chain, s>>>(p);
+        uni_tile_kernel<kKindCbcEnc, false><<<g1, dim3(32 * kKeyChainWarps),
+                                              (size_t)kKeyChainWarps * kChainWarpBytes, s>>>(p);
+        uni_mixed_kernel<true><<<g1, b, (size_t)kUniWarps * kChainWarpBytes, s>>>(p);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && skipped != nullptr) {
