@@ -44,7 +44,8 @@ constexpr int kUniWarps = 8;                            // warps per CTA of the 
 constexpr int kKeyChainWarps = 9;                       // single-key CBC-encryption tiles: 9 x 25 KB
 constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per warp
 // CBC-encryption chains: a warp's table, its 1024 chains' message indices and
-// one held block per chain (25 KB; 8 warps per SM)
+// one held block per chain (25 KB; one CTA per SM of 8 warps for mixed-key
+// chains, 9 for single-key tiles)
 constexpr int kChainWarpBytes = kUniTableBytes + 32 * 32 * 4 + 32 * 32 * 8;
 constexpr int kScanThreads = 1024;
 constexpr uint32_t kChainsPerTile = kTileBlocks;       // class 2: one chain per tile slot
