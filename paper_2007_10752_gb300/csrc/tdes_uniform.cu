@@ -48,7 +48,7 @@ constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per 
 // chains, 9 for single-key tiles)
 constexpr int kChainWarpBytes = kUniTableBytes + 32 * 32 * 4 + 32 * 32 * 8;
 constexpr int kScanThreads = 1024;
-constexpr uint32_t kChainsPerTile = kTileBlocks;       // class 2: one chain per tile slot
+constexpr uint32_t kChainsPerTile = kTileBlocks;       // CBC encryption: one chain per tile slot
 constexpr uint32_t kModes = 5;                         // groups per key: one per TDES_MODE_*
 constexpr uint32_t kMaxKeys = 1u << 26;                // 5 groups per key fit 32-bit indices
 
