@@ -88,6 +88,7 @@ CASES = [
     (64, 3000, 700),
     (8, 12000, 2),
     (24, 6000, 3),
+    (16, 6000, 2),  # two blocks: one pair of chain passes per message
     (200, 1500, 4),
     (256, 1200, 3),
 ]
