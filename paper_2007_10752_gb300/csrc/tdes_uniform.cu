@@ -47,6 +47,12 @@ constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per 
 // one held block per chain (25 KB; one CTA per SM of 8 warps for mixed-key
 // chains, 9 for single-key tiles)
 constexpr int kChainWarpBytes = kUniTableBytes + 32 * 32 * 4 + 32 * 32 * 8;
+// sm_103a shared memory: 228 KB per SM, 1 KB of it reserved per resident CTA,
+// so a CTA may take at most 227 KB
+constexpr int kSmemPerSm = 228 * 1024, kSmemReservedPerCta = 1024;
+static_assert(kKeyChainWarps * kChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm, "single-key chain CTA");
+static_assert(kUniWarps * kChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm, "mixed-key chain CTA");
+static_assert(2 * (kUniWarps * kUniTableBytes + kSmemReservedPerCta) <= kSmemPerSm, "two tile CTAs per SM");
 constexpr int kScanThreads = 1024;
 constexpr uint32_t kChainsPerTile = kTileBlocks;       // CBC encryption: one chain per tile slot
 constexpr uint32_t kModes = 5;                         // groups per key: one per TDES_MODE_*
