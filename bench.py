@@ -464,9 +464,6 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
-        "batched": batched,
-        "serving": serving,
-        "large_streaming": streaming,
         "paper_design_context": paper_ctx,
         "extra": {"kernel_ms_per_launch": round(per_launch_ms, 4),
                   "ecb_decrypt_gbs": round(NBYTES / (dec_ms * 1e-3) / 1e9, 3),
@@ -493,9 +490,39 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(keys)
         line["cpu_library_reference"] = openssl_reference(keys, host, ecb_out)
+    line["batched"] = batched
+    line["serving"] = serving
+    line["large_streaming"] = streaming
+    line["summary"] = summary(line)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def summary(line: dict) -> dict:
+    """The headline figures of every workload in a few hundred bytes, printed
+    last so that a truncated copy of the line still carries them."""
+    out = {"ecb_1gib_gbs": line["value"], "roofline_frac": line["roofline"]["frac"],
+           "e2e_gbs": round(line["e2e"]["value"], 1) if line.get("e2e") else None}
+    b = line.get("batched")
+    if b:
+        out["batched"] = {"parallel_gbs": b["parallel_modes_gbs"],
+                          "vs_ecb": b["parallel_modes_vs_plain_ecb"],
+                          "makespan_ms": b["makespan_ms"],
+                          "tuned_gain": b["autotune"]["gain"]}
+    sv = line.get("serving")
+    if sv:
+        out["serving"] = {"peak_gbs": sv["peak_closed_loop_gbs"],
+                          "p50_p99_ms": {str(p["load"]): [p["p50_ms"], p["p99_ms"]]
+                                         for p in sv["points"]},
+                          "gbs_at_0.95": sv["points"][-1]["achieved_gbs"],
+                          "max_slots_busy": max(p["max_slots_busy"] for p in sv["points"])}
+    st = line.get("large_streaming")
+    if st:
+        u = st.get("uniform_reading") or {}
+        out["streaming"] = {"gbs": st["gbps"], "uniform_msgs_gbs": u.get("messages_gbps"),
+                            "uniform_all_gbs": u.get("gbps")}
+    return out
 
 
 # ---------------------------------------------------------------- batched
@@ -550,18 +577,23 @@ def run_batched(torch, tdes, synth, stream, ecb_gbs):
     total = int(lens.sum())
     par = ents[ents["mode"] != 4]
     par_bytes = int(par["nbytes"].sum())
-    # autotune the launch shape on the parallel-mode part (the throughput part)
+    # the library's autotuner on the parallel-mode part (the throughput part;
+    # out of place, so its repeated runs leave the inputs intact): it times
+    # the candidate shapes and stores the winner in the cache, then the whole
+    # batch runs in the same shape
     bpar = tdes.Batch(kt, par)
-    best = None
-    for shape in ((8, 0), (8, 1), (6, 0), (4, 0)):
-        bpar.configure(*shape)
-        ms = time_graph(torch, bpar, stream, 5)
-        if best is None or ms < best[1]:
-            best = (shape, ms)
-    bpar.configure(*best[0])
+    tune = bpar.autotune(reps=5, flags=tdes.TUNE_FORCE)
     par_ms = time_graph(torch, bpar, stream, 20)
+    default_shape = tune["baseline"]
+    bdef = tdes.Batch(kt, par)
+    bdef.set_shape(default_shape["warps_per_cta"], default_shape["ctas_per_sm"],
+                   default_shape["tiles_per_claim"], default_shape["round_form"])
+    par_default_ms = time_graph(torch, bdef, stream, 20)
+    del bdef
     ball = tdes.Batch(kt, ents)
-    ball.configure(*best[0])
+    best = tune["best"]
+    ball.set_shape(best["warps_per_cta"], best["ctas_per_sm"], best["tiles_per_claim"],
+                   best["round_form"])
     all_ms = time_graph(torch, ball, stream, 2)
     cbc = ents[ents["mode"] == 4]
     longest = int(cbc["nbytes"].max()) if len(cbc) else 0
@@ -579,7 +611,11 @@ def run_batched(torch, tdes, synth, stream, ecb_gbs):
         "cbc_encrypt_longest_bytes": longest,
         "cbc_encrypt_longest_chain_ms": round(chain_ms, 3),
         "cbc_encrypt_ns_per_block": round(chain_ms * 1e6 / max(1, longest // 8), 1),
-        "autotuned_shape": {"warps_per_cta": best[0][0], "ctas_per_sm": info["ctas_per_sm"]},
+        "autotune": {"class": tune["key"], "tuned_shape": tune["best"],
+                     "default_shape": default_shape, "candidates": tune["candidates"],
+                     "tuned_ms": round(par_ms, 3), "default_ms": round(par_default_ms, 3),
+                     "gain": round(par_default_ms / par_ms, 4),
+                     "cache": tdes.tdes_autotune_cache_path()},
         "tiles": info["n_tiles"], "small_items": info["n_small_items"],
         "cbc_encrypt_messages": info["n_cbc_enc_messages"],
     }
@@ -727,8 +763,12 @@ SERVE_WORKLOAD = ("open-loop Poisson arrivals; sizes 80% uniform 64 B..4 KiB, 20
 
 def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
     kt = tdes.KeyTable(synth.key_triples(4, 16384))
-    srv = tdes.Server(kt, budget_bytes=8 << 30, slots=4, warps_per_cta=4)
     out_pool = torch.empty(8 << 30, dtype=torch.uint8, device=in_pool.device)
+    # the library's server autotuner on this request mix (closed loop); the
+    # server below then starts in the tuned configuration by default
+    tune = tdes.tdes_server_autotune(kt, in_pool, out_pool, n_peak, flags=tdes.TUNE_FORCE,
+                                     seed=11)
+    srv = tdes.Server(kt, budget_bytes=8 << 30)
     srv.loadtest(in_pool, out_pool, 2000, 0.0, seed=99)  # warm-up
     peak = srv.loadtest(in_pool, out_pool, n_peak, 0.0, seed=5)
     points = []
@@ -743,6 +783,9 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
                        "large_p50_ms": round(r["large_p50_ms"], 4),
                        "large_p99_ms": round(r["large_p99_ms"], 4),
                        "requests": r["requests"], "batches": r["batches"],
+                       "max_slots_busy": r["max_slots_busy"],
+                       "max_device_overlap": r["max_device_overlap"],
+                       "device_overlap_frac": round(r["device_overlap_frac"], 4),
                        "duration_s": round(r["duration_s"], 3)})
     # host payloads: request buffers in pinned host memory, read and written by
     # the kernels over the host link (the server's default; its optional device
@@ -753,8 +796,17 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
     hhalf = srv.loadtest(host_in, host_out, n_points // 2, 0.5 * hpeak["gbps"], seed=8)
     srv.close()
     del out_pool, host_in, host_out
+    tuned = {k: tune["best"][k] for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots")}
+    default = {k: tune["baseline"][k] for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots")}
     return {"workload": SERVE_WORKLOAD, "peak_closed_loop_gbs": round(peak["gbps"], 2),
-            "peak_p50_ms": round(peak["p50_ms"], 3), "points": points,
+            "peak_p50_ms": round(peak["p50_ms"], 3),
+            "peak_max_slots_busy": peak["max_slots_busy"],
+            "peak_device_overlap_frac": round(peak["device_overlap_frac"], 4),
+            "autotune": {"class": tune["key"], "tuned": tuned, "default": default,
+                         "tuned_gbs": round(tune["best_gbps"], 2),
+                         "default_gbs": round(tune["baseline_gbps"], 2),
+                         "candidates": tune["candidates"]},
+            "points": points,
             "host_payloads": {"note": "same request mix, payloads in pinned host memory "
                                       "(kernels access it over NVLink-C2C)",
                               "peak_closed_loop_gbs": round(hpeak["gbps"], 2),

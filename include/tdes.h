@@ -135,9 +135,12 @@ int tdes_cbc_encrypt(const tdes_ks_t *ks, uint64_t iv, const void *in, void *out
  * TDES_EINVAL.  Out-of-place calls use no scratch and have no size limit
  * beyond the 2^31 tiles of every call.
  * The call never calls cudaMalloc, cudaFree or any allocating routine.
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array: two in-place
+ * The first in-place call of more than one tile on each device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with that device
+ * current, and looks it up again after the device's context changes (e.g.
+ * after cudaDeviceReset); make that first call before any stream capture.
+ * The size checks come before any device query, so an oversized call is
+ * refused without touching the device.  All calls share the one array: two in-place
  * calls that overlap in time on the GPU (different streams, no ordering
  * between them) race on it and may return wrong plaintext.  Nothing in the
  * array needs clearing: each call writes every entry it reads first. */
@@ -197,7 +200,24 @@ typedef struct {
                                     (batches with 8192 or more small-message blocks) */
     uint32_t n_direct_messages;  /* messages of 64 MiB or more (ECB, CTR, out-of-place CBC
                                     decryption) run by the single-key kernels */
+    int tiles_per_claim;         /* tiles a warp claims at once (the automatic choice resolved) */
+    int round_form;              /* TDES_ROUNDS_PER_PASS or TDES_ROUNDS_COMPACT */
+    int tuned;                   /* 1: the shape came from the autotuner's cache at planning */
 } tdes_batch_info_t;
+
+/* Launch shape of a batch's kernels, i.e. what the autotuner searches.  A
+ * shape changes how the work is spread over the GPU, never the result. */
+#define TDES_ROUNDS_PER_PASS 0 /* the 48 rounds as three loops, one per DES pass */
+#define TDES_ROUNDS_COMPACT 1  /* one loop body for all three passes (a third of the code) */
+typedef struct {
+    int warps_per_cta;   /* 1..8; each warp owns a 13 KB shared-memory slice */
+    int ctas_per_sm;     /* resident CTAs per SM in the persistent grid; <= 0: as many as fit
+                            (the grid is SMs x this) */
+    int tiles_per_claim; /* 1024-block tiles a warp takes from the work counter per claim,
+                            i.e. blocks per warp claim / 1024; 0: automatic (1, or 4 when
+                            the batch has over 256 tiles per warp); at most 1024 */
+    int round_form;      /* TDES_ROUNDS_PER_PASS or TDES_ROUNDS_COMPACT */
+} tdes_launch_shape_t;
 
 /* Key schedules (Sec. III-A) of `count` triples (keys: count x 24 bytes,
  * K1||K2||K3 each) computed by the key-schedule kernels and kept in device
@@ -223,8 +243,18 @@ int tdes_batch_plan(const tdes_keytable_t *kt, const tdes_desc_t *descs, uint32_
                     int *per_desc_status, tdes_batch_t **out);
 
 /* Launch shape of the persistent kernel: warps per CTA (1..8; each warp owns
- * a 13 KB shared-memory slice) and CTAs per SM (<= 0: as many as fit). */
+ * a 13 KB shared-memory slice) and CTAs per SM (<= 0: as many as fit); the
+ * shape's other fields are kept. */
 int tdes_batch_configure(tdes_batch_t *b, int warps_per_cta, int ctas_per_sm);
+
+/* Sets (TDES_EINVAL outside the ranges of tdes_launch_shape_t) or reads a
+ * plan's whole launch shape.  A plan starts in the shape the autotuner's
+ * cache holds for its workload class (see tdes_batch_autotune), else in the
+ * default shape: 8 warps per CTA, as many CTAs as fit, automatic tiles per
+ * claim, TDES_ROUNDS_PER_PASS.  Setting a shape drops the plan's captured
+ * graph, which tdes_batch_launch_graph then captures again. */
+int tdes_batch_set_shape(tdes_batch_t *b, const tdes_launch_shape_t *shape);
+int tdes_batch_get_shape(const tdes_batch_t *b, tdes_launch_shape_t *shape);
 
 /* Runs the whole batch on `stream`: one persistent launch whose warps claim
  * work items from an atomic counter (preceded by a small snapshot launch
@@ -239,6 +269,117 @@ int tdes_batch_info(const tdes_batch_t *b, tdes_batch_info_t *info);
 
 /* Frees a plan; no launch of it may still be running. */
 void tdes_batch_free(tdes_batch_t *b);
+
+/* ------------------------------------------------------------------------
+ * Autotuner.  Not in the paper: it picks the launch shape (warps per CTA,
+ * CTAs per SM, i.e. grid size, tiles per claim, i.e. blocks per warp claim,
+ * and the round loop's form) of the batch kernels by timing them, and keeps
+ * the winner in a cache file keyed by workload class, which every later plan
+ * (tdes_batch_plan, tdes_batch_submit) and server (tdes_server_config_default)
+ * reads.  The class is the GPU's SM count, the share of the payload in each
+ * kind of work (bitsliced tiles, mixed-key tiles, one-block-per-lane items,
+ * CBC-encryption chains, graded 0..3) and the floor of log2 of the payload.
+ * The cache file is TDES_AUTOTUNE_CACHE when that environment variable is
+ * set, else $XDG_CACHE_HOME/tdes_gb300/autotune.jsonl, else
+ * $HOME/.cache/tdes_gb300/autotune.jsonl: JSON lines, the last line of a
+ * class winning.
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    char key[64];                  /* workload class */
+    tdes_launch_shape_t best;      /* the shape chosen */
+    tdes_launch_shape_t baseline;  /* the default shape */
+    double best_ms, baseline_ms;   /* median device time per launch (CUDA events on `stream`);
+                                      from the cache when from_cache is 1 */
+    uint32_t candidates;           /* shapes timed (0 when taken from the cache) */
+    int from_cache;
+} tdes_autotune_result_t;
+
+#define TDES_TUNE_FORCE 1u    /* time the candidates even if the cache has the class */
+#define TDES_TUNE_NO_STORE 2u /* leave the cache file unchanged */
+
+/* Tunes the launch shape of plan b: a coordinate search, timing `reps`
+ * launches (after one warm-up launch) of each candidate on `stream` with
+ * CUDA events -- (warps per CTA, CTAs per SM) over 4 and 8 warps and the
+ * fitting CTA counts, then tiles per claim over 0, 1, 2, 4 and 8, then the
+ * round form -- and a final alternating re-timing of the best against the
+ * default shape, which is kept unless the best is faster.  The plan is left
+ * in the chosen shape and, unless TDES_TUNE_NO_STORE, the choice is appended
+ * to the cache.  If the cache already has b's class and TDES_TUNE_FORCE is
+ * not set, that shape is applied without timing.  Synchronous (waits for
+ * the device).  The plan's whole work runs (reps + 1) times per candidate:
+ * every output is rewritten each time, so messages processed in place are
+ * transformed again and again -- tune on a plan whose outputs are scratch,
+ * or out of place with inputs left intact. */
+int tdes_batch_autotune(tdes_batch_t *b, unsigned flags, int reps, tdes_stream_t stream,
+                        tdes_autotune_result_t *res);
+
+/* Path of the cache file in use (valid until the next call on this thread). */
+const char *tdes_autotune_cache_path(void);
+
+/* ------------------------------------------------------------------------
+ * Batch contexts: submit, poll, wait.  The paper states the problem as
+ * plaintext of 64-bit blocks, three 64-bit keys and a mode (Sec. IV-B,
+ * IV-C); a batch is many such problems at once, each message with its own
+ * key triple (an index into the context's key table) and mode, and a ticket
+ * tells the caller when its batch is done without blocking on the device.
+ * ------------------------------------------------------------------------ */
+
+typedef struct tdes_ctx tdes_ctx_t; /* opaque */
+
+typedef struct {
+    uint32_t streams; /* batches in flight at once, each on its own stream (1..16) */
+} tdes_ctx_config_t;
+
+/* Defaults: 2 streams. */
+void tdes_ctx_config_default(tdes_ctx_config_t *cfg);
+
+/* A context on the current device over key table kt (which must outlive
+ * it), owning its streams.  TDES_EINVAL if kt lives on another device. */
+int tdes_ctx_create(const tdes_keytable_t *kt, const tdes_ctx_config_t *cfg, tdes_ctx_t **out);
+
+/* Waits for every batch the context queued, then frees it and its tickets. */
+void tdes_ctx_destroy(tdes_ctx_t *ctx);
+
+/* Plans `count` descriptors as tdes_batch_plan does (rejected descriptors
+ * are skipped and reported by tdes_batch_poll), queues the batch's work on
+ * one of the context's streams -- a stream with nothing in flight if there
+ * is one -- and returns without waiting for the device.  The plan is copied
+ * into stream-ordered device memory (cudaMallocAsync) that returns to the
+ * pool when the batch's kernels are done; the launch shape is the
+ * autotuner's for the batch's class if the cache has one.  The context's
+ * streams are non-blocking: they do not wait for work the caller queued
+ * elsewhere (the legacy default stream included), so inputs must be ready
+ * before the call.  Buffers must stay valid, and must not be touched by
+ * other work, until the ticket completes.
+ * *ticket identifies the batch (tickets increase by one per submission).
+ * TDES_EINVAL for NULL arguments or a context of another device;
+ * TDES_ENOMEM / TDES_ECUDA if queueing failed (no ticket is issued). */
+int tdes_batch_submit(tdes_ctx_t *ctx, const tdes_desc_t *descs, uint32_t count,
+                      uint64_t *ticket);
+
+/* The same for a batch planned by tdes_batch_plan (it must use the
+ * context's key table): its CUDA graph is replayed on a context stream.
+ * The plan must not be freed or reconfigured before the ticket completes. */
+int tdes_batch_submit_plan(tdes_ctx_t *ctx, tdes_batch_t *b, uint64_t *ticket);
+
+/* Non-blocking.  Returns 1 while the batch is pending (also for a ticket not
+ * issued yet), and once it is done TDES_OK if every descriptor ran, else the
+ * first rejected descriptor's status (TDES_EINVAL), or TDES_ECUDA if the
+ * batch failed on the device.  per_desc_status (nullable; as many entries as
+ * the batch had descriptors) receives per descriptor: 0 done, 1 pending, or
+ * < 0 (TDES_EINVAL: rejected at submission and skipped; TDES_ECUDA).
+ * TDES_EINVAL for a released ticket. */
+int tdes_batch_poll(tdes_ctx_t *ctx, uint64_t ticket, int *per_desc_status);
+
+/* Waits at most timeout_ns for a ticket, sleeping between polls (from 2 us
+ * doubling up to 1 ms); returns tdes_batch_poll's final status or
+ * TDES_ETIMEDOUT.  Never hangs. */
+int tdes_batch_wait(tdes_ctx_t *ctx, uint64_t ticket, uint64_t timeout_ns);
+
+/* Forgets a completed ticket (its per-descriptor statuses); TDES_EBUSY
+ * while it is pending.  Tickets are otherwise kept until tdes_ctx_destroy. */
+int tdes_batch_release(tdes_ctx_t *ctx, uint64_t ticket);
 
 /* ------------------------------------------------------------------------
  * Uniform messages: n_msgs messages of msg_bytes each, back to back (message
@@ -321,14 +462,20 @@ typedef struct {
 } tdes_server_config_t;
 
 /* Defaults: 8 GiB budget, 4 slots, 16384 requests per batch, 4 warps per CTA,
- * 1 CTA per SM reserved, 2^21 completion records. */
+ * 1 CTA per SM reserved, 2^21 completion records -- except that slots, warps
+ * per CTA and reserved CTAs come from the autotune cache when it has an
+ * entry for the current device's SM count (tdes_server_autotune). */
 void tdes_server_config_default(tdes_server_config_t *cfg);
 
 /* Starts a server on the current device over a key table (which must
  * outlive it).  A dispatcher thread admits queued requests in arrival order
  * while the admitted bytes stay within the budget, plans each admitted group
  * into one persistent batch launch on a free slot, and records completions;
- * requests arriving while batches run go into the next free slot. */
+ * requests arriving while batches run go into the next free slot.  With
+ * nothing queued and nothing in flight the dispatcher sleeps until a
+ * submission; while batches are in flight it polls their events, yielding
+ * for 50 us after its last progress and then napping (5 us doubling to
+ * 100 us, ended early by a submission). */
 int tdes_server_create(const tdes_keytable_t *kt, const tdes_server_config_t *cfg,
                        tdes_server_t **out);
 
@@ -340,7 +487,9 @@ int tdes_server_submit(tdes_server_t *s, const tdes_desc_t *req, uint64_t *ticke
 /* 0 complete, 1 pending, < 0 the request failed. */
 int tdes_server_poll(tdes_server_t *s, uint64_t ticket);
 
-/* Waits (bounded) for a ticket: its status, or TDES_ETIMEDOUT; never hangs. */
+/* Waits (bounded) for a ticket: its status, or TDES_ETIMEDOUT; never hangs.
+ * The thread sleeps until the dispatcher signals a completion (at most 1 ms
+ * per sleep).  A ticket not issued yet reads as pending. */
 int tdes_server_wait(tdes_server_t *s, uint64_t ticket, uint64_t timeout_ns);
 
 /* A group of `count` (>= 1) requests under one ticket.  Every descriptor is
@@ -397,10 +546,55 @@ typedef struct {
     double offered_gbps;
     double duration_s;
     uint64_t requests, bytes, batches;
+    uint32_t max_slots_busy;     /* tdes_server_stats over this run */
+    uint32_t max_device_overlap;
+    double device_overlap_frac;  /* device_overlap_ms / device_busy_ms */
 } tdes_loadtest_result_t;
 
 int tdes_serve_loadtest(tdes_server_t *s, const tdes_loadtest_config_t *cfg,
                         tdes_loadtest_result_t *res);
+
+/* Overlap of a server's batches.  A batch is "in flight" from its dispatch
+ * to the dispatcher's noticing its completion event, and "on the device"
+ * from an event recorded on its slot's stream before its plan copy to one
+ * after its last kernel (CUDA event times). */
+typedef struct {
+    uint64_t batches;            /* batches completed (and timed) since the last reset */
+    uint32_t max_slots_busy;     /* most batches in flight at once */
+    uint32_t max_device_overlap; /* most batches on the device at one instant */
+    double device_busy_ms;       /* time with at least one batch on the device */
+    double device_overlap_ms;    /* time with two or more batches on the device */
+    double batch_ms_sum;         /* sum of the batches' times on the device */
+    uint64_t untimed_batches;    /* batches whose events could not be read (errors) */
+} tdes_server_stats_t;
+
+/* Statistics since the server started or since the last call with reset != 0
+ * (which clears them after reading).  tdes_serve_loadtest resets them when
+ * it starts. */
+int tdes_server_stats(tdes_server_t *s, int reset, tdes_server_stats_t *out);
+
+/* Autotuner of the server's shape (warps per CTA, CTAs per SM each batch
+ * leaves free for the next, and slots): a coordinate search over warps 2, 4,
+ * 8, reserved CTAs 0, 1, 2 and slots 2, 4, 8, each candidate the median
+ * closed-loop GB/s of three tdes_serve_loadtest runs of `load` (its
+ * offered_gbps is ignored: every request arrives at once) on a fresh server,
+ * then the best against the built-in default (4 warps, 1 reserved CTA, 4
+ * slots), alternating, kept only if faster.  Unless TDES_TUNE_NO_STORE, the
+ * choice is appended to the autotune cache, from which
+ * tdes_server_config_default takes it on this kind of GPU.  If the cache
+ * already has it and TDES_TUNE_FORCE is not set, nothing is timed.  The
+ * load test writes into load->out_pool. */
+typedef struct {
+    char key[64];
+    tdes_server_config_t best;     /* the default configuration with the tuned fields */
+    tdes_server_config_t baseline; /* the built-in default */
+    double best_gbps, baseline_gbps;
+    uint32_t candidates;
+    int from_cache;
+} tdes_server_autotune_result_t;
+
+int tdes_server_autotune(const tdes_keytable_t *kt, const tdes_loadtest_config_t *load,
+                         unsigned flags, tdes_server_autotune_result_t *res);
 
 /* Number of LOP3 instructions the eight generated S-box circuits take per
  * round, i.e. per 32 blocks per round (the circuit size fixed at build time). */

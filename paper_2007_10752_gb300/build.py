@@ -22,6 +22,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtdes_gb300.so")
 TOOLS_LIB = os.path.join(HERE, "libtdes_tools.so")  # benchmark/test tools, not the cipher
 SOURCES = ["tdes_api.cu", "tdes_kernels.cu", "tdes_small.cu", "tdes_noalloc.cu", "tdes_batch.cu",
+           "tdes_tune.cu", "tdes_ctx.cu",
            "tdes_serve.cu", "tdes_uniform.cu"]
 TOOLS_SOURCES = ["tdes_tools.cu", "tdes_paper_design.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

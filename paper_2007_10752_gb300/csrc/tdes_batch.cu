@@ -29,9 +29,11 @@
 #include "../../include/tdes.h"
 #include "tdes_batch_internal.h"
 #include "tdes_internal.h"
+#include "tdes_compact.cuh"
 #include "tdes_keysched.cuh"
 #include "tdes_mixed.cuh"
 #include "tdes_scalar.cuh"
+#include "tdes_tune.h"
 
 namespace tdes {
 
@@ -146,7 +148,11 @@ __device__ __forceinline__ void store_be(uint8_t* p, uint64_t i, uint64_t v) {
 
 // One bitsliced tile: blocks [b0, b0 + 1024) of message m (ragged at the end).
 // The message record is read again after the rounds rather than kept in
-// registers across them (the 64 planes need the register file).
+// registers across them (the 64 planes need the register file).  COMPACT
+// runs the 48 rounds as one loop body for all three passes
+// (tdes_compact.cuh) instead of one loop per pass: a launch-shape choice of
+// the autotuner, the same arithmetic.
+template <bool COMPACT>
 __device__ __forceinline__ void batch_bs_tile(const BatchMsg* __restrict__ mp, uint64_t tile,
                                               uint64_t gtile, const uint32_t* __restrict__ tab,
                                               const uint64_t* __restrict__ halo, uint32_t lane,
@@ -193,7 +199,10 @@ __device__ __forceinline__ void batch_bs_tile(const BatchMsg* __restrict__ mp, u
             }
     }
     }
-    tdes_process32_rt(A0, A1, tab, one_pass);
+    if (COMPACT)
+        tdes_process32_compact<false>(A0, A1, tab, one_pass);
+    else
+        tdes_process32_rt(A0, A1, tab, one_pass);
     const BatchMsg m = *mp;
     const uint64_t n = m.nblocks;
     const bool full = b0 + kTileBlocks <= n;
@@ -459,8 +468,9 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
 // when the other items are gone and the chains are gone or its slot is held
 // by another warp, which will come back for them.  Without such chains the
 // kernel claims from one counter only (the slot logic measured 3% slower on
-// the other items even when unused).
-template <bool SOLO_SLOTS>
+// the other items even when unused).  COMPACT: the round form of the tiles
+// (batch_bs_tile).
+template <bool SOLO_SLOTS, bool COMPACT>
 __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
     for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) g_st.sp[i] = (&kBatchSP[0][0])[i];
     for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) {
@@ -537,7 +547,7 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
                     __syncwarp();
                     staged = want;
                 }
-                batch_bs_tile(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane, one_pass);
+                batch_bs_tile<COMPACT>(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane, one_pass);
             }
             continue;
         }
@@ -628,7 +638,13 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     std::vector<MSlice> m_slices;
     uint64_t small_blocks = 0;
     for (uint32_t mi : s_list) small_blocks += msgs[mi].nblocks;
-    if (small_blocks >= kMixedMinBlocks) {
+    const bool mixed = small_blocks >= kMixedMinBlocks;
+    h->kind_bytes[mixed ? 1 : 2] += 8 * small_blocks;
+    for (uint32_t mi : c_list) h->kind_bytes[3] += 8 * msgs[mi].nblocks;
+    for (uint32_t mi : b_msg) h->kind_bytes[0] += 8 * msgs[mi].nblocks;
+    for (const SPiece& pc : split) h->kind_bytes[2] += 8ull * pc.n;
+    for (const DirectMsg& m : h->direct) h->kind_bytes[4] += 8 * m.nblocks;
+    if (mixed) {
         auto keydir = [&](uint32_t mi) {
             const uint32_t dir = (msgs[mi].mode == TDES_MODE_ECB_DECRYPT ||
                                   msgs[mi].mode == TDES_MODE_CBC_DECRYPT) ? 1u : 0u;
@@ -740,37 +756,44 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
     const size_t dyn = (size_t)warps * kWarpSmemBytes;
     // The limit is a property of the kernel function shared by every plan, so
     // it is always set for the largest shape (8 warps) rather than this one.
-    cudaError_t e = cudaFuncSetAttribute(tdes_batch_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8 * kWarpSmemBytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tdes_batch_kernel<true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kWarpSmemBytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tdes_batch_mixed_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kWarpSmemBytes);
-    if (e != cudaSuccess) return e;
+    const void* fns[] = {(const void*)tdes_batch_kernel<false, false>,
+                         (const void*)tdes_batch_kernel<true, false>,
+                         (const void*)tdes_batch_kernel<false, true>,
+                         (const void*)tdes_batch_kernel<true, true>,
+                         (const void*)tdes_batch_mixed_kernel};
+    cudaError_t e = cudaSuccess;
+    for (const void* f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 8 * kWarpSmemBytes);
+        if (e != cudaSuccess) return e;
+    }
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_batch_kernel<false>, 32 * warps,
-                                                      dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tdes_batch_kernel<false, false>,
+                                                      32 * warps, dyn);
     if (e != cudaSuccess) return e;
     *dyn_smem = dyn;
     *ctas_fit = n < 1 ? 1 : n;
     return cudaSuccess;
 }
 
-cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool needs_halo, int warps,
-                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s, bool counter_fresh) {
+// A claimed tile takes a warp tens of microseconds at full occupancy, which
+// already hides its message search and key staging behind the other warps,
+// so claims are single tiles unless a batch has so many tiles (over 256 per
+// warp) that the atomic counter itself and the restaging become worth
+// amortising; the tail of a batch then costs at most one claim.
+uint32_t auto_tiles_per_claim(uint64_t n_tiles, uint64_t warps_total) {
+    return n_tiles > 256 * std::max<uint64_t>(1, warps_total) ? 4u : 1u;
+}
+
+cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool needs_halo,
+                          const LaunchShape& shape, size_t dyn_smem, uint64_t max_ctas,
+                          cudaStream_t s, bool counter_fresh) {
     if (total_items == 0) return cudaSuccess;
-    // Tiles per claim.  A claimed tile takes a warp tens of microseconds at
-    // full occupancy, which already hides its message search and key staging
-    // behind the other warps, so claims are single tiles unless a batch has
-    // so many tiles (over 256 per warp) that the atomic counter itself and
-    // the restaging become worth amortising; the tail of a batch then costs
-    // at most one claim.
     BatchParams p = p_in;
+    const int warps = shape.warps;
     const uint64_t warps_total = std::max<uint64_t>(1, max_ctas * (uint64_t)warps);
-    p.b_chunk = p.n_b_tiles > 256 * warps_total ? 4u : 1u;
+    p.b_chunk = shape.tiles_per_claim > 0 ? (uint32_t)shape.tiles_per_claim
+                                          : auto_tiles_per_claim(p.n_b_tiles, warps_total);
     p.n_b_chunks = (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk;
     total_items = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
     cudaError_t e = cudaSuccess;
@@ -791,10 +814,15 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
     if (total_items == 0) return cudaSuccess;
     const uint64_t want = (total_items + warps - 1) / (uint64_t)warps;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
-    if (p.n_c_solo)
-        tdes_batch_kernel<true><<<grid, 32 * warps, dyn_smem, s>>>(p);
+    const bool solo = p.n_c_solo != 0, compact = shape.round_form == 1;
+    if (solo && compact)
+        tdes_batch_kernel<true, true><<<grid, 32 * warps, dyn_smem, s>>>(p);
+    else if (solo)
+        tdes_batch_kernel<true, false><<<grid, 32 * warps, dyn_smem, s>>>(p);
+    else if (compact)
+        tdes_batch_kernel<false, true><<<grid, 32 * warps, dyn_smem, s>>>(p);
     else
-        tdes_batch_kernel<false><<<grid, 32 * warps, dyn_smem, s>>>(p);
+        tdes_batch_kernel<false, false><<<grid, 32 * warps, dyn_smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -824,23 +852,6 @@ cudaError_t enqueue_direct(const std::vector<DirectMsg>& direct, const tdes_keyt
 
 }  // namespace tdes
 
-struct tdes_batch {
-    int device;
-    const tdes_keytable* kt;
-    void* mem;
-    tdes::BatchParams params;
-    uint64_t total_items;
-    bool needs_halo;
-    int warps;         // warps per CTA
-    int ctas_per_sm;   // resident CTAs per SM used for the grid
-    int sms;
-    size_t dyn_smem;
-    cudaGraph_t graph;
-    cudaGraphExec_t exec;
-    uint64_t bytes[5];  // payload bytes per mode
-    std::vector<tdes::DirectMsg> direct;  // run by the single-key kernels
-};
-
 namespace {
 
 int bfail(int status, const char* fmt, ...) {
@@ -858,14 +869,24 @@ int bcuda(cudaError_t e, const char* what) {
                  cudaGetErrorString(e));
 }
 
-int set_launch_config(tdes_batch_t* b, int warps, int ctas_per_sm) {
+}  // namespace
+
+namespace tdes {
+
+int set_batch_shape(tdes_batch* b, const LaunchShape& shape_in) {
+    LaunchShape shape = shape_in;
+    if (shape.warps < 1 || shape.warps > 8 || shape.tiles_per_claim < 0 ||
+        shape.tiles_per_claim > 1024 || shape.round_form < 0 || shape.round_form > 1)
+        return bfail(TDES_EINVAL, "launch shape: 1..8 warps per CTA, 0..1024 tiles per claim, "
+                                  "round form 0 or 1");
     size_t dyn = 0;
     int fit = 1;
-    cudaError_t e = tdes::prepare_batch_kernel(warps, &dyn, &fit);
+    cudaError_t e = prepare_batch_kernel(shape.warps, &dyn, &fit);
     if (e != cudaSuccess) return bcuda(e, "batch kernel set-up");
-    b->warps = warps;
+    shape.ctas_per_sm = shape.ctas_per_sm < 1 ? fit : std::min(shape.ctas_per_sm, fit);
+    b->shape = shape;
+    b->ctas_fit = fit;
     b->dyn_smem = dyn;
-    b->ctas_per_sm = ctas_per_sm < 1 ? fit : std::min(ctas_per_sm, fit);
     if (b->exec) {  // launch shape changed: recapture on next graph launch
         cudaGraphExecDestroy(b->exec);
         cudaGraphDestroy(b->graph);
@@ -875,16 +896,17 @@ int set_launch_config(tdes_batch_t* b, int warps, int ctas_per_sm) {
     return TDES_OK;
 }
 
-cudaError_t enqueue(tdes_batch_t* b, cudaStream_t s) {
-    cudaError_t e = tdes::enqueue_direct(b->direct, b->kt, b->device, s);
+cudaError_t enqueue_planned(tdes_batch* b, cudaStream_t s) {
+    cudaError_t e = enqueue_direct(b->direct, b->kt, b->device, s);
     if (e != cudaSuccess || b->total_items == 0) return e;
-    return tdes::enqueue_batch(b->params, b->total_items, b->needs_halo, b->warps, b->dyn_smem,
-                               (uint64_t)b->sms * b->ctas_per_sm, s);
+    return enqueue_batch(b->params, b->total_items, b->needs_halo, b->shape, b->dyn_smem,
+                         (uint64_t)b->sms * b->shape.ctas_per_sm, s);
 }
 
-}  // namespace
+}  // namespace tdes
 
 extern "C" {
+
 
 int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** out) {
     if (out == nullptr || (keys == nullptr && count > 0))
@@ -932,6 +954,9 @@ int tdes_keytable_create(const uint8_t* keys, uint32_t count, tdes_keytable_t** 
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(dkeys, 0, (size_t)count * 24, s);  // keys not kept
+    kt->host_stages.assign(count, 3);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(kt->host_stages.data(), kt->stages, count, cudaMemcpyDeviceToHost, s);
     if (s) {
         cudaError_t e2 = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = e2;
@@ -967,12 +992,7 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     if (dev != kt->device) return bfail(TDES_EINVAL, "key table lives on another device");
     tdes::PlanHost h;
     tdes::build_plan(descs, count, kt->count, per_desc_status, &h, true);
-    for (tdes::DirectMsg& m : h.direct) {  // the key's DES passes, from the key table
-        uint8_t st = 3;
-        e = cudaMemcpy(&st, kt->stages + m.key, 1, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return bcuda(e, "reading a key's pass count");
-        m.stages = st;
-    }
+    for (tdes::DirectMsg& m : h.direct) m.stages = kt->host_stages[m.key];  // the key's DES passes
     if (!h.direct.empty()) tdes::geometry_for(1, tdes::kEcb, dev);  // kernel set-up, outside any capture
     void* mem = nullptr;
     e = cudaMalloc(&mem, h.image.size());
@@ -994,9 +1014,27 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     b->total_items = h.total_items;
     b->needs_halo = h.needs_halo;
     memcpy(b->bytes, h.bytes_per_mode, sizeof b->bytes);
+    memcpy(b->kind_bytes, h.kind_bytes, sizeof b->kind_bytes);
     b->direct = h.direct;
+    if (per_desc_status) b->status.assign(per_desc_status, per_desc_status + count);
+    else {
+        b->status.resize(count);
+        for (uint32_t i = 0; i < count; ++i) b->status[i] = tdes::validate_desc(descs[i], kt->count);
+    }
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    int rc = set_launch_config(b, tdes::kWideWarps, 0);
+    // the autotuner's shape for this class of batch, if it has one; else the default
+    tdes::TunedShape tuned;
+    b->tuned = tdes::tune_lookup(tdes::tune_key(h, b->sms), &tuned);
+    tdes::LaunchShape shape;
+    shape.warps = tdes::kWideWarps;
+    if (b->tuned) shape = tuned.shape;
+    int rc = tdes::set_batch_shape(b, shape);
+    if (rc != TDES_OK && b->tuned) {  // a cache entry this build cannot use
+        b->tuned = false;
+        shape = tdes::LaunchShape();
+        shape.warps = tdes::kWideWarps;
+        rc = tdes::set_batch_shape(b, shape);
+    }
     if (rc != TDES_OK) {
         cudaFree(mem);
         delete b;
@@ -1010,13 +1048,35 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
 int tdes_batch_configure(tdes_batch_t* b, int warps_per_cta, int ctas_per_sm) {
     if (b == nullptr || warps_per_cta < 1 || warps_per_cta > 8)
         return bfail(TDES_EINVAL, "tdes_batch_configure: 1..8 warps per CTA");
-    return set_launch_config(b, warps_per_cta, ctas_per_sm);
+    tdes::LaunchShape shape = b->shape;
+    shape.warps = warps_per_cta;
+    shape.ctas_per_sm = ctas_per_sm;
+    return tdes::set_batch_shape(b, shape);
+}
+
+int tdes_batch_set_shape(tdes_batch_t* b, const tdes_launch_shape_t* shape) {
+    if (b == nullptr || shape == nullptr) return bfail(TDES_EINVAL, "NULL argument");
+    tdes::LaunchShape s;
+    s.warps = shape->warps_per_cta;
+    s.ctas_per_sm = shape->ctas_per_sm;
+    s.tiles_per_claim = shape->tiles_per_claim;
+    s.round_form = shape->round_form;
+    return tdes::set_batch_shape(b, s);
+}
+
+int tdes_batch_get_shape(const tdes_batch_t* b, tdes_launch_shape_t* shape) {
+    if (b == nullptr || shape == nullptr) return bfail(TDES_EINVAL, "NULL argument");
+    shape->warps_per_cta = b->shape.warps;
+    shape->ctas_per_sm = b->shape.ctas_per_sm;
+    shape->tiles_per_claim = b->shape.tiles_per_claim;
+    shape->round_form = b->shape.round_form;
+    return TDES_OK;
 }
 
 int tdes_batch_launch(tdes_batch_t* b, tdes_stream_t stream) {
     if (b == nullptr) return bfail(TDES_EINVAL, "batch is NULL");
     if (b->total_items == 0 && b->direct.empty()) return TDES_OK;
-    cudaError_t e = enqueue(b, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = tdes::enqueue_planned(b, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? TDES_OK : bcuda(e, "batch launch");
 }
 
@@ -1032,7 +1092,7 @@ int tdes_batch_launch_graph(tdes_batch_t* b, tdes_stream_t stream) {
         if (e != cudaSuccess) return bcuda(e, "cudaStreamCreate");
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = enqueue(b, cap);
+            cudaError_t e1 = tdes::enqueue_planned(b, cap);
             cudaGraph_t g = nullptr;
             e = cudaStreamEndCapture(cap, &g);
             if (e == cudaSuccess) e = e1;
@@ -1057,8 +1117,15 @@ int tdes_batch_info(const tdes_batch_t* b, tdes_batch_info_t* info) {
     info->n_small_items = b->params.n_s_items;
     info->n_mixed_tiles = b->params.n_m_tiles;
     info->n_direct_messages = (uint32_t)b->direct.size();
-    info->warps_per_cta = b->warps;
-    info->ctas_per_sm = b->ctas_per_sm;
+    info->warps_per_cta = b->shape.warps;
+    info->ctas_per_sm = b->shape.ctas_per_sm;
+    info->tiles_per_claim = b->shape.tiles_per_claim > 0
+                                ? b->shape.tiles_per_claim
+                                : (int)tdes::auto_tiles_per_claim(
+                                      b->params.n_b_tiles,
+                                      (uint64_t)b->sms * b->shape.ctas_per_sm * b->shape.warps);
+    info->round_form = b->shape.round_form;
+    info->tuned = b->tuned ? 1 : 0;
     for (int i = 0; i < 5; ++i) info->bytes_per_mode[i] = b->bytes[i];
     return TDES_OK;
 }

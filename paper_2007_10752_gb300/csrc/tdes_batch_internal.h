@@ -16,6 +16,7 @@ struct tdes_keytable {
     uint8_t* chunks;  // [key][dir][384] scalar round-key words
     uint8_t* stages;  // [key] DES passes: 3, or 1 for a triple that reduces to single DES
     uint32_t* packed; // [key][dir][104] three-pass tables, one bit per word (mixed-key tiles)
+    std::vector<uint8_t> host_stages;  // host copy of `stages`, for planning without a device read
 };
 
 namespace tdes {
@@ -92,6 +93,14 @@ struct DirectMsg {
     int stages;   // DES passes of the key (read from the key table at plan time)
 };
 
+// Launch shape of the batch kernels (the autotuner's search space).
+struct LaunchShape {
+    int warps = 8;             // warps per CTA, 1..8 (each owns a 13 KB shared-memory slice)
+    int ctas_per_sm = 0;       // resident CTAs per SM for the grid; <= 0: as many as fit
+    int tiles_per_claim = 0;   // 1024-block tiles a warp claims at once; 0: automatic
+    int round_form = 0;        // 0: three loop bodies (one per DES pass); 1: one compact body
+};
+
 // A batch laid out on the host as the byte image of its device buffer.
 struct PlanHost {
     std::vector<uint8_t> image;
@@ -101,6 +110,9 @@ struct PlanHost {
     uint64_t n_b_tiles = 0, total_items = 0;
     bool needs_halo = false;
     uint64_t bytes_per_mode[5] = {0, 0, 0, 0, 0};
+    // payload bytes per kind of work: [0] bitsliced tiles, [1] mixed-key tiles,
+    // [2] one block per lane (S items), [3] CBC-encryption chains, [4] direct
+    uint64_t kind_bytes[5] = {0, 0, 0, 0, 0};
     int invalid = 0;
     std::vector<DirectMsg> direct;  // only when the plan allows them
 };
@@ -121,13 +133,45 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
 cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit);
 // Counter reset (unless the caller has just copied the plan image, whose
 // counter is zero), halo snapshot (if needed), the mixed-key kernel (if any)
-// and the persistent kernel on s.
-cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo, int warps,
-                          size_t dyn_smem, uint64_t max_ctas, cudaStream_t s,
-                          bool counter_fresh = false);
+// and the persistent kernel on s, in the given shape (shape.warps warps per
+// CTA, at most max_ctas CTAs; dyn_smem from prepare_batch_kernel).
+cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo,
+                          const LaunchShape& shape, size_t dyn_smem, uint64_t max_ctas,
+                          cudaStream_t s, bool counter_fresh = false);
+// Tiles per claim that a shape's 0 (automatic) stands for, for a plan of
+// n_tiles tiles run by warps_total warps.
+uint32_t auto_tiles_per_claim(uint64_t n_tiles, uint64_t warps_total);
 // The single-key kernel launches of a plan's direct messages on s (before
 // its batch launches; each uses the whole GPU).
 cudaError_t enqueue_direct(const std::vector<DirectMsg>& direct, const tdes_keytable* kt,
                            int device, cudaStream_t s);
 
+}  // namespace tdes
+
+// A planned batch (opaque tdes_batch_t in include/tdes.h).
+struct tdes_batch {
+    int device;
+    const tdes_keytable* kt;
+    void* mem;
+    tdes::BatchParams params;
+    uint64_t total_items;
+    bool needs_halo;
+    tdes::LaunchShape shape;  // ctas_per_sm resolved (>= 1)
+    int ctas_fit;             // CTAs of shape.warps warps that fit on an SM
+    int sms;
+    size_t dyn_smem;
+    bool tuned;               // shape taken from the autotuner's cache
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    uint64_t bytes[5];  // payload bytes per mode
+    uint64_t kind_bytes[5];
+    std::vector<tdes::DirectMsg> direct;  // run by the single-key kernels
+    std::vector<int> status;              // per descriptor, from planning
+};
+
+namespace tdes {
+// Sets a batch's launch shape (recapturing its graph on next use).
+int set_batch_shape(tdes_batch* b, const LaunchShape& shape);
+// Queues a batch's whole work on s (direct messages, then the batch kernels).
+cudaError_t enqueue_planned(tdes_batch* b, cudaStream_t s);
 }  // namespace tdes

@@ -9,6 +9,7 @@
 // allocation on its hot path, or code that has to keep a bounded, fixed
 // memory footprint.  For them, tdes_cbc_decrypt_noalloc keeps that scratch in
 // a fixed array compiled into this library instead.
+#include <cuda.h>  // CUcontext and cuCtxGetCurrent's type only: resolved through the runtime
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -26,9 +27,15 @@ namespace {
 constexpr uint64_t kMaxTiles = TDES_NOALLOC_MAX_TILES;
 static __device__ __align__(256) uint64_t g_halo_scratch[kMaxTiles];
 
-// Device address of g_halo_scratch, looked up once per device.
+// Device address of g_halo_scratch, looked up once per device and context:
+// a new context on a device (after cudaDeviceReset, say) loads the module
+// again, possibly elsewhere, so the address is looked up again then.
 constexpr int kMaxDevices = 64;
-uint64_t* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    CUcontext ctx = nullptr;
+    uint64_t* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mutex;
 
 int fail(int status, const char* fmt, ...) {
@@ -41,20 +48,44 @@ int fail(int status, const char* fmt, ...) {
     return status;
 }
 
+// The driver's cuCtxGetCurrent, found through the runtime (so that the
+// library does not link the driver library itself).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<CtxGetCurrentFn>(p);
+    }();
+    return fn;
+}
+
 // With `device` current, return the device address of the scratch array.
 // In host code g_halo_scratch names only a host-side shadow of the symbol,
 // never the device memory, so the address must come from the runtime.
 int scratch_for(int device, uint64_t** out) {
     if (device < 0 || device >= kMaxDevices) return fail(TDES_EINVAL, "device %d out of range", device);
+    CUcontext ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get == nullptr || get(&ctx) != CUDA_SUCCESS || ctx == nullptr)
+        return fail(TDES_ECUDA, "no current CUDA context on device %d", device);
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (g_scratch_addr[device] == nullptr) {
+    ScratchAddr& a = g_scratch_addr[device];
+    if (a.addr == nullptr || a.ctx != ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_halo_scratch);
         if (e != cudaSuccess)
             return fail(TDES_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_scratch_addr[device] = static_cast<uint64_t*>(p);
+        a.addr = static_cast<uint64_t*>(p);
+        a.ctx = ctx;
     }
-    *out = g_scratch_addr[device];
+    *out = a.addr;
     return TDES_OK;
 }
 
@@ -72,6 +103,17 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t* ks, uint64_t iv, const void* in, v
     if ((a | b) & 7u) return fail(TDES_EINVAL, "data pointers must be 8-byte aligned");
     if (a != b && a < b + nbytes && b < a + nbytes)
         return fail(TDES_EINVAL, "input and output overlap without being the same buffer");
+    // size limits first: they need no device and touch no memory
+    const uint64_t nblocks = nbytes / 8;
+    const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
+    if (nblocks / tdes::kTileBlocks >= (1ull << 31))
+        return fail(TDES_EINVAL, "a call is limited to 2^31 tiles of 8 KiB (16 TiB)");
+    if (in == out && ntiles > kMaxTiles)
+        return fail(TDES_EINVAL,
+                    "in-place call of %zu bytes exceeds the fixed scratch limit of %llu bytes "
+                    "(%llu tiles of 8 KiB)",
+                    nbytes, (unsigned long long)(kMaxTiles * 8 * tdes::kTileBlocks),
+                    (unsigned long long)kMaxTiles);
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(TDES_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
@@ -80,19 +122,9 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t* ks, uint64_t iv, const void* in, v
                     ks->device, dev);
     if (!tdes::gpu_addressable(in) || !tdes::gpu_addressable(out))
         return fail(TDES_EINVAL, "buffers must be device memory or pinned, mapped host memory");
-    const uint64_t nblocks = nbytes / 8;
-    const uint64_t ntiles = (nblocks + tdes::kTileBlocks - 1) / tdes::kTileBlocks;
-    if (nblocks / tdes::kTileBlocks >= (1ull << 31))
-        return fail(TDES_EINVAL, "a call is limited to 2^31 tiles of 8 KiB (16 TiB)");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint64_t* halo = nullptr;
     if (in == out && ntiles > 1) {
-        if (ntiles > kMaxTiles)
-            return fail(TDES_EINVAL,
-                        "in-place call of %zu bytes exceeds the fixed scratch limit of %llu bytes "
-                        "(%llu tiles of 8 KiB)",
-                        nbytes, (unsigned long long)(kMaxTiles * 8 * tdes::kTileBlocks),
-                        (unsigned long long)kMaxTiles);
         int rc = scratch_for(dev, &halo);
         if (rc != TDES_OK) return rc;
         // Every entry the decryption reads (tiles 1..ntiles-1) is written here

@@ -13,22 +13,27 @@
 // copied from pinned staging owned by its slot.
 #include <cuda_runtime.h>
 
+#include <sys/prctl.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
 #include "../../include/tdes.h"
 #include "tdes_batch_internal.h"
 #include "tdes_internal.h"
+#include "tdes_tune.h"
 
 namespace {
 
@@ -55,7 +60,8 @@ int64_t now_ns() {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;  // before the batch's first operation on the stream
+    cudaEvent_t done = nullptr;   // after its last
     void* dmem = nullptr;
     size_t dcap = 0;
     uint8_t* pinned = nullptr;
@@ -88,6 +94,35 @@ struct Completion {
 
 uint64_t cost_of(const tdes_desc_t& d) { return d.in == d.out ? d.nbytes : 2 * d.nbytes; }
 
+// A batch's time on the device: from the event before its plan copy to the
+// event after its last kernel, in ms since the server's base event.
+struct Interval {
+    double t0, t1;
+};
+
+// Sweep over intervals: most at once, time with >= 1 and with >= 2.
+void sweep(std::vector<Interval> v, uint32_t* max_at_once, double* busy, double* overlap) {
+    std::vector<std::pair<double, int>> ev;
+    ev.reserve(2 * v.size());
+    for (const Interval& iv : v) {
+        ev.push_back({iv.t0, +1});
+        ev.push_back({iv.t1, -1});
+    }
+    std::sort(ev.begin(), ev.end());  // at equal times an end (-1) sorts before a start
+    int k = 0, mx = 0;
+    double b = 0.0, o = 0.0, prev = ev.empty() ? 0.0 : ev[0].first;
+    for (const auto& e : ev) {
+        if (k >= 1) b += e.first - prev;
+        if (k >= 2) o += e.first - prev;
+        prev = e.first;
+        k += e.second;
+        mx = std::max(mx, k);
+    }
+    *max_at_once = (uint32_t)mx;
+    *busy = b;
+    *overlap = o;
+}
+
 }  // namespace
 
 struct tdes_server {
@@ -106,6 +141,25 @@ struct tdes_server {
     std::atomic<uint64_t> batches{0}, completed{0};
     std::atomic<int> sticky_error{0};
     uint64_t admitted = 0;  // dispatcher thread only
+    // the dispatcher sleeps on cv_work when it has nothing to do or poll;
+    // waiters sleep on cv_done, which the dispatcher signals after completions
+    std::condition_variable cv_work;
+    std::mutex done_mu;
+    std::condition_variable cv_done;
+    std::atomic<int> waiters{0};
+    // overlap statistics: batches in flight (dispatched, not complete) and
+    // every completed batch's device interval since the last reset
+    cudaEvent_t base = nullptr;
+    std::mutex stats_mu;
+    uint32_t busy_now = 0, max_busy = 0;
+    std::vector<Interval> intervals;
+    uint64_t interval_errors = 0;
+
+    void notify_done() {
+        if (waiters.load(std::memory_order_acquire) == 0) return;
+        { std::lock_guard<std::mutex> lock(done_mu); }
+        cv_done.notify_all();
+    }
 
     bool wants_stage(const tdes_desc_t& d) const {
         return cfg.stage_bytes && d.nbytes >= cfg.stage_min_bytes && d.nbytes <= cfg.stage_bytes &&
@@ -152,9 +206,15 @@ struct tdes_server {
         const uint64_t per_sm = std::max<uint64_t>(1, (uint64_t)ctas_fit > reserve
                                                           ? (uint64_t)ctas_fit - reserve : 1);
         const uint64_t max_ctas = (uint64_t)sms * per_sm;
+        tdes::LaunchShape shape;
+        shape.warps = cfg.warps_per_cta;
+        prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);  // naps below end within a microsecond
+        int64_t last_progress = now_ns();
+        int64_t nap_ns = 0;
         for (;;) {
             bool worked = false;
             bool any_busy = false;
+            bool completed_any = false;
             for (Slot& sl : slots) {
                 if (!sl.busy) continue;
                 const cudaError_t q = cudaEventQuery(sl.done);
@@ -169,7 +229,18 @@ struct tdes_server {
                 admitted -= sl.cost;
                 sl.busy = false;
                 worked = true;
+                completed_any = true;
+                float a = 0.f, b = 0.f;
+                const bool timed = st == TDES_OK &&
+                                   cudaEventElapsedTime(&a, base, sl.start) == cudaSuccess &&
+                                   cudaEventElapsedTime(&b, base, sl.done) == cudaSuccess;
+                if (!timed) cudaGetLastError();
+                std::lock_guard<std::mutex> lock(stats_mu);
+                --busy_now;
+                if (timed) intervals.push_back({(double)a, (double)b});
+                else ++interval_errors;
             }
+            if (completed_any) notify_done();
             for (Slot& sl : slots) {
                 if (sl.busy) continue;
                 take.clear();
@@ -203,6 +274,7 @@ struct tdes_server {
                 tdes::build_plan(descs.data(), (uint32_t)descs.size(), kt->count, nullptr, &plan);
                 cudaError_t e = cudaSuccess;
                 if (!ensure_capacity(sl, plan.image.size())) e = cudaErrorMemoryAllocation;
+                if (e == cudaSuccess) e = cudaEventRecord(sl.start, sl.stream);
                 for (const StagedCopy& c : copy_in)
                     if (e == cudaSuccess)
                         e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyHostToDevice, sl.stream);
@@ -213,8 +285,8 @@ struct tdes_server {
                 }
                 if (e == cudaSuccess) {  // the image just copied holds a zeroed claim counter
                     const tdes::BatchParams p = tdes::bind_plan(plan, sl.dmem, kt);
-                    e = tdes::enqueue_batch(p, plan.total_items, plan.needs_halo,
-                                            cfg.warps_per_cta, dyn_smem, max_ctas, sl.stream, true);
+                    e = tdes::enqueue_batch(p, plan.total_items, plan.needs_halo, shape,
+                                            dyn_smem, max_ctas, sl.stream, true);
                 }
                 for (const StagedCopy& c : copy_out)
                     if (e == cudaSuccess)
@@ -224,6 +296,7 @@ struct tdes_server {
                     sticky_error.store(TDES_ECUDA);
                     const int64_t t = now_ns();
                     for (const Pending& pd : take) complete(pd.ticket, TDES_ECUDA, t);
+                    notify_done();
                     continue;
                 }
                 sl.tickets.clear();
@@ -234,15 +307,71 @@ struct tdes_server {
                 any_busy = true;
                 worked = true;
                 batches.fetch_add(1, std::memory_order_relaxed);
+                std::lock_guard<std::mutex> lock(stats_mu);
+                max_busy = std::max(max_busy, ++busy_now);
             }
-            if (stop.load(std::memory_order_acquire) && !any_busy) {
-                std::lock_guard<std::mutex> lock(mu);
-                if (queue.empty()) break;
+            std::unique_lock<std::mutex> lock(mu);
+            if (stop.load(std::memory_order_acquire) && !any_busy && queue.empty()) break;
+            const int64_t now = now_ns();
+            if (worked) {
+                last_progress = now;
+                nap_ns = 0;
+                continue;
             }
-            if (!worked) std::this_thread::yield();
+            if (!any_busy) {
+                // nothing in flight: the queue is empty (anything queued fits the
+                // empty budget), so sleep until a submission or the stop
+                cv_work.wait(lock, [&] {
+                    return !queue.empty() || stop.load(std::memory_order_acquire);
+                });
+                last_progress = now_ns();
+                nap_ns = 0;
+                continue;
+            }
+            // batches in flight: poll their events, yielding for the first
+            // 50 us after the last progress, then in naps of 5 us doubling up
+            // to 100 us; a submission ends a nap at once
+            if (now - last_progress < 50000) {
+                lock.unlock();
+                std::this_thread::yield();
+                continue;
+            }
+            nap_ns = nap_ns ? std::min<int64_t>(2 * nap_ns, 100000) : 5000;
+            const size_t queued = queue.size();
+            cv_work.wait_for(lock, std::chrono::nanoseconds(nap_ns), [&] {
+                return queue.size() != queued || stop.load(std::memory_order_acquire);
+            });
         }
     }
 };
+
+namespace {
+
+// Sleeps on the server's completion signal until poll() stops returning 1
+// or the deadline passes (each sleep at most 1 ms, so a missed signal costs
+// no more than that).
+template <class Poll>
+int wait_until_done(tdes_server_t* s, uint64_t timeout_ns, Poll poll) {
+    const int64_t until = now_ns() + (int64_t)std::min<uint64_t>(timeout_ns, INT64_MAX / 4);
+    int r = poll();
+    if (r != 1) return r;
+    s->waiters.fetch_add(1, std::memory_order_acq_rel);
+    {
+        std::unique_lock<std::mutex> lock(s->done_mu);
+        for (;;) {
+            r = poll();
+            if (r != 1) break;
+            const int64_t now = now_ns();
+            if (now >= until) break;
+            s->cv_done.wait_for(lock, std::chrono::nanoseconds(std::min<int64_t>(until - now,
+                                                                                  1000000)));
+        }
+    }
+    s->waiters.fetch_sub(1, std::memory_order_acq_rel);
+    return r;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -256,6 +385,20 @@ void tdes_server_config_default(tdes_server_config_t* cfg) {
     cfg->ring_entries = 1u << 21;
     cfg->stage_bytes = 0;  // host payloads zero-copy by default: measured faster
     cfg->stage_min_bytes = 64ull << 10;
+    // the autotuner's choice for this GPU, if the cache has one
+    int dev = -1, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    tdes::TunedShape t;
+    if (tdes::tune_lookup(tdes::serve_tune_key(sms), &t) && t.shape.warps >= 1 &&
+        t.shape.warps <= 8 && t.slots >= 1 && t.slots <= 64 && t.shape.ctas_per_sm >= 0) {
+        cfg->warps_per_cta = t.shape.warps;
+        cfg->reserve_ctas_per_sm = t.shape.ctas_per_sm;
+        cfg->slots = (uint32_t)t.slots;
+    }
 }
 
 int tdes_server_create(const tdes_keytable_t* kt, const tdes_server_config_t* cfg_in,
@@ -281,14 +424,18 @@ int tdes_server_create(const tdes_keytable_t* kt, const tdes_server_config_t* cf
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
     e = tdes::prepare_batch_kernel(cfg.warps_per_cta, &s->dyn_smem, &s->ctas_fit);
     s->slots.resize(cfg.slots);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->base);
     for (Slot& sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl.start);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl.done);
         if (e == cudaSuccess && cfg.stage_bytes) {
             e = cudaMalloc(reinterpret_cast<void**>(&sl.stage), cfg.stage_bytes);
             if (e == cudaSuccess) sl.stage_cap = cfg.stage_bytes;
         }
     }
+    if (e == cudaSuccess) e = cudaEventRecord(s->base, s->slots[0].stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(s->base);
     if (e != cudaSuccess) {
         int rc = scuda(e, "server set-up");
         tdes_server_destroy(s);
@@ -311,14 +458,19 @@ int tdes_server_submit(tdes_server_t* s, const tdes_desc_t* req, uint64_t* ticke
         return sfail(TDES_EINVAL, "request of %llu bytes exceeds the admission budget",
                      (unsigned long long)req->nbytes);
     if (s->sticky_error.load()) return sfail(s->sticky_error.load(), "server stopped by an error");
-    std::lock_guard<std::mutex> lock(s->mu);
-    const uint64_t t = s->next_ticket++;
-    *ticket = t;
-    if (req->nbytes == 0) {
-        s->complete(t, TDES_OK, now_ns());
-        return TDES_OK;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        const uint64_t t = s->next_ticket++;
+        *ticket = t;
+        if (req->nbytes == 0) {
+            s->complete(t, TDES_OK, now_ns());
+        } else {
+            s->queue.push_back({*req, t, cost, s->wants_stage(*req)});
+            s->cv_work.notify_one();
+            return TDES_OK;
+        }
     }
-    s->queue.push_back({*req, t, cost, s->wants_stage(*req)});
+    s->notify_done();
     return TDES_OK;
 }
 
@@ -332,14 +484,11 @@ int tdes_server_poll(tdes_server_t* s, uint64_t ticket) {
 }
 
 int tdes_server_wait(tdes_server_t* s, uint64_t ticket, uint64_t timeout_ns) {
-    const int64_t until = now_ns() + (int64_t)std::min<uint64_t>(timeout_ns, INT64_MAX / 2);
-    for (;;) {
-        const int r = tdes_server_poll(s, ticket);
-        if (r != 1) return r;
-        if (now_ns() > until) return sfail(TDES_ETIMEDOUT, "ticket %llu still pending",
-                                           (unsigned long long)ticket);
-        std::this_thread::yield();
-    }
+    if (s == nullptr || ticket == 0) return sfail(TDES_EINVAL, "bad ticket");
+    const int r = wait_until_done(s, timeout_ns, [&] { return tdes_server_poll(s, ticket); });
+    if (r == 1)
+        return sfail(TDES_ETIMEDOUT, "ticket %llu still pending", (unsigned long long)ticket);
+    return r;
 }
 
 int tdes_server_submit_group(tdes_server_t* s, const tdes_desc_t* reqs, uint32_t count,
@@ -356,16 +505,20 @@ int tdes_server_submit_group(tdes_server_t* s, const tdes_desc_t* reqs, uint32_t
             return sfail(TDES_EINVAL, "request %u exceeds the admission budget", i);
     }
     if (s->sticky_error.load()) return sfail(s->sticky_error.load(), "server stopped by an error");
-    std::lock_guard<std::mutex> lock(s->mu);
-    const uint64_t t0 = s->next_ticket;
-    s->next_ticket += count;
-    *ticket = t0;
-    for (uint32_t i = 0; i < count; ++i) {
-        if (reqs[i].nbytes == 0)
-            s->complete(t0 + i, TDES_OK, now_ns());
-        else
-            s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i]), s->wants_stage(reqs[i])});
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        const uint64_t t0 = s->next_ticket;
+        s->next_ticket += count;
+        *ticket = t0;
+        for (uint32_t i = 0; i < count; ++i) {
+            if (reqs[i].nbytes == 0)
+                s->complete(t0 + i, TDES_OK, now_ns());
+            else
+                s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i]), s->wants_stage(reqs[i])});
+        }
+        s->cv_work.notify_one();
     }
+    s->notify_done();
     return TDES_OK;
 }
 
@@ -385,22 +538,48 @@ int tdes_server_poll_group(tdes_server_t* s, uint64_t ticket, uint32_t count,
 
 int tdes_server_wait_group(tdes_server_t* s, uint64_t ticket, uint32_t count,
                            uint64_t timeout_ns) {
-    const int64_t until = now_ns() + (int64_t)std::min<uint64_t>(timeout_ns, INT64_MAX / 2);
-    for (;;) {
-        const int r = tdes_server_poll_group(s, ticket, count, nullptr);
-        if (r != 1) return r;
-        if (now_ns() > until) return sfail(TDES_ETIMEDOUT, "group %llu still pending",
-                                           (unsigned long long)ticket);
-        std::this_thread::yield();
+    if (s == nullptr || ticket == 0 || count == 0) return sfail(TDES_EINVAL, "bad group");
+    const int r = wait_until_done(
+        s, timeout_ns, [&] { return tdes_server_poll_group(s, ticket, count, nullptr); });
+    if (r == 1)
+        return sfail(TDES_ETIMEDOUT, "group %llu still pending", (unsigned long long)ticket);
+    return r;
+}
+
+int tdes_server_stats(tdes_server_t* s, int reset, tdes_server_stats_t* out) {
+    if (s == nullptr || out == nullptr) return sfail(TDES_EINVAL, "NULL argument");
+    std::vector<Interval> iv;
+    {
+        std::lock_guard<std::mutex> lock(s->stats_mu);
+        iv = s->intervals;
+        out->max_slots_busy = s->max_busy;
+        out->untimed_batches = s->interval_errors;
+        if (reset) {
+            s->intervals.clear();
+            s->interval_errors = 0;
+            s->max_busy = s->busy_now;
+        }
     }
+    out->batches = iv.size();
+    double sum = 0.0;
+    for (const Interval& x : iv) sum += x.t1 - x.t0;
+    out->batch_ms_sum = sum;
+    sweep(std::move(iv), &out->max_device_overlap, &out->device_busy_ms, &out->device_overlap_ms);
+    return TDES_OK;
 }
 
 void tdes_server_destroy(tdes_server_t* s) {
     if (s == nullptr) return;
-    s->stop.store(true, std::memory_order_release);
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop.store(true, std::memory_order_release);
+        s->cv_work.notify_all();
+    }
     if (s->thread.joinable()) s->thread.join();
+    if (s->base) cudaEventDestroy(s->base);
     for (Slot& sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.start) cudaEventDestroy(sl.start);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.dmem) cudaFree(sl.dmem);
@@ -487,6 +666,8 @@ int tdes_serve_loadtest(tdes_server_t* s, const tdes_loadtest_config_t* c,
     std::vector<uint64_t> tickets(n);
     const int64_t t0 = now_ns() + 1000000;
     const uint64_t batches0 = s->batches.load();
+    tdes_server_stats_t st0;
+    tdes_server_stats(s, 1, &st0);  // overlap statistics of this run only
     for (uint64_t i = 0; i < n; ++i) {
         tdes_desc_t& d = reqs[i];
         if (head + d.nbytes > c->out_pool_bytes) head = 0;
@@ -505,7 +686,13 @@ int tdes_serve_loadtest(tdes_server_t* s, const tdes_loadtest_config_t* c,
             std::this_thread::yield();
         }
         d.out = static_cast<uint8_t*>(c->out_pool) + lo;
-        while (now_ns() < t0 + arrive[i]) std::this_thread::yield();
+        // the scheduled arrival: sleep while it is far ahead, then spin to it
+        for (int64_t ahead = t0 + arrive[i] - now_ns(); ahead > 0; ahead = t0 + arrive[i] - now_ns()) {
+            if (ahead > 200000)
+                std::this_thread::sleep_for(std::chrono::nanoseconds(ahead - 100000));
+            else
+                std::this_thread::yield();
+        }
         const int rc = tdes_server_submit(s, &d, &tickets[i]);
         if (rc != TDES_OK) return rc;
         held.push_back({tickets[i], lo, hi});
@@ -546,6 +733,147 @@ int tdes_serve_loadtest(tdes_server_t* s, const tdes_loadtest_config_t* c,
     res->small_p99_ms = percentile(lat_s, 0.99);
     res->large_p50_ms = percentile(lat_l, 0.50);
     res->large_p99_ms = percentile(lat_l, 0.99);
+    tdes_server_stats_t st;
+    tdes_server_stats(s, 0, &st);
+    res->max_slots_busy = st.max_slots_busy;
+    res->max_device_overlap = st.max_device_overlap;
+    res->device_overlap_frac = st.device_busy_ms > 0 ? st.device_overlap_ms / st.device_busy_ms : 0.0;
+    return TDES_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- autotuning
+
+namespace {
+
+// Median closed-loop GB/s of `runs` load tests of a fresh server in cfg
+// (after a warm-up of a tenth of the requests).
+int serve_gbps(const tdes_keytable_t* kt, const tdes_server_config_t& cfg,
+               const tdes_loadtest_config_t& load, int runs, double* gbps) {
+    tdes_server_t* s = nullptr;
+    int rc = tdes_server_create(kt, &cfg, &s);
+    if (rc != TDES_OK) return rc;
+    tdes_loadtest_config_t c = load;
+    tdes_loadtest_result_t r;
+    c.offered_gbps = 0.0;
+    c.n_requests = std::max<uint64_t>(1, load.n_requests / 10);
+    rc = tdes_serve_loadtest(s, &c, &r);
+    std::vector<double> v;
+    c.n_requests = load.n_requests;
+    for (int i = 0; i < runs && rc == TDES_OK; ++i) {
+        c.seed = load.seed + 1 + (uint64_t)i;
+        rc = tdes_serve_loadtest(s, &c, &r);
+        v.push_back(r.gbps);
+    }
+    tdes_server_destroy(s);
+    if (rc != TDES_OK) return rc;
+    std::sort(v.begin(), v.end());
+    *gbps = v[v.size() / 2];
+    return TDES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t* load,
+                         unsigned flags, tdes_server_autotune_result_t* res) {
+    if (kt == nullptr || load == nullptr || res == nullptr) return sfail(TDES_EINVAL, "NULL argument");
+    memset(res, 0, sizeof *res);
+    int dev = -1, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return scuda(e, "device query");
+    const std::string key = tdes::serve_tune_key(sms);
+    snprintf(res->key, sizeof res->key, "%s", key.c_str());
+    // the built-in defaults, not a cached choice
+    tdes_server_config_t base;
+    tdes_server_config_default(&base);
+    base.warps_per_cta = 4;
+    base.reserve_ctas_per_sm = 1;
+    base.slots = 4;
+    res->baseline = base;
+    tdes::TunedShape cached;
+    if (!(flags & TDES_TUNE_FORCE) && tdes::tune_lookup(key, &cached)) {
+        tdes_server_config_default(&res->best);
+        res->best_gbps = cached.gbps;
+        res->baseline_gbps = cached.baseline_gbps;
+        res->from_cache = 1;
+        return TDES_OK;
+    }
+    const int runs = 3;
+    tdes_server_config_t best = base;
+    double best_gbps = 0.0;
+    int rc = serve_gbps(kt, best, *load, runs, &best_gbps);
+    if (rc != TDES_OK) return rc;
+    uint32_t timed = 1;
+    auto consider = [&](tdes_server_config_t t) -> int {
+        if (t.warps_per_cta == best.warps_per_cta && t.reserve_ctas_per_sm == best.reserve_ctas_per_sm &&
+            t.slots == best.slots)
+            return TDES_OK;
+        double g = 0.0;
+        const int r = serve_gbps(kt, t, *load, runs, &g);
+        if (r != TDES_OK) return r;
+        ++timed;
+        if (g > best_gbps) {
+            best = t;
+            best_gbps = g;
+        }
+        return TDES_OK;
+    };
+    for (int w : {2, 4, 8}) {
+        tdes_server_config_t t = best;
+        t.warps_per_cta = w;
+        if ((rc = consider(t)) != TDES_OK) return rc;
+    }
+    for (int r : {0, 1, 2}) {
+        tdes_server_config_t t = best;
+        t.reserve_ctas_per_sm = r;
+        if ((rc = consider(t)) != TDES_OK) return rc;
+    }
+    for (uint32_t k : {2u, 4u, 8u}) {
+        tdes_server_config_t t = best;
+        t.slots = k;
+        if ((rc = consider(t)) != TDES_OK) return rc;
+    }
+    // the winner against the default, alternating
+    double base_gbps = best_gbps;
+    const bool differs = best.warps_per_cta != base.warps_per_cta ||
+                         best.reserve_ctas_per_sm != base.reserve_ctas_per_sm ||
+                         best.slots != base.slots;
+    if (differs) {
+        std::vector<double> gb, gt;
+        for (int i = 0; i < 3; ++i) {
+            double x = 0.0;
+            if ((rc = serve_gbps(kt, base, *load, 1, &x)) != TDES_OK) return rc;
+            gb.push_back(x);
+            if ((rc = serve_gbps(kt, best, *load, 1, &x)) != TDES_OK) return rc;
+            gt.push_back(x);
+        }
+        std::sort(gb.begin(), gb.end());
+        std::sort(gt.begin(), gt.end());
+        base_gbps = gb[1];
+        best_gbps = gt[1];
+        if (!(best_gbps > base_gbps)) {
+            best = base;
+            best_gbps = base_gbps;
+        }
+    }
+    res->best = best;
+    res->best_gbps = best_gbps;
+    res->baseline_gbps = base_gbps;
+    res->candidates = timed;
+    if (!(flags & TDES_TUNE_NO_STORE)) {
+        tdes::TunedShape t;
+        t.shape.warps = best.warps_per_cta;
+        t.shape.ctas_per_sm = best.reserve_ctas_per_sm;
+        t.slots = (int)best.slots;
+        t.gbps = best_gbps;
+        t.baseline_gbps = base_gbps;
+        rc = tdes::tune_store(key, t);
+        if (rc != TDES_OK) return rc;
+    }
     return TDES_OK;
 }
 

@@ -30,12 +30,21 @@ EXPORTED = (
     "tdes_ctr_crypt", "tdes_cbc_decrypt", "tdes_cbc_encrypt", "tdes_cbc_decrypt_noalloc",
     "tdes_ecb_crypt_host", "tdes_keytable_create", "tdes_keytable_free", "tdes_batch_plan",
     "tdes_batch_configure", "tdes_batch_launch", "tdes_batch_launch_graph", "tdes_batch_info",
-    "tdes_batch_free", "tdes_uniform_scratch_bytes", "tdes_uniform_crypt", "tdes_uniform_info",
+    "tdes_batch_free", "tdes_batch_set_shape", "tdes_batch_get_shape", "tdes_batch_autotune",
+    "tdes_autotune_cache_path", "tdes_ctx_config_default", "tdes_ctx_create", "tdes_ctx_destroy",
+    "tdes_batch_submit", "tdes_batch_submit_plan", "tdes_batch_poll", "tdes_batch_wait",
+    "tdes_batch_release", "tdes_uniform_scratch_bytes", "tdes_uniform_crypt", "tdes_uniform_info",
     "tdes_server_config_default", "tdes_server_create", "tdes_server_submit",
     "tdes_server_poll", "tdes_server_wait", "tdes_server_submit_group",
     "tdes_server_poll_group", "tdes_server_wait_group", "tdes_server_destroy", "tdes_serve_loadtest",
+    "tdes_server_stats", "tdes_server_autotune",
     "tdes_sbox_gate_count", "tdes_set_small_cutoff", "tdes_strerror", "tdes_last_error",
 )
+
+TUNE_FORCE = 1
+TUNE_NO_STORE = 2
+ROUNDS_PER_PASS = 0
+ROUNDS_COMPACT = 1
 
 MODE_ECB_ENCRYPT = 0
 MODE_ECB_DECRYPT = 1
@@ -75,7 +84,24 @@ class LoadtestResult(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "p50_ms", "p90_ms", "p99_ms", "p999_ms", "mean_ms", "max_ms", "small_p50_ms",
         "small_p99_ms", "large_p50_ms", "large_p99_ms", "gbps", "offered_gbps", "duration_s")] + [
-        ("requests", ctypes.c_uint64), ("bytes", ctypes.c_uint64), ("batches", ctypes.c_uint64)]
+        ("requests", ctypes.c_uint64), ("bytes", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+        ("max_slots_busy", ctypes.c_uint32), ("max_device_overlap", ctypes.c_uint32),
+        ("device_overlap_frac", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    """tdes_server_stats_t"""
+    _fields_ = [("batches", ctypes.c_uint64), ("max_slots_busy", ctypes.c_uint32),
+                ("max_device_overlap", ctypes.c_uint32), ("device_busy_ms", ctypes.c_double),
+                ("device_overlap_ms", ctypes.c_double), ("batch_ms_sum", ctypes.c_double),
+                ("untimed_batches", ctypes.c_uint64)]
+
+
+class ServerAutotuneResult(ctypes.Structure):
+    """tdes_server_autotune_result_t"""
+    _fields_ = [("key", ctypes.c_char * 64), ("best", ServerConfig), ("baseline", ServerConfig),
+                ("best_gbps", ctypes.c_double), ("baseline_gbps", ctypes.c_double),
+                ("candidates", ctypes.c_uint32), ("from_cache", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -83,7 +109,30 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("n_cbc_enc_messages", ctypes.c_uint32), ("n_tiles", ctypes.c_uint64),
                 ("n_small_items", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("bytes_per_mode", ctypes.c_uint64 * 5),
-                ("n_mixed_tiles", ctypes.c_uint64), ("n_direct_messages", ctypes.c_uint32)]
+                ("n_mixed_tiles", ctypes.c_uint64), ("n_direct_messages", ctypes.c_uint32),
+                ("tiles_per_claim", ctypes.c_int), ("round_form", ctypes.c_int),
+                ("tuned", ctypes.c_int)]
+
+
+class LaunchShape(ctypes.Structure):
+    """tdes_launch_shape_t"""
+    _fields_ = [("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("tiles_per_claim", ctypes.c_int), ("round_form", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class AutotuneResult(ctypes.Structure):
+    """tdes_autotune_result_t"""
+    _fields_ = [("key", ctypes.c_char * 64), ("best", LaunchShape), ("baseline", LaunchShape),
+                ("best_ms", ctypes.c_double), ("baseline_ms", ctypes.c_double),
+                ("candidates", ctypes.c_uint32), ("from_cache", ctypes.c_int)]
+
+
+class CtxConfig(ctypes.Structure):
+    """tdes_ctx_config_t"""
+    _fields_ = [("streams", ctypes.c_uint32)]
 
 class UniformInfo(ctypes.Structure):
     """tdes_uniform_info_t"""
@@ -135,6 +184,22 @@ def load(path: str = LIB_PATH):
     lib.tdes_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     lib.tdes_batch_free.argtypes = [vp]
     lib.tdes_batch_free.restype = None
+    lib.tdes_batch_set_shape.argtypes = [vp, ctypes.POINTER(LaunchShape)]
+    lib.tdes_batch_get_shape.argtypes = [vp, ctypes.POINTER(LaunchShape)]
+    lib.tdes_batch_autotune.argtypes = [vp, ctypes.c_uint, ctypes.c_int, vp,
+                                        ctypes.POINTER(AutotuneResult)]
+    lib.tdes_autotune_cache_path.argtypes = []
+    lib.tdes_autotune_cache_path.restype = ctypes.c_char_p
+    lib.tdes_ctx_config_default.argtypes = [ctypes.POINTER(CtxConfig)]
+    lib.tdes_ctx_config_default.restype = None
+    lib.tdes_ctx_create.argtypes = [vp, ctypes.POINTER(CtxConfig), ctypes.POINTER(vp)]
+    lib.tdes_ctx_destroy.argtypes = [vp]
+    lib.tdes_ctx_destroy.restype = None
+    lib.tdes_batch_submit.argtypes = [vp, vp, u32, ctypes.POINTER(u64)]
+    lib.tdes_batch_submit_plan.argtypes = [vp, vp, ctypes.POINTER(u64)]
+    lib.tdes_batch_poll.argtypes = [vp, u64, vp]
+    lib.tdes_batch_wait.argtypes = [vp, u64, u64]
+    lib.tdes_batch_release.argtypes = [vp, u64]
     lib.tdes_uniform_scratch_bytes.argtypes = [vp, u64, u64, ctypes.POINTER(sz)]
     lib.tdes_uniform_crypt.argtypes = [vp, vp, vp, vp, vp, vp, u64, u64, vp, sz, vp, vp]
     lib.tdes_uniform_info.argtypes = [vp, ctypes.POINTER(UniformInfo)]
@@ -151,6 +216,9 @@ def load(path: str = LIB_PATH):
     lib.tdes_server_destroy.restype = None
     lib.tdes_serve_loadtest.argtypes = [vp, ctypes.POINTER(LoadtestConfig),
                                         ctypes.POINTER(LoadtestResult)]
+    lib.tdes_server_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ServerStats)]
+    lib.tdes_server_autotune.argtypes = [vp, ctypes.POINTER(LoadtestConfig), ctypes.c_uint,
+                                         ctypes.POINTER(ServerAutotuneResult)]
     lib.tdes_sbox_gate_count.argtypes = []
     lib.tdes_set_small_cutoff.argtypes = [u64]
     lib.tdes_set_small_cutoff.restype = u64
@@ -403,7 +471,29 @@ class Batch:
         return {"n_cbc_enc_messages": bi.n_cbc_enc_messages, "n_tiles": bi.n_tiles,
                 "n_small_items": bi.n_small_items, "warps_per_cta": bi.warps_per_cta,
                 "ctas_per_sm": bi.ctas_per_sm, "bytes_per_mode": list(bi.bytes_per_mode),
-                "n_mixed_tiles": bi.n_mixed_tiles, "n_direct_messages": bi.n_direct_messages}
+                "n_mixed_tiles": bi.n_mixed_tiles, "n_direct_messages": bi.n_direct_messages,
+                "tiles_per_claim": bi.tiles_per_claim, "round_form": bi.round_form,
+                "tuned": bool(bi.tuned)}
+
+    def set_shape(self, warps_per_cta: int, ctas_per_sm: int = 0, tiles_per_claim: int = 0,
+                  round_form: int = ROUNDS_PER_PASS):
+        sh = LaunchShape(warps_per_cta, ctas_per_sm, tiles_per_claim, round_form)
+        _check(load().tdes_batch_set_shape(self.handle, ctypes.byref(sh)))
+
+    def shape(self) -> dict:
+        sh = LaunchShape()
+        _check(load().tdes_batch_get_shape(self.handle, ctypes.byref(sh)))
+        return sh.as_dict()
+
+    def autotune(self, reps: int = 5, flags: int = 0, stream=None) -> dict:
+        """tdes_batch_autotune: runs the batch's whole work repeatedly (its
+        outputs are rewritten each time)."""
+        r = AutotuneResult()
+        _check(load().tdes_batch_autotune(self.handle, flags, reps, _stream(stream),
+                                          ctypes.byref(r)))
+        return {"key": r.key.decode(), "best": r.best.as_dict(), "baseline": r.baseline.as_dict(),
+                "best_ms": r.best_ms, "baseline_ms": r.baseline_ms, "candidates": r.candidates,
+                "from_cache": bool(r.from_cache)}
 
     def free(self):
         if self.handle:
@@ -413,6 +503,74 @@ class Batch:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+def tdes_autotune_cache_path() -> str:
+    return load().tdes_autotune_cache_path().decode()
+
+
+class Ctx:
+    """Owns a tdes_ctx_t: batches submitted with a ticket, polled per
+    descriptor and waited on with a time limit (tdes_batch_submit / poll /
+    wait / release)."""
+
+    def __init__(self, kt: KeyTable, streams: int = 2):
+        lib = load()
+        cfg = CtxConfig()
+        lib.tdes_ctx_config_default(ctypes.byref(cfg))
+        cfg.streams = streams
+        h = ctypes.c_void_p()
+        _check(lib.tdes_ctx_create(kt.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self.kt = kt
+        self._counts = {}
+
+    def submit(self, entries) -> int:
+        """entries: (mode, key_index, iv_or_ctr, in, out, nbytes) each, or a
+        DESC_DTYPE array; returns the ticket."""
+        if isinstance(entries, np.ndarray):
+            descs = np.ascontiguousarray(entries, dtype=DESC_DTYPE)
+            n, addr = descs.shape[0], descs.ctypes.data
+        else:
+            descs, n = make_descs(entries)
+            addr = ctypes.addressof(descs)
+        t = ctypes.c_uint64()
+        _check(load().tdes_batch_submit(self.handle, addr, n, ctypes.byref(t)))
+        self._counts[t.value] = n
+        return t.value
+
+    def submit_plan(self, batch: "Batch") -> int:
+        t = ctypes.c_uint64()
+        _check(load().tdes_batch_submit_plan(self.handle, batch.handle, ctypes.byref(t)))
+        self._counts[t.value] = len(batch.status)
+        return t.value
+
+    def poll(self, ticket: int, count: int | None = None) -> tuple:
+        """(status, per-descriptor statuses) of a ticket."""
+        n = self._counts.get(ticket, 0) if count is None else count
+        st = np.zeros(max(1, n), dtype=np.int32)
+        r = int(load().tdes_batch_poll(self.handle, ticket, st.ctypes.data if n else None))
+        return r, st[:n]
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        return int(load().tdes_batch_wait(self.handle, ticket, int(timeout_s * 1e9)))
+
+    def release(self, ticket: int) -> int:
+        r = int(load().tdes_batch_release(self.handle, ticket))
+        if r == TDES_OK:
+            self._counts.pop(ticket, None)
+        return r
+
+    def close(self):
+        if self.handle:
+            load().tdes_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 
@@ -455,6 +613,27 @@ def tdes_uniform_info(scratch) -> dict:
     _check(load().tdes_uniform_info(_ptr(scratch), ctypes.byref(ui)))
     return {"skipped": ui.skipped, "key_tiles": ui.key_tiles, "mixed_slices": ui.mixed_slices,
             "chain_key_tiles": ui.chain_key_tiles, "chain_slices": ui.chain_slices}
+
+
+def loadtest_config(kt, in_pool, out_pool, n_requests, offered_gbps, seed=1, small_frac=0.8,
+                    small=(64, 4096), large=(64 << 10, 16 << 20), mode_probs=(1, 1, 1),
+                    n_keys=None) -> LoadtestConfig:
+    return LoadtestConfig(n_requests, offered_gbps, seed, small_frac, small[0], small[1],
+                          large[0], large[1], (ctypes.c_double * 3)(*mode_probs),
+                          kt.count if n_keys is None else n_keys, _ptr(in_pool),
+                          _nbytes(in_pool), _ptr(out_pool), _nbytes(out_pool))
+
+
+def tdes_server_autotune(kt, in_pool, out_pool, n_requests, flags=0, **mix) -> dict:
+    """tdes_server_autotune over closed-loop load tests of the given request
+    mix (the keyword arguments of Server.loadtest)."""
+    c = loadtest_config(kt, in_pool, out_pool, n_requests, 0.0, **mix)
+    r = ServerAutotuneResult()
+    _check(load().tdes_server_autotune(kt.handle, ctypes.byref(c), flags, ctypes.byref(r)))
+    cfg = lambda x: {f: getattr(x, f) for f, _ in ServerConfig._fields_}  # noqa: E731
+    return {"key": r.key.decode(), "best": cfg(r.best), "baseline": cfg(r.baseline),
+            "best_gbps": r.best_gbps, "baseline_gbps": r.baseline_gbps,
+            "candidates": r.candidates, "from_cache": bool(r.from_cache)}
 
 
 class Server:
@@ -508,13 +687,16 @@ class Server:
     def loadtest(self, in_pool, out_pool, n_requests, offered_gbps, seed=1, small_frac=0.8,
                  small=(64, 4096), large=(64 << 10, 16 << 20), mode_probs=(1, 1, 1),
                  n_keys=None) -> dict:
-        c = LoadtestConfig(n_requests, offered_gbps, seed, small_frac, small[0], small[1],
-                           large[0], large[1], (ctypes.c_double * 3)(*mode_probs),
-                           self.kt.count if n_keys is None else n_keys, _ptr(in_pool),
-                           _nbytes(in_pool), _ptr(out_pool), _nbytes(out_pool))
+        c = loadtest_config(self.kt, in_pool, out_pool, n_requests, offered_gbps, seed,
+                            small_frac, small, large, mode_probs, n_keys)
         r = LoadtestResult()
         _check(load().tdes_serve_loadtest(self.handle, ctypes.byref(c), ctypes.byref(r)))
         return {f: getattr(r, f) for f, _ in LoadtestResult._fields_}
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(load().tdes_server_stats(self.handle, int(bool(reset)), ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
 
     def close(self):
         if self.handle:

@@ -1,11 +1,18 @@
 import os
 import sys
+import tempfile
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+# The library reads its autotuner's cache of launch shapes from this file.  A
+# fresh one per test session keeps every test in the default shapes unless
+# the test itself tunes (and a user's own cache out of the results).
+os.environ["TDES_AUTOTUNE_CACHE"] = os.path.join(
+    tempfile.mkdtemp(prefix="tdes_tune_"), "autotune.jsonl")
 
 
 def pytest_configure(config):

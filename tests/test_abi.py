@@ -61,3 +61,29 @@ def test_argument_checks_without_device(lib):
     assert lib.tdes_ecb_crypt_host(None, 0, vp(8), vp(8), 8, vp(16), 1 << 20) == tdes.TDES_EINVAL
     assert lib.tdes_key_schedule(None, None, None, None) == tdes.TDES_EINVAL
     assert tdes.tdes_strerror(tdes.TDES_EINVAL) == "invalid argument"
+
+
+def test_oversized_calls_refused_without_device(lib):
+    """A call of 2^31 tiles of 8 KiB (16 TiB) is refused by the host checks,
+    before any device query, in every mode.  Run without a GPU: the pointers
+    are placeholders that nothing dereferences (the key-schedule handle is a
+    zeroed host buffer, never read before the size check), and no kernel can
+    launch here."""
+    fake_ks = ctypes.create_string_buffer(256)
+    ks = ctypes.addressof(fake_ks)
+    p, big = ctypes.c_void_p(1 << 20), (1 << 31) * 8192
+    calls = {
+        "ecb_encrypt": lambda: lib.tdes_ecb_encrypt(ks, p, p, big, None),
+        "ecb_decrypt": lambda: lib.tdes_ecb_decrypt(ks, p, p, big, None),
+        "ctr": lambda: lib.tdes_ctr_crypt(ks, 0, 0, p, p, big, None),
+        "cbc_decrypt": lambda: lib.tdes_cbc_decrypt(ks, 0, p, p, big, None),
+        "cbc_encrypt": lambda: lib.tdes_cbc_encrypt(ks, 0, p, p, big, None),
+        "cbc_decrypt_noalloc": lambda: lib.tdes_cbc_decrypt_noalloc(ks, 0, p, p, big, None),
+    }
+    for name, call in calls.items():
+        assert call() == tdes.TDES_EINVAL, name
+        assert "2^31 tiles" in lib.tdes_last_error().decode(), name
+    # the allocation-free call's in-place scratch limit is a host check too
+    rc = lib.tdes_cbc_decrypt_noalloc(ks, 0, p, p, tdes.TDES_NOALLOC_MAX_BYTES + 8192, None)
+    assert rc == tdes.TDES_EINVAL
+    assert "scratch limit" in lib.tdes_last_error().decode()

@@ -51,11 +51,12 @@ def _run(T, srv, reqs, keys):
 
 
 def test_server_results_match_oracle_and_alone(cuda_lib):
+    """16384 resident key triples, as in the serving workload."""
     T = cuda_lib
-    keys = synth.key_triples(21, 64)
+    keys = synth.key_triples(21, 16384)
     kt = T.KeyTable(keys)
     srv = T.Server(kt)
-    reqs = _requests(21, 400, 64, big_every=37)
+    reqs = _requests(21, 400, 16384, big_every=37)
     got = _run(T, srv, reqs, keys)
     for i, (r, g) in enumerate(zip(reqs, got)):
         want = _oracle(r["mode"], keys[r["key"]].tobytes(), r["iv"], r["data"])
@@ -144,6 +145,9 @@ def test_loadtest_reports(cuda_lib):
     assert r["gbps"] > 0
     sat = srv.loadtest(pool, out, 3000, 0.0, large=(64 << 10, 4 << 20))
     assert sat["gbps"] > 0
+    # at saturation the slots fill: batches are in flight and on the device together
+    assert sat["max_slots_busy"] >= 2 and sat["max_device_overlap"] >= 2, sat
+    assert 0.0 < sat["device_overlap_frac"] <= 1.0, sat
     srv.close()
 
 
@@ -168,4 +172,66 @@ def test_server_host_payloads(cuda_lib, staged):
     page = np.zeros(4096, dtype=np.uint8)
     with pytest.raises(T.TdesError):
         srv.submit(0, 0, 0, page, page)
+    srv.close()
+
+
+def test_requests_overlap_on_the_device(cuda_lib):
+    """Continuous batching: a large request (4 MiB of CBC encryption, one
+    serial chain of 2^19 blocks, about half a second) is submitted first and
+    200 small requests after it.  The small ones are dispatched into other
+    slots while the large one runs: all of them complete before it, at least
+    two batches are in flight and on the device at once (device intervals
+    from CUDA events), and every result equals the oracle.  Keys are drawn
+    from 16384 resident triples."""
+    T = cuda_lib
+    keys = synth.key_triples(24, 16384)
+    kt = T.KeyTable(keys)
+    srv = T.Server(kt, slots=4)
+    big_data = synth.random_bytes(2400, 4 << 20)
+    bx = torch.from_numpy(big_data).cuda()
+    by = torch.zeros_like(bx)
+    big_iv = synth.iv64(2400)
+    small = _requests(25, 200, 16384)
+    small = [r for r in small if r["data"].size <= 4096][:150]
+    ins = [torch.from_numpy(r["data"]).cuda() for r in small]
+    outs = [torch.empty_like(x) for x in ins]
+    torch.cuda.synchronize()
+    srv.stats(reset=True)
+    tb = srv.submit(4, 1234, big_iv, bx, by)
+    ts = [srv.submit(r["mode"], r["key"], r["iv"], x, y) for r, x, y in zip(small, ins, outs)]
+    for t in ts:
+        assert srv.wait(t, 30.0) == 0
+    assert srv.poll(tb) == 1, "the small requests waited for the large one"
+    assert srv.wait(tb, 60.0) == 0
+    st = srv.stats()
+    assert st["max_slots_busy"] >= 2, st
+    assert st["max_device_overlap"] >= 2, st
+    assert st["device_overlap_ms"] > 0.0, st
+    assert st["untimed_batches"] == 0, st
+    for r, y in zip(small, outs):
+        want = _oracle(r["mode"], keys[r["key"]].tobytes(), r["iv"], r["data"])
+        assert (y.cpu().numpy() == want).all()
+    want = oracle.tdes_cbc_encrypt(keys[1234].tobytes(), big_iv, big_data)
+    assert (by.cpu().numpy() == want).all()
+    srv.close()
+
+
+def test_idle_server_sleeps(cuda_lib):
+    """With nothing queued and nothing in flight the dispatcher sleeps on a
+    condition variable: an idle server uses almost no CPU time."""
+    import resource
+    import time
+    T = cuda_lib
+    kt = T.KeyTable(synth.key_triples(26, 4))
+    srv = T.Server(kt)
+    buf = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    assert srv.wait(srv.submit(0, 0, 0, buf, torch.empty_like(buf)), 10.0) == 0
+    time.sleep(0.05)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    time.sleep(0.5)
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    wall = time.perf_counter() - t0
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    assert cpu < 0.2 * wall, f"{cpu:.3f} s of CPU in {wall:.3f} s idle"
     srv.close()
