@@ -471,7 +471,10 @@ void tdes_server_config_default(tdes_server_config_t *cfg);
  * outlive it).  A dispatcher thread admits queued requests in arrival order
  * while the admitted bytes stay within the budget, plans each admitted group
  * into one persistent batch launch on a free slot, and records completions;
- * requests arriving while batches run go into the next free slot.  With
+ * requests arriving while batches run go into the next free slot.  A batch
+ * completes as a whole, so a CBC-encryption request of more than 512 blocks
+ * (one serial chain, about a microsecond per block) is batched alone and
+ * holds up no other request.  With
  * nothing queued and nothing in flight the dispatcher sleeps until a
  * submission; while batches are in flight it polls their events, yielding
  * for 50 us after its last progress and then napping (5 us doubling to

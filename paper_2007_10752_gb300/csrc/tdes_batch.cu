@@ -704,7 +704,7 @@ void build_plan(const tdes_desc_t* descs, uint32_t count, uint32_t key_count, in
     h->o_sl = take(pieces.size() * sizeof(SPiece));
     h->o_si = take(s_items.size() * sizeof(uint2));
     h->o_halo = take(h->needs_halo ? h->n_b_tiles * 8 : 0);
-    h->o_ctr = take(16 + 4 * kChainSlots);  // counter, C counter, chain slots: zeroed together
+    h->o_ctr = take(kCounterBytes);  // claim counters and chain slots: zeroed together
     h->image.assign(align16(off), 0);
     auto put = [&](size_t o, const void* src, size_t n) {
         if (n) memcpy(h->image.data() + o, src, n);
@@ -748,7 +748,8 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
     p.halo = h.needs_halo ? reinterpret_cast<uint64_t*>(base + h.o_halo) : nullptr;
     p.counter = reinterpret_cast<unsigned long long*>(base + h.o_ctr);
     p.c_counter = p.counter + 1;
-    p.chain_slot = reinterpret_cast<uint32_t*>(p.counter + 2);
+    p.tile_counter = p.counter + 2;
+    p.chain_slot = reinterpret_cast<uint32_t*>(p.counter + 4);
     return p;
 }
 
@@ -776,15 +777,6 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
     return cudaSuccess;
 }
 
-// A claimed tile takes a warp tens of microseconds at full occupancy, which
-// already hides its message search and key staging behind the other warps,
-// so claims are single tiles unless a batch has so many tiles (over 256 per
-// warp) that the atomic counter itself and the restaging become worth
-// amortising; the tail of a batch then costs at most one claim.
-uint32_t auto_tiles_per_claim(uint64_t n_tiles, uint64_t warps_total) {
-    return n_tiles > 256 * std::max<uint64_t>(1, warps_total) ? 4u : 1u;
-}
-
 cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool needs_halo,
                           const LaunchShape& shape, size_t dyn_smem, uint64_t max_ctas,
                           cudaStream_t s, bool counter_fresh) {
@@ -792,13 +784,18 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
     BatchParams p = p_in;
     const int warps = shape.warps;
     const uint64_t warps_total = std::max<uint64_t>(1, max_ctas * (uint64_t)warps);
-    p.b_chunk = shape.tiles_per_claim > 0 ? (uint32_t)shape.tiles_per_claim
-                                          : auto_tiles_per_claim(p.n_b_tiles, warps_total);
-    p.n_b_chunks = (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk;
+    // Fixed claims of tiles_per_claim tiles, or (0) guided claims: a warp
+    // takes ceil(remaining / (2 x warps)) tiles (at most kGuidedMaxTiles), so
+    // early claims are long runs of one message's tiles -- one key-table
+    // staging for many tiles -- and the last ones single tiles, which keeps
+    // the tail short (guided self-scheduling, Polychronopoulos and Kuck 1987).
+    p.b_chunk = shape.tiles_per_claim > 0 ? (uint32_t)shape.tiles_per_claim : 0u;
+    p.n_b_chunks = p.b_chunk ? (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk : 0;
+    p.guided_div = (uint32_t)std::min<uint64_t>(2 * warps_total, 1u << 30);
     total_items = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
     cudaError_t e = cudaSuccess;
     if (!counter_fresh) {
-        e = cudaMemsetAsync(p.counter, 0, 16 + 4 * kChainSlots, s);
+        e = cudaMemsetAsync(p.counter, 0, kCounterBytes, s);
         if (e != cudaSuccess) return e;
     }
     if (needs_halo && p.n_b_tiles) {
@@ -811,8 +808,9 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
         tdes_batch_mixed_kernel<<<grid, 32 * warps, dyn_smem, s>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (total_items == 0) return cudaSuccess;
-    const uint64_t want = (total_items + warps - 1) / (uint64_t)warps;
+    if (total_items == 0 && p.n_b_tiles == 0) return cudaSuccess;
+    const uint64_t work_units = total_items + (p.b_chunk ? 0 : p.n_b_tiles);
+    const uint64_t want = (work_units + warps - 1) / (uint64_t)warps;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
     const bool solo = p.n_c_solo != 0, compact = shape.round_form == 1;
     if (solo && compact)
@@ -1119,11 +1117,7 @@ int tdes_batch_info(const tdes_batch_t* b, tdes_batch_info_t* info) {
     info->n_direct_messages = (uint32_t)b->direct.size();
     info->warps_per_cta = b->shape.warps;
     info->ctas_per_sm = b->shape.ctas_per_sm;
-    info->tiles_per_claim = b->shape.tiles_per_claim > 0
-                                ? b->shape.tiles_per_claim
-                                : (int)tdes::auto_tiles_per_claim(
-                                      b->params.n_b_tiles,
-                                      (uint64_t)b->sms * b->shape.ctas_per_sm * b->shape.warps);
+    info->tiles_per_claim = b->shape.tiles_per_claim;
     info->round_form = b->shape.round_form;
     info->tuned = b->tuned ? 1 : 0;
     for (int i = 0; i < 5; ++i) info->bytes_per_mode[i] = b->bytes[i];

@@ -23,6 +23,10 @@ namespace tdes {
 
 constexpr int kPackedWords = 104;  // 3328 table words at one bit each
 constexpr int kChainSlots = 1024;  // SM sub-partitions tracked for C items (4 per SM)
+// A plan's claim counters, zeroed together: the item counter, the C-item
+// counter, the B-tile counter of guided claims, padding, then the chain slots.
+constexpr int kCounterBytes = 32 + 4 * kChainSlots;
+constexpr uint32_t kGuidedMaxTiles = 128;  // largest guided claim
 
 // One slice (bit position) of a mixed-key tile: up to 32 blocks of small
 // messages under one key and direction, one block per lane.
@@ -74,9 +78,11 @@ struct BatchParams {
     uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
     unsigned long long* counter;   // claims of B and S items (and C items, see below)
     unsigned long long* c_counter; // claims of C items by warps on an SMSP without one
+    unsigned long long* tile_counter; // guided claims of B tiles
     uint32_t* chain_slot;          // [kChainSlots]: 1 while an SMSP runs a C item
-    uint32_t b_chunk;          // B tiles per claimed item (set at launch)
-    uint64_t n_b_chunks;       // ceil(n_b_tiles / b_chunk)
+    uint32_t b_chunk;          // B tiles per claimed item; 0: guided claims (set at launch)
+    uint64_t n_b_chunks;       // ceil(n_b_tiles / b_chunk); 0 with guided claims
+    uint32_t guided_div;       // guided claims take ceil(remaining / guided_div) tiles
 };
 
 
@@ -97,7 +103,7 @@ struct DirectMsg {
 struct LaunchShape {
     int warps = 8;             // warps per CTA, 1..8 (each owns a 13 KB shared-memory slice)
     int ctas_per_sm = 0;       // resident CTAs per SM for the grid; <= 0: as many as fit
-    int tiles_per_claim = 0;   // 1024-block tiles a warp claims at once; 0: automatic
+    int tiles_per_claim = 0;   // 1024-block tiles a warp claims at once; 0: guided
     int round_form = 0;        // 0: three loop bodies (one per DES pass); 1: one compact body
 };
 
@@ -138,9 +144,7 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit);
 cudaError_t enqueue_batch(const BatchParams& p, uint64_t total_items, bool needs_halo,
                           const LaunchShape& shape, size_t dyn_smem, uint64_t max_ctas,
                           cudaStream_t s, bool counter_fresh = false);
-// Tiles per claim that a shape's 0 (automatic) stands for, for a plan of
-// n_tiles tiles run by warps_total warps.
-uint32_t auto_tiles_per_claim(uint64_t n_tiles, uint64_t warps_total);
+
 // The single-key kernel launches of a plan's direct messages on s (before
 // its batch launches; each uses the whole GPU).
 cudaError_t enqueue_direct(const std::vector<DirectMsg>& direct, const tdes_keytable* kt,

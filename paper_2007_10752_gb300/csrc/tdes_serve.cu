@@ -78,7 +78,17 @@ struct Pending {
     uint64_t ticket;
     uint64_t cost;
     bool stage;  // host buffers, large enough to be staged through the device
+    bool alone;  // a long serial chain: batched on its own (see lone_request)
 };
+
+// A CBC-encryption request of more than 512 blocks is one serial chain that
+// a warp walks at about a microsecond per block.  A batch completes as a
+// whole, so requests batched with it would wait for it: it gets a batch of
+// its own instead.
+constexpr uint64_t kLoneChainBlocks = 512;
+bool lone_request(const tdes_desc_t& d) {
+    return d.mode == TDES_MODE_CBC_ENCRYPT && d.nbytes / 8 > kLoneChainBlocks;
+}
 
 struct StagedCopy {
     void* dst;
@@ -249,9 +259,12 @@ struct tdes_server {
                     std::lock_guard<std::mutex> lock(mu);
                     while (!queue.empty() && take.size() < cfg.max_batch &&
                            admitted + cost + queue.front().cost <= cfg.budget_bytes) {
+                        const bool alone = queue.front().alone;
+                        if (alone && !take.empty()) break;  // it starts the next batch
                         cost += queue.front().cost;
                         take.push_back(queue.front());
                         queue.pop_front();
+                        if (alone) break;
                     }
                 }
                 if (take.empty()) break;
@@ -465,7 +478,7 @@ int tdes_server_submit(tdes_server_t* s, const tdes_desc_t* req, uint64_t* ticke
         if (req->nbytes == 0) {
             s->complete(t, TDES_OK, now_ns());
         } else {
-            s->queue.push_back({*req, t, cost, s->wants_stage(*req)});
+            s->queue.push_back({*req, t, cost, s->wants_stage(*req), lone_request(*req)});
             s->cv_work.notify_one();
             return TDES_OK;
         }
@@ -514,7 +527,8 @@ int tdes_server_submit_group(tdes_server_t* s, const tdes_desc_t* reqs, uint32_t
             if (reqs[i].nbytes == 0)
                 s->complete(t0 + i, TDES_OK, now_ns());
             else
-                s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i]), s->wants_stage(reqs[i])});
+                s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i]), s->wants_stage(reqs[i]),
+                                    lone_request(reqs[i])});
         }
         s->cv_work.notify_one();
     }

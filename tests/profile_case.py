@@ -1,15 +1,16 @@
-"""A small, self-contained launch sequence for profiler captures.
+"""A small, self-contained launch sequence for profiler captures (test and
+measurement infrastructure, not part of the library).
 
 Runs `--launches` back-to-back launches of one kernel of the library on a
 seeded buffer of `--mib` MiB (default 256 MiB: larger than the 129 MB L2, a
 few hundred MB on the device) and exits.  Used as the target of ncu
 captures, whose commands are recorded beside their summaries in profiles/.
 
-  python -m paper_2007_10752_gb300.profile_case --kernel ecb --mib 256 --launches 3
-  python -m paper_2007_10752_gb300.profile_case --kernel batch --launches 3
-  python -m paper_2007_10752_gb300.profile_case --kernel batch_ctr --mib 256   (one CTR message as a batch)
-  python -m paper_2007_10752_gb300.profile_case --kernel ecb --des   (single-DES schedule)
-  python -m paper_2007_10752_gb300.profile_case --kernel uniform --msgs 268435456 --keys 65536
+  python tests/profile_case.py --kernel ecb --mib 256 --launches 3
+  python tests/profile_case.py --kernel batch --launches 3
+  python tests/profile_case.py --kernel batch_ctr --mib 256   (one CTR message as a batch)
+  python tests/profile_case.py --kernel ecb --des   (single-DES schedule)
+  python tests/profile_case.py --kernel uniform --msgs 268435456 --keys 65536
       (tdes_uniform_crypt: 64-byte messages in place, the second half of the
        large streaming workload; every kernel of the call, --launches calls)
 """
@@ -19,7 +20,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))  # the repository
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
