@@ -481,6 +481,51 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t* wtab = reinterpret_cast<uint32_t*>(g_dyn + (size_t)warp * kWarpSmemBytes);
     uint32_t staged = ~0u;  // (key << 1 | dir) of the table in wtab
+    // B tiles [t0, t1): the plan maps each tile to its message entry; the
+    // warp restages its key table only when the key or direction changes
+    auto run_tiles = [&](uint64_t t0, uint64_t t1) {
+        for (uint64_t t = t0; t < t1; ++t) {
+            const uint32_t lo = p.b_tile[t];
+            const BatchMsg* mp = p.msgs + p.b_msg[lo];
+            const uint32_t key = mp->key, dir = (uint32_t)dir_of(mp->mode);
+            const uint32_t want = (key << 1) | dir;
+            const bool one_pass = p.keystages[key] == 1;
+            if (want != staged) {
+                __syncwarp();
+                const uint4* src = reinterpret_cast<const uint4*>(
+                    p.keytab + (uint64_t)key * kPerKeyWords + TDES_TABLE_WORDS * dir);
+                const int n4 = (one_pass ? TDES1_TABLE_WORDS : TDES_TABLE_WORDS) / 4;
+                for (int i = lane; i < n4; i += 32)
+                    reinterpret_cast<uint4*>(wtab)[i] = __ldg(src + i);
+                __syncwarp();
+                staged = want;
+            }
+            batch_bs_tile<COMPACT>(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane, one_pass);
+        }
+    };
+    // With guided claims the B tiles are not in the item space: a warp runs
+    // them, claim by claim, after its last C item and before its first S item
+    // (or its exit), so chains still start first and small items come last.
+    bool guided_left = p.b_chunk == 0 && p.n_b_tiles != 0;
+    auto run_guided = [&]() {
+        for (;;) {
+            unsigned long long t0 = 0, t1 = 0;
+            if (lane == 0) {
+                const unsigned long long cur = __ldcg(p.tile_counter);
+                if (cur < p.n_b_tiles) {
+                    const unsigned long long rem = p.n_b_tiles - cur;
+                    unsigned long long k = (rem + p.guided_div - 1) / p.guided_div;
+                    k = k < 1 ? 1 : (k > kGuidedMaxTiles ? kGuidedMaxTiles : k);
+                    t0 = atomicAdd(p.tile_counter, k);
+                    t1 = min(t0 + k, (unsigned long long)p.n_b_tiles);
+                }
+            }
+            t0 = __shfl_sync(0xFFFFFFFFu, t0, 0);
+            t1 = __shfl_sync(0xFFFFFFFFu, t1, 0);
+            if (t0 >= t1) return;
+            run_tiles(t0, t1);
+        }
+    };
     const uint64_t total = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
     uint32_t slot = 0;
     bool solo_left = SOLO_SLOTS;
@@ -496,7 +541,7 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
         if (!SOLO_SLOTS) {
             if (lane == 0) item = atomicAdd(p.counter, 1ull);
             item = __shfl_sync(0xFFFFFFFFu, item, 0);
-            if (item >= total) break;
+            if (item >= total) item = ~0ull;
         } else {
             uint32_t gone = 0;
             item = ~0ull;
@@ -517,7 +562,6 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
             }
             item = __shfl_sync(0xFFFFFFFFu, item, 0);
             if (__shfl_sync(0xFFFFFFFFu, gone, 0)) solo_left = false;
-            if (item == ~0ull) break;
             slotted = item < p.n_c_solo;
         }
         if (item < p.n_c_items) {
@@ -526,29 +570,15 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
             staged = ~0u;
             continue;
         }
+        if (guided_left) {
+            guided_left = false;
+            run_guided();
+        }
+        if (item == ~0ull) break;
         item -= p.n_c_items;
-        if (item < p.n_b_chunks) {
-            // a run of b_chunk consecutive tiles; the plan maps each tile to
-            // its message entry
+        if (item < p.n_b_chunks) {  // fixed claims: a run of b_chunk consecutive tiles
             const uint64_t t0 = item * p.b_chunk;
-            for (uint64_t t = t0; t < min(t0 + p.b_chunk, p.n_b_tiles); ++t) {
-                const uint32_t lo = p.b_tile[t];
-                const BatchMsg* mp = p.msgs + p.b_msg[lo];
-                const uint32_t key = mp->key, dir = (uint32_t)dir_of(mp->mode);
-                const uint32_t want = (key << 1) | dir;
-                const bool one_pass = p.keystages[key] == 1;
-                if (want != staged) {
-                    __syncwarp();
-                    const uint4* src = reinterpret_cast<const uint4*>(
-                        p.keytab + (uint64_t)key * kPerKeyWords + TDES_TABLE_WORDS * dir);
-                    const int n4 = (one_pass ? TDES1_TABLE_WORDS : TDES_TABLE_WORDS) / 4;
-                    for (int i = lane; i < n4; i += 32)
-                        reinterpret_cast<uint4*>(wtab)[i] = __ldg(src + i);
-                    __syncwarp();
-                    staged = want;
-                }
-                batch_bs_tile<COMPACT>(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane, one_pass);
-            }
+            run_tiles(t0, min(t0 + p.b_chunk, p.n_b_tiles));
             continue;
         }
         item -= p.n_b_chunks;

@@ -58,6 +58,12 @@ struct Record {
     int first_error = TDES_OK;   // first rejected descriptor's status
     bool complete = false;
     int result = 1;              // once complete: TDES_OK, first_error or TDES_ECUDA
+    // The plan's host image, the source of its copy to the device.  It is
+    // pageable memory, which the copy may read when it runs on the stream (a
+    // GPU that addresses host memory directly, as on Grace, is not bound to
+    // stage it before cudaMemcpyAsync returns), so it lives until the batch
+    // is complete.
+    std::vector<uint8_t> image;
 };
 
 }  // namespace
@@ -111,6 +117,7 @@ struct tdes_ctx {
         const cudaError_t q = cudaEventQuery(r.done);
         if (q == cudaErrorNotReady) return;
         r.complete = true;
+        std::vector<uint8_t>().swap(r.image);
         r.result = q == cudaSuccess ? r.first_error : TDES_ECUDA;
         if (q != cudaSuccess) {
             cudaGetLastError();
@@ -158,7 +165,6 @@ int queue_plan(tdes_ctx* c, tdes::PlanHost& h, std::vector<int>&& status, uint64
         cudaError_t e = cudaSuccess;
         if (h.total_items) {
             e = cudaMallocAsync(&mem, h.image.size(), s);
-            // pageable source: the runtime copies it to staging before returning
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(mem, h.image.data(), h.image.size(), cudaMemcpyHostToDevice, s);
         }
@@ -175,10 +181,14 @@ int queue_plan(tdes_ctx* c, tdes::PlanHost& h, std::vector<int>&& status, uint64
         if (e == cudaSuccess) e = cudaEventRecord(done, s);
         if (e != cudaSuccess) {
             c->free_events.push_back(done);
-            return ccuda(e, "batch submission");
+            const int rc = ccuda(e, "batch submission");
+            cudaStreamSynchronize(s);  // whatever was queued has read the image before it goes
+            cudaGetLastError();
+            return rc;
         }
         r.done = done;
         r.stream = k;
+        r.image = std::move(h.image);
         c->last[k] = done;
     }
     const uint64_t t = c->next_ticket++;

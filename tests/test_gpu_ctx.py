@@ -170,3 +170,39 @@ def test_tickets_in_flight_together_and_planned_batch(cuda_lib):
             o, nb = int(offs[i]), int(lens[i])
             assert (got[o:o + nb] == want[o:o + nb]).all(), f"planned message {i}"
     ctx.close()
+
+
+def test_many_submissions_with_host_heap_churn(cuda_lib):
+    """Thirty batches submitted back to back while the host allocates and
+    frees memory between submissions: a plan's host image must stay intact
+    until its copy to the device has run (on a GPU that reads host memory
+    directly the copy may run after the call returns).  Every message against
+    the oracle."""
+    T = cuda_lib
+    seed, n_keys = 53, 17
+    keys = synth.key_triples(seed, n_keys)
+    kt = T.KeyTable(keys)
+    ctx = T.Ctx(kt, streams=3)
+    jobs, junk = [], []
+    for j in range(30):
+        lens, modes, kidx, ivs, offs, data = mixed_workload(seed + j, 60, 32 << 10, n_keys)
+        src = torch.from_numpy(data).cuda()
+        dst = torch.zeros_like(src)
+        ents = [(int(modes[i]), int(kidx[i]), int(ivs[i]), src.data_ptr() + int(offs[i]),
+                 dst.data_ptr() + int(offs[i]), int(lens[i])) for i in range(len(lens))]
+        torch.cuda.synchronize()
+        # src and dst stay referenced until the ticket completes: the context's
+        # streams are not ordered with torch's, whose allocator would hand a
+        # freed input to the next tensor while the batch still reads it
+        jobs.append((ctx.submit(ents), (lens, modes, kidx, ivs, offs, data), src, dst))
+        junk = [bytearray(b"\xa5" * (4096 + 64 * k)) for k in range(64)]  # reuse freed chunks
+    del junk
+    for t, w, src, dst in jobs:
+        assert ctx.wait(t, 60.0) == 0
+        lens, modes, kidx, ivs, offs, data = w
+        want = expected(keys, lens, modes, kidx, ivs, offs, data)
+        got = dst.cpu().numpy()
+        for i in range(len(lens)):
+            o, nb = int(offs[i]), int(lens[i])
+            assert (got[o:o + nb] == want[o:o + nb]).all(), f"ticket {t} message {i}"
+    ctx.close()
