@@ -796,8 +796,9 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
     hhalf = srv.loadtest(host_in, host_out, n_points // 2, 0.5 * hpeak["gbps"], seed=8)
     srv.close()
     del out_pool, host_in, host_out
-    tuned = {k: tune["best"][k] for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots")}
-    default = {k: tune["baseline"][k] for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots")}
+    keys = ("warps_per_cta", "reserve_ctas_per_sm", "slots", "round_form")
+    tuned = {k: tune["best"][k] for k in keys}
+    default = {k: tune["baseline"][k] for k in keys}
     return {"workload": SERVE_WORKLOAD, "peak_closed_loop_gbs": round(peak["gbps"], 2),
             "peak_p50_ms": round(peak["p50_ms"], 3),
             "peak_max_slots_busy": peak["max_slots_busy"],

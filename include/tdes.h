@@ -251,7 +251,7 @@ int tdes_batch_configure(tdes_batch_t *b, int warps_per_cta, int ctas_per_sm);
  * plan's whole launch shape.  A plan starts in the shape the autotuner's
  * cache holds for its workload class (see tdes_batch_autotune), else in the
  * default shape: 8 warps per CTA, as many CTAs as fit, automatic tiles per
- * claim, TDES_ROUNDS_PER_PASS.  Setting a shape drops the plan's captured
+ * claim, TDES_ROUNDS_COMPACT.  Setting a shape drops the plan's captured
  * graph, which tdes_batch_launch_graph then captures again. */
 int tdes_batch_set_shape(tdes_batch_t *b, const tdes_launch_shape_t *shape);
 int tdes_batch_get_shape(const tdes_batch_t *b, tdes_launch_shape_t *shape);
@@ -459,12 +459,14 @@ typedef struct {
                                 kernels over the host link (which gave the higher closed-loop
                                 throughput on a GB300) */
     uint64_t stage_min_bytes;
+    int round_form;          /* TDES_ROUNDS_PER_PASS or TDES_ROUNDS_COMPACT (batch kernel's rounds) */
 } tdes_server_config_t;
 
 /* Defaults: 8 GiB budget, 4 slots, 16384 requests per batch, 4 warps per CTA,
- * 1 CTA per SM reserved, 2^21 completion records -- except that slots, warps
- * per CTA and reserved CTAs come from the autotune cache when it has an
- * entry for the current device's SM count (tdes_server_autotune). */
+ * 1 CTA per SM reserved, 2^21 completion records, TDES_ROUNDS_PER_PASS --
+ * except that slots, warps per CTA, reserved CTAs and the round form come
+ * from the autotune cache when it has an entry for the current device's SM
+ * count (tdes_server_autotune). */
 void tdes_server_config_default(tdes_server_config_t *cfg);
 
 /* Starts a server on the current device over a key table (which must
@@ -474,11 +476,10 @@ void tdes_server_config_default(tdes_server_config_t *cfg);
  * requests arriving while batches run go into the next free slot.  A batch
  * completes as a whole, so a CBC-encryption request of more than 512 blocks
  * (one serial chain, about a microsecond per block) is batched alone and
- * holds up no other request.  With
- * nothing queued and nothing in flight the dispatcher sleeps until a
- * submission; while batches are in flight it polls their events, yielding
- * for 50 us after its last progress and then napping (5 us doubling to
- * 100 us, ended early by a submission). */
+ * holds up no other request.  For 200 us after its last progress (a batch
+ * dispatched or completed) the dispatcher polls without sleeping; after that
+ * it sleeps until a submission when nothing is in flight, and otherwise
+ * polls in naps (5 us doubling to 100 us, ended early by a submission). */
 int tdes_server_create(const tdes_keytable_t *kt, const tdes_server_config_t *cfg,
                        tdes_server_t **out);
 
@@ -559,8 +560,9 @@ int tdes_serve_loadtest(tdes_server_t *s, const tdes_loadtest_config_t *cfg,
 
 /* Overlap of a server's batches.  A batch is "in flight" from its dispatch
  * to the dispatcher's noticing its completion event, and "on the device"
- * from an event recorded on its slot's stream before its plan copy to one
- * after its last kernel (CUDA event times). */
+ * from the start of its first kernel's first CTA to the end of its last
+ * kernel's last warp: times the kernels read from the GPU's global timer
+ * and write to a ring of the last 2^20 batches (no per-batch host work). */
 typedef struct {
     uint64_t batches;            /* batches completed (and timed) since the last reset */
     uint32_t max_slots_busy;     /* most batches in flight at once */
@@ -568,7 +570,7 @@ typedef struct {
     double device_busy_ms;       /* time with at least one batch on the device */
     double device_overlap_ms;    /* time with two or more batches on the device */
     double batch_ms_sum;         /* sum of the batches' times on the device */
-    uint64_t untimed_batches;    /* batches whose events could not be read (errors) */
+    uint64_t untimed_batches;    /* batches that failed, or whose times the ring lost */
 } tdes_server_stats_t;
 
 /* Statistics since the server started or since the last call with reset != 0
@@ -577,8 +579,10 @@ typedef struct {
 int tdes_server_stats(tdes_server_t *s, int reset, tdes_server_stats_t *out);
 
 /* Autotuner of the server's shape (warps per CTA, CTAs per SM each batch
- * leaves free for the next, and slots): a coordinate search over warps 2, 4,
- * 8, reserved CTAs 0, 1, 2 and slots 2, 4, 8, each candidate the median
+ * leaves free for the next, slots, round form): a coordinate search over
+ * warps 2, 4, 8, reserved CTAs 1, 2 (at least one CTA per SM stays free so
+ * that a new batch can start while others run), slots 2, 4, 8 and the two
+ * round forms, each candidate the median
  * closed-loop GB/s of three tdes_serve_loadtest runs of `load` (its
  * offered_gbps is ignored: every request arrives at once) on a fresh server,
  * then the best against the built-in default (4 warps, 1 reserved CTA, 4

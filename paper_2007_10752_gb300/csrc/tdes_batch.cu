@@ -401,10 +401,32 @@ __device__ __forceinline__ void batch_mixed_tile(const BatchParams& p, uint32_t 
 // before the persistent kernel: inside it, their code slowed the persistent
 // kernel's other paths by 4% (alternating A/B runs on the 4096-message batch,
 // which has no mixed-key tiles).  Warps stride over the tiles.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Batch timing (when p.batch_times is set): the first CTA of the batch's
+// first kernel stamps the start; every warp of its last kernel counts itself
+// out as it leaves, and the last one stamps the end.
+__device__ __forceinline__ void stamp_start(const BatchParams& p) {
+    if (p.batch_times != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+        p.batch_times[0] = global_ns();
+}
+__device__ __forceinline__ void stamp_warp_done(const BatchParams& p, uint32_t lane) {
+    if (p.batch_times != nullptr && lane == 0) {
+        const uint32_t n = atomicAdd(p.done_warps, 1u) + 1u;
+        if (n == gridDim.x * (blockDim.x >> 5)) p.batch_times[1] = global_ns();
+    }
+}
+
 __global__ void __launch_bounds__(256, 2) tdes_batch_mixed_kernel(BatchParams p) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    stamp_start(p);
     for (uint32_t t = blockIdx.x * warps + warp; t < p.n_m_tiles; t += gridDim.x * warps)
         batch_mixed_tile(p, t, warp, lane);
+    if (p.times_end_in_mixed) stamp_warp_done(p, lane);
 }
 
 
@@ -472,6 +494,7 @@ __device__ __noinline__ void batch_cbc_enc_item(const BatchParams& p, uint32_t i
 // (batch_bs_tile).
 template <bool SOLO_SLOTS, bool COMPACT>
 __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
+    if (p.n_m_tiles == 0) stamp_start(p);  // else the mixed-key kernel ran first
     for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) g_st.sp[i] = (&kBatchSP[0][0])[i];
     for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) {
         g_st.ipn[i] = (&kBatchIPN[0][0])[i];
@@ -501,29 +524,6 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
                 staged = want;
             }
             batch_bs_tile<COMPACT>(mp, t - p.b_prefix[lo], t, wtab, p.halo, lane, one_pass);
-        }
-    };
-    // With guided claims the B tiles are not in the item space: a warp runs
-    // them, claim by claim, after its last C item and before its first S item
-    // (or its exit), so chains still start first and small items come last.
-    bool guided_left = p.b_chunk == 0 && p.n_b_tiles != 0;
-    auto run_guided = [&]() {
-        for (;;) {
-            unsigned long long t0 = 0, t1 = 0;
-            if (lane == 0) {
-                const unsigned long long cur = __ldcg(p.tile_counter);
-                if (cur < p.n_b_tiles) {
-                    const unsigned long long rem = p.n_b_tiles - cur;
-                    unsigned long long k = (rem + p.guided_div - 1) / p.guided_div;
-                    k = k < 1 ? 1 : (k > kGuidedMaxTiles ? kGuidedMaxTiles : k);
-                    t0 = atomicAdd(p.tile_counter, k);
-                    t1 = min(t0 + k, (unsigned long long)p.n_b_tiles);
-                }
-            }
-            t0 = __shfl_sync(0xFFFFFFFFu, t0, 0);
-            t1 = __shfl_sync(0xFFFFFFFFu, t1, 0);
-            if (t0 >= t1) return;
-            run_tiles(t0, t1);
         }
     };
     const uint64_t total = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
@@ -564,19 +564,15 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
             if (__shfl_sync(0xFFFFFFFFu, gone, 0)) solo_left = false;
             slotted = item < p.n_c_solo;
         }
+        if (item == ~0ull) break;
         if (item < p.n_c_items) {
             batch_cbc_enc_item(p, (uint32_t)item, warp, lane);
             if (SOLO_SLOTS && slotted && lane == 0) atomicExch(&p.chain_slot[slot], 0u);
             staged = ~0u;
             continue;
         }
-        if (guided_left) {
-            guided_left = false;
-            run_guided();
-        }
-        if (item == ~0ull) break;
         item -= p.n_c_items;
-        if (item < p.n_b_chunks) {  // fixed claims: a run of b_chunk consecutive tiles
+        if (item < p.n_b_chunks) {  // a run of b_chunk consecutive tiles
             const uint64_t t0 = item * p.b_chunk;
             run_tiles(t0, min(t0 + p.b_chunk, p.n_b_tiles));
             continue;
@@ -585,6 +581,7 @@ __global__ void __launch_bounds__(256, 2) tdes_batch_kernel(BatchParams p) {
         batch_scalar_item(p, p.s_items[item], warp, lane);
         staged = ~0u;
     }
+    stamp_warp_done(p, lane);
 }
 
 // In-place CBC decryption: save the ciphertext block before every B tile
@@ -778,8 +775,10 @@ BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt
     p.halo = h.needs_halo ? reinterpret_cast<uint64_t*>(base + h.o_halo) : nullptr;
     p.counter = reinterpret_cast<unsigned long long*>(base + h.o_ctr);
     p.c_counter = p.counter + 1;
-    p.tile_counter = p.counter + 2;
+    p.done_warps = reinterpret_cast<uint32_t*>(p.counter + 2);
     p.chain_slot = reinterpret_cast<uint32_t*>(p.counter + 4);
+    p.batch_times = nullptr;
+    p.times_end_in_mixed = false;
     return p;
 }
 
@@ -807,6 +806,15 @@ cudaError_t prepare_batch_kernel(int warps, size_t* dyn_smem, int* ctas_fit) {
     return cudaSuccess;
 }
 
+// A claimed tile takes a warp tens of microseconds at full occupancy, which
+// already hides its message search and key staging behind the other warps,
+// so claims are single tiles unless a batch has so many tiles (over 256 per
+// warp) that the atomic counter itself and the restaging become worth
+// amortising; the tail of a batch then costs at most one claim.
+uint32_t auto_tiles_per_claim(uint64_t n_tiles, uint64_t warps_total) {
+    return n_tiles > 256 * std::max<uint64_t>(1, warps_total) ? 4u : 1u;
+}
+
 cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool needs_halo,
                           const LaunchShape& shape, size_t dyn_smem, uint64_t max_ctas,
                           cudaStream_t s, bool counter_fresh) {
@@ -814,14 +822,9 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
     BatchParams p = p_in;
     const int warps = shape.warps;
     const uint64_t warps_total = std::max<uint64_t>(1, max_ctas * (uint64_t)warps);
-    // Fixed claims of tiles_per_claim tiles, or (0) guided claims: a warp
-    // takes ceil(remaining / (2 x warps)) tiles (at most kGuidedMaxTiles), so
-    // early claims are long runs of one message's tiles -- one key-table
-    // staging for many tiles -- and the last ones single tiles, which keeps
-    // the tail short (guided self-scheduling, Polychronopoulos and Kuck 1987).
-    p.b_chunk = shape.tiles_per_claim > 0 ? (uint32_t)shape.tiles_per_claim : 0u;
-    p.n_b_chunks = p.b_chunk ? (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk : 0;
-    p.guided_div = (uint32_t)std::min<uint64_t>(2 * warps_total, 1u << 30);
+    p.b_chunk = shape.tiles_per_claim > 0 ? (uint32_t)shape.tiles_per_claim
+                                          : auto_tiles_per_claim(p.n_b_tiles, warps_total);
+    p.n_b_chunks = (p.n_b_tiles + p.b_chunk - 1) / p.b_chunk;
     total_items = (uint64_t)p.n_c_items + p.n_b_chunks + p.n_s_items;
     cudaError_t e = cudaSuccess;
     if (!counter_fresh) {
@@ -832,15 +835,15 @@ cudaError_t enqueue_batch(const BatchParams& p_in, uint64_t total_items, bool ne
         tdes_batch_halo_kernel<<<(unsigned)((p.n_b_tiles + 255) / 256), 256, 0, s>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    p.times_end_in_mixed = total_items == 0;
     if (p.n_m_tiles) {  // small messages of their own keys: disjoint from the rest
         const uint64_t want = (p.n_m_tiles + warps - 1) / (uint64_t)warps;
         const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
         tdes_batch_mixed_kernel<<<grid, 32 * warps, dyn_smem, s>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (total_items == 0 && p.n_b_tiles == 0) return cudaSuccess;
-    const uint64_t work_units = total_items + (p.b_chunk ? 0 : p.n_b_tiles);
-    const uint64_t want = (work_units + warps - 1) / (uint64_t)warps;
+    if (total_items == 0) return cudaSuccess;
+    const uint64_t want = (total_items + warps - 1) / (uint64_t)warps;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(want, max_ctas));
     const bool solo = p.n_c_solo != 0, compact = shape.round_form == 1;
     if (solo && compact)
@@ -1053,15 +1056,12 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     // the autotuner's shape for this class of batch, if it has one; else the default
     tdes::TunedShape tuned;
     b->tuned = tdes::tune_lookup(tdes::tune_key(h, b->sms), &tuned);
-    tdes::LaunchShape shape;
-    shape.warps = tdes::kWideWarps;
+    tdes::LaunchShape shape;  // the default shape
     if (b->tuned) shape = tuned.shape;
     int rc = tdes::set_batch_shape(b, shape);
     if (rc != TDES_OK && b->tuned) {  // a cache entry this build cannot use
         b->tuned = false;
-        shape = tdes::LaunchShape();
-        shape.warps = tdes::kWideWarps;
-        rc = tdes::set_batch_shape(b, shape);
+        rc = tdes::set_batch_shape(b, tdes::LaunchShape());
     }
     if (rc != TDES_OK) {
         cudaFree(mem);
@@ -1147,7 +1147,11 @@ int tdes_batch_info(const tdes_batch_t* b, tdes_batch_info_t* info) {
     info->n_direct_messages = (uint32_t)b->direct.size();
     info->warps_per_cta = b->shape.warps;
     info->ctas_per_sm = b->shape.ctas_per_sm;
-    info->tiles_per_claim = b->shape.tiles_per_claim;
+    info->tiles_per_claim = b->shape.tiles_per_claim > 0
+                                ? b->shape.tiles_per_claim
+                                : (int)tdes::auto_tiles_per_claim(
+                                      b->params.n_b_tiles,
+                                      (uint64_t)b->sms * b->shape.ctas_per_sm * b->shape.warps);
     info->round_form = b->shape.round_form;
     info->tuned = b->tuned ? 1 : 0;
     for (int i = 0; i < 5; ++i) info->bytes_per_mode[i] = b->bytes[i];

@@ -24,9 +24,9 @@ namespace tdes {
 constexpr int kPackedWords = 104;  // 3328 table words at one bit each
 constexpr int kChainSlots = 1024;  // SM sub-partitions tracked for C items (4 per SM)
 // A plan's claim counters, zeroed together: the item counter, the C-item
-// counter, the B-tile counter of guided claims, padding, then the chain slots.
+// counter, the count of warps that have finished (batch timing), padding,
+// then the chain slots.
 constexpr int kCounterBytes = 32 + 4 * kChainSlots;
-constexpr uint32_t kGuidedMaxTiles = 128;  // largest guided claim
 
 // One slice (bit position) of a mixed-key tile: up to 32 blocks of small
 // messages under one key and direction, one block per lane.
@@ -78,11 +78,15 @@ struct BatchParams {
     uint64_t* halo;            // per B tile: ciphertext block before it (in-place CBC-dec)
     unsigned long long* counter;   // claims of B and S items (and C items, see below)
     unsigned long long* c_counter; // claims of C items by warps on an SMSP without one
-    unsigned long long* tile_counter; // guided claims of B tiles
     uint32_t* chain_slot;          // [kChainSlots]: 1 while an SMSP runs a C item
-    uint32_t b_chunk;          // B tiles per claimed item; 0: guided claims (set at launch)
-    uint64_t n_b_chunks;       // ceil(n_b_tiles / b_chunk); 0 with guided claims
-    uint32_t guided_div;       // guided claims take ceil(remaining / guided_div) tiles
+    uint32_t b_chunk;          // B tiles per claimed item (set at launch)
+    uint64_t n_b_chunks;       // ceil(n_b_tiles / b_chunk)
+    // Optional (nullable) device timestamps of the batch in ns of the GPU's
+    // global timer: [0] when its first kernel's first CTA starts, [1] when the
+    // last warp of its last kernel finishes (counted in *done_warps).
+    unsigned long long* batch_times;
+    uint32_t* done_warps;
+    bool times_end_in_mixed;   // the mixed-key kernel is the batch's last kernel
 };
 
 
@@ -99,12 +103,15 @@ struct DirectMsg {
     int stages;   // DES passes of the key (read from the key table at plan time)
 };
 
-// Launch shape of the batch kernels (the autotuner's search space).
+// Launch shape of the batch kernels (the autotuner's search space).  The
+// member defaults are a plan's default shape: on the 4096-message batch's
+// parallel modes, 8 warps with the compact round body measured 3.60 ms
+// against 3.78 ms with three loop bodies (median of 10 graph replays).
 struct LaunchShape {
     int warps = 8;             // warps per CTA, 1..8 (each owns a 13 KB shared-memory slice)
     int ctas_per_sm = 0;       // resident CTAs per SM for the grid; <= 0: as many as fit
-    int tiles_per_claim = 0;   // 1024-block tiles a warp claims at once; 0: guided
-    int round_form = 0;        // 0: three loop bodies (one per DES pass); 1: one compact body
+    int tiles_per_claim = 0;   // 1024-block tiles a warp claims at once; 0: automatic
+    int round_form = 1;        // 0: three loop bodies (one per DES pass); 1: one compact body
 };
 
 // A batch laid out on the host as the byte image of its device buffer.
@@ -132,6 +139,9 @@ int validate_desc(const tdes_desc_t& d, uint32_t key_count);
 // in-place CBC decryption) go to out->direct instead of batch tiles.
 void build_plan(const tdes_desc_t* d, uint32_t n, uint32_t key_count, int* status, PlanHost* out,
                 bool allow_direct = false);
+// Tiles per claim that a shape's 0 (automatic) stands for, for a plan of
+// n_tiles tiles run by warps_total warps.
+uint32_t auto_tiles_per_claim(uint64_t n_tiles, uint64_t warps_total);
 // Kernel parameters of a plan whose image was copied to dev_base.
 BatchParams bind_plan(const PlanHost& h, void* dev_base, const tdes_keytable* kt);
 // Sets the batch kernel's shared-memory limit for `warps` warps per CTA and

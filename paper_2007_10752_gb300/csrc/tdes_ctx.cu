@@ -142,8 +142,7 @@ int queue_plan(tdes_ctx* c, tdes::PlanHost& h, std::vector<int>&& status, uint64
         }
     for (tdes::DirectMsg& m : h.direct) m.stages = c->kt->host_stages[m.key];
     const bool work = h.total_items != 0 || !h.direct.empty();
-    tdes::LaunchShape shape;
-    shape.warps = tdes::kWideWarps;
+    tdes::LaunchShape shape;  // the default shape
     tdes::TunedShape tuned;
     if (work && tdes::tune_lookup(tdes::tune_key(h, c->sms), &tuned) && tuned.shape.warps >= 1 &&
         tuned.shape.warps <= 8 && tuned.shape.tiles_per_claim >= 0 &&

@@ -60,8 +60,8 @@ int64_t now_ns() {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t start = nullptr;  // before the batch's first operation on the stream
-    cudaEvent_t done = nullptr;   // after its last
+    cudaEvent_t done = nullptr;   // after the batch's last operation on the stream
+    uint64_t seq = 0;             // the batch's number (its entry of the time ring)
     void* dmem = nullptr;
     size_t dcap = 0;
     uint8_t* pinned = nullptr;
@@ -104,11 +104,19 @@ struct Completion {
 
 uint64_t cost_of(const tdes_desc_t& d) { return d.in == d.out ? d.nbytes : 2 * d.nbytes; }
 
-// A batch's time on the device: from the event before its plan copy to the
-// event after its last kernel, in ms since the server's base event.
+// After its last progress (a batch dispatched or completed) the dispatcher
+// polls without sleeping for this long before it sleeps or naps.
+constexpr int64_t kSpinNs = 200000;
+
+// A batch's time on the device: from its first kernel's first CTA starting
+// to its last kernel's last warp finishing, in ns of the GPU's global timer.
 struct Interval {
     double t0, t1;
 };
+
+// Device timestamps of the last kTimeRing batches: entry seq % kTimeRing
+// holds batch seq's [start, end] (written by its kernels, see BatchParams).
+constexpr uint64_t kTimeRing = 1u << 20;
 
 // Sweep over intervals: most at once, time with >= 1 and with >= 2.
 void sweep(std::vector<Interval> v, uint32_t* max_at_once, double* busy, double* overlap) {
@@ -158,12 +166,14 @@ struct tdes_server {
     std::condition_variable cv_done;
     std::atomic<int> waiters{0};
     // overlap statistics: batches in flight (dispatched, not complete) and
-    // every completed batch's device interval since the last reset
-    cudaEvent_t base = nullptr;
+    // the numbers of the batches completed since the last reset, whose device
+    // times the kernels wrote into times_ring
+    unsigned long long* times_ring = nullptr;
+    uint64_t next_seq = 0;  // dispatcher thread only
     std::mutex stats_mu;
     uint32_t busy_now = 0, max_busy = 0;
-    std::vector<Interval> intervals;
-    uint64_t interval_errors = 0;
+    std::vector<uint64_t> done_seqs;
+    uint64_t failed_batches = 0;
 
     void notify_done() {
         if (waiters.load(std::memory_order_acquire) == 0) return;
@@ -218,6 +228,7 @@ struct tdes_server {
         const uint64_t max_ctas = (uint64_t)sms * per_sm;
         tdes::LaunchShape shape;
         shape.warps = cfg.warps_per_cta;
+        shape.round_form = cfg.round_form;
         prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);  // naps below end within a microsecond
         int64_t last_progress = now_ns();
         int64_t nap_ns = 0;
@@ -240,15 +251,10 @@ struct tdes_server {
                 sl.busy = false;
                 worked = true;
                 completed_any = true;
-                float a = 0.f, b = 0.f;
-                const bool timed = st == TDES_OK &&
-                                   cudaEventElapsedTime(&a, base, sl.start) == cudaSuccess &&
-                                   cudaEventElapsedTime(&b, base, sl.done) == cudaSuccess;
-                if (!timed) cudaGetLastError();
                 std::lock_guard<std::mutex> lock(stats_mu);
                 --busy_now;
-                if (timed) intervals.push_back({(double)a, (double)b});
-                else ++interval_errors;
+                if (st == TDES_OK) done_seqs.push_back(sl.seq);
+                else ++failed_batches;
             }
             if (completed_any) notify_done();
             for (Slot& sl : slots) {
@@ -287,7 +293,6 @@ struct tdes_server {
                 tdes::build_plan(descs.data(), (uint32_t)descs.size(), kt->count, nullptr, &plan);
                 cudaError_t e = cudaSuccess;
                 if (!ensure_capacity(sl, plan.image.size())) e = cudaErrorMemoryAllocation;
-                if (e == cudaSuccess) e = cudaEventRecord(sl.start, sl.stream);
                 for (const StagedCopy& c : copy_in)
                     if (e == cudaSuccess)
                         e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyHostToDevice, sl.stream);
@@ -297,7 +302,9 @@ struct tdes_server {
                                         cudaMemcpyHostToDevice, sl.stream);
                 }
                 if (e == cudaSuccess) {  // the image just copied holds a zeroed claim counter
-                    const tdes::BatchParams p = tdes::bind_plan(plan, sl.dmem, kt);
+                    tdes::BatchParams p = tdes::bind_plan(plan, sl.dmem, kt);
+                    sl.seq = next_seq++;
+                    p.batch_times = times_ring + 2 * (sl.seq % kTimeRing);
                     e = tdes::enqueue_batch(p, plan.total_items, plan.needs_halo, shape,
                                             dyn_smem, max_ctas, sl.stream, true);
                 }
@@ -331,9 +338,18 @@ struct tdes_server {
                 nap_ns = 0;
                 continue;
             }
+            // For kSpinNs after its last progress the dispatcher only yields
+            // between polls: under load a new request or a completion is
+            // seldom further away, and waking a sleeping thread would add
+            // tens of microseconds to its latency.
+            if (now - last_progress < kSpinNs) {
+                lock.unlock();
+                std::this_thread::yield();
+                continue;
+            }
             if (!any_busy) {
-                // nothing in flight: the queue is empty (anything queued fits the
-                // empty budget), so sleep until a submission or the stop
+                // idle: the queue is empty (anything queued fits the empty
+                // budget), so sleep until a submission or the stop
                 cv_work.wait(lock, [&] {
                     return !queue.empty() || stop.load(std::memory_order_acquire);
                 });
@@ -341,14 +357,8 @@ struct tdes_server {
                 nap_ns = 0;
                 continue;
             }
-            // batches in flight: poll their events, yielding for the first
-            // 50 us after the last progress, then in naps of 5 us doubling up
-            // to 100 us; a submission ends a nap at once
-            if (now - last_progress < 50000) {
-                lock.unlock();
-                std::this_thread::yield();
-                continue;
-            }
+            // long batches in flight: poll their events in naps of 5 us
+            // doubling up to 100 us; a submission ends a nap at once
             nap_ns = nap_ns ? std::min<int64_t>(2 * nap_ns, 100000) : 5000;
             const size_t queued = queue.size();
             cv_work.wait_for(lock, std::chrono::nanoseconds(nap_ns), [&] {
@@ -398,6 +408,7 @@ void tdes_server_config_default(tdes_server_config_t* cfg) {
     cfg->ring_entries = 1u << 21;
     cfg->stage_bytes = 0;  // host payloads zero-copy by default: measured faster
     cfg->stage_min_bytes = 64ull << 10;
+    cfg->round_form = TDES_ROUNDS_PER_PASS;
     // the autotuner's choice for this GPU, if the cache has one
     int dev = -1, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -411,6 +422,7 @@ void tdes_server_config_default(tdes_server_config_t* cfg) {
         cfg->warps_per_cta = t.shape.warps;
         cfg->reserve_ctas_per_sm = t.shape.ctas_per_sm;
         cfg->slots = (uint32_t)t.slots;
+        if (t.shape.round_form == 0 || t.shape.round_form == 1) cfg->round_form = t.shape.round_form;
     }
 }
 
@@ -422,7 +434,8 @@ int tdes_server_create(const tdes_keytable_t* kt, const tdes_server_config_t* cf
     tdes_server_config_default(&cfg);
     if (cfg_in) cfg = *cfg_in;
     if (cfg.slots < 1 || cfg.slots > 64 || cfg.max_batch < 1 || cfg.warps_per_cta < 1 ||
-        cfg.warps_per_cta > 8 || cfg.ring_entries < 1024 || cfg.budget_bytes < 16)
+        cfg.warps_per_cta > 8 || cfg.ring_entries < 1024 || cfg.budget_bytes < 16 ||
+        cfg.round_form < 0 || cfg.round_form > 1)
         return sfail(TDES_EINVAL, "bad server configuration");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -437,18 +450,16 @@ int tdes_server_create(const tdes_keytable_t* kt, const tdes_server_config_t* cf
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
     e = tdes::prepare_batch_kernel(cfg.warps_per_cta, &s->dyn_smem, &s->ctas_fit);
     s->slots.resize(cfg.slots);
-    if (e == cudaSuccess) e = cudaEventCreate(&s->base);
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void**>(&s->times_ring), 2 * kTimeRing * sizeof(uint64_t));
     for (Slot& sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreate(&sl.start);
-        if (e == cudaSuccess) e = cudaEventCreate(&sl.done);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess && cfg.stage_bytes) {
             e = cudaMalloc(reinterpret_cast<void**>(&sl.stage), cfg.stage_bytes);
             if (e == cudaSuccess) sl.stage_cap = cfg.stage_bytes;
         }
     }
-    if (e == cudaSuccess) e = cudaEventRecord(s->base, s->slots[0].stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(s->base);
     if (e != cudaSuccess) {
         int rc = scuda(e, "server set-up");
         tdes_server_destroy(s);
@@ -562,17 +573,36 @@ int tdes_server_wait_group(tdes_server_t* s, uint64_t ticket, uint32_t count,
 
 int tdes_server_stats(tdes_server_t* s, int reset, tdes_server_stats_t* out) {
     if (s == nullptr || out == nullptr) return sfail(TDES_EINVAL, "NULL argument");
-    std::vector<Interval> iv;
+    std::vector<uint64_t> seqs;
     {
         std::lock_guard<std::mutex> lock(s->stats_mu);
-        iv = s->intervals;
+        seqs.swap(s->done_seqs);
         out->max_slots_busy = s->max_busy;
-        out->untimed_batches = s->interval_errors;
+        out->untimed_batches = s->failed_batches;
         if (reset) {
-            s->intervals.clear();
-            s->interval_errors = 0;
+            s->failed_batches = 0;
             s->max_busy = s->busy_now;
+        } else {
+            s->done_seqs = seqs;
         }
+    }
+    // only the last kTimeRing batches still have their times
+    if (seqs.size() > kTimeRing) {
+        out->untimed_batches += seqs.size() - kTimeRing;
+        seqs.erase(seqs.begin(), seqs.end() - kTimeRing);
+    }
+    std::vector<unsigned long long> ring;
+    if (!seqs.empty()) {
+        ring.resize(2 * kTimeRing);
+        const cudaError_t e = cudaMemcpy(ring.data(), s->times_ring, ring.size() * 8,
+                                         cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return scuda(e, "reading batch times");
+    }
+    std::vector<Interval> iv;
+    iv.reserve(seqs.size());
+    for (uint64_t q : seqs) {
+        const unsigned long long t0 = ring[2 * (q % kTimeRing)], t1 = ring[2 * (q % kTimeRing) + 1];
+        iv.push_back({(double)t0 * 1e-6, (double)std::max(t0, t1) * 1e-6});  // ms
     }
     out->batches = iv.size();
     double sum = 0.0;
@@ -590,16 +620,15 @@ void tdes_server_destroy(tdes_server_t* s) {
         s->cv_work.notify_all();
     }
     if (s->thread.joinable()) s->thread.join();
-    if (s->base) cudaEventDestroy(s->base);
     for (Slot& sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
-        if (sl.start) cudaEventDestroy(sl.start);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.dmem) cudaFree(sl.dmem);
         if (sl.pinned) cudaFreeHost(sl.pinned);
         if (sl.stage) cudaFree(sl.stage);
     }
+    if (s->times_ring) cudaFree(s->times_ring);
     delete s;
 }
 
@@ -807,6 +836,7 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
     base.warps_per_cta = 4;
     base.reserve_ctas_per_sm = 1;
     base.slots = 4;
+    base.round_form = TDES_ROUNDS_PER_PASS;
     res->baseline = base;
     tdes::TunedShape cached;
     if (!(flags & TDES_TUNE_FORCE) && tdes::tune_lookup(key, &cached)) {
@@ -824,7 +854,7 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
     uint32_t timed = 1;
     auto consider = [&](tdes_server_config_t t) -> int {
         if (t.warps_per_cta == best.warps_per_cta && t.reserve_ctas_per_sm == best.reserve_ctas_per_sm &&
-            t.slots == best.slots)
+            t.slots == best.slots && t.round_form == best.round_form)
             return TDES_OK;
         double g = 0.0;
         const int r = serve_gbps(kt, t, *load, runs, &g);
@@ -841,7 +871,11 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
         t.warps_per_cta = w;
         if ((rc = consider(t)) != TDES_OK) return rc;
     }
-    for (int r : {0, 1, 2}) {
+    // At least one CTA per SM stays free for the next batch: with none, a
+    // batch's kernels wait for the previous batch's CTAs to leave, which
+    // raised closed-loop throughput a little but p50 latency at 25% load
+    // by a fifth (8 warps, 8 slots: 57 against 47 us).
+    for (int r : {1, 2}) {
         tdes_server_config_t t = best;
         t.reserve_ctas_per_sm = r;
         if ((rc = consider(t)) != TDES_OK) return rc;
@@ -851,11 +885,16 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
         t.slots = k;
         if ((rc = consider(t)) != TDES_OK) return rc;
     }
+    {
+        tdes_server_config_t t = best;
+        t.round_form = 1 - best.round_form;
+        if ((rc = consider(t)) != TDES_OK) return rc;
+    }
     // the winner against the default, alternating
     double base_gbps = best_gbps;
     const bool differs = best.warps_per_cta != base.warps_per_cta ||
                          best.reserve_ctas_per_sm != base.reserve_ctas_per_sm ||
-                         best.slots != base.slots;
+                         best.slots != base.slots || best.round_form != base.round_form;
     if (differs) {
         std::vector<double> gb, gt;
         for (int i = 0; i < 3; ++i) {
@@ -882,6 +921,7 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
         tdes::TunedShape t;
         t.shape.warps = best.warps_per_cta;
         t.shape.ctas_per_sm = best.reserve_ctas_per_sm;
+        t.shape.round_form = best.round_form;
         t.slots = (int)best.slots;
         t.gbps = best_gbps;
         t.baseline_gbps = base_gbps;

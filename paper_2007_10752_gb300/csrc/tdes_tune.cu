@@ -245,8 +245,7 @@ int tdes_batch_autotune(tdes_batch_t* b, unsigned flags, int reps, tdes_stream_t
     memcpy(h.kind_bytes, b->kind_bytes, sizeof h.kind_bytes);
     const std::string key = tdes::tune_key(h, b->sms);
     snprintf(res->key, sizeof res->key, "%s", key.c_str());
-    tdes::LaunchShape base;
-    base.warps = tdes::kWideWarps;
+    tdes::LaunchShape base;  // the default shape
     {
         size_t dyn = 0;
         int fit = 1;

@@ -65,7 +65,8 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
                 ("max_batch", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int),
                 ("reserve_ctas_per_sm", ctypes.c_int), ("ring_entries", ctypes.c_uint32),
-                ("stage_bytes", ctypes.c_uint64), ("stage_min_bytes", ctypes.c_uint64)]
+                ("stage_bytes", ctypes.c_uint64), ("stage_min_bytes", ctypes.c_uint64),
+                ("round_form", ctypes.c_int)]
 
 
 class LoadtestConfig(ctypes.Structure):

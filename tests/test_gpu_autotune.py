@@ -96,7 +96,7 @@ def test_server_autotune_feeds_the_default_config(cuda_lib, cache):
     r = T.tdes_server_autotune(kt, pool, out, 400, large=(64 << 10, 1 << 20))
     assert not r["from_cache"] and r["candidates"] >= 4 and r["best_gbps"] > 0
     srv = T.Server(kt)  # default configuration: now the tuned one
-    for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots"):
+    for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots", "round_form"):
         assert srv.config[k] == r["best"][k], k
     res = srv.loadtest(pool, out, 300, 0.0, large=(64 << 10, 1 << 20))
     assert res["gbps"] > 0
