@@ -152,6 +152,7 @@ struct tdes_server {
     std::vector<Slot> slots;
     std::mutex mu;
     std::deque<Pending> queue;
+    std::atomic<size_t> queued{0};  // queue.size(), readable without the lock
     uint64_t next_ticket = 1;
     std::vector<Completion> ring;
     std::thread thread;
@@ -174,6 +175,14 @@ struct tdes_server {
     uint32_t busy_now = 0, max_busy = 0;
     std::vector<uint64_t> done_seqs;
     uint64_t failed_batches = 0;
+
+    // Clears the overlap statistics (cheap: no device read).
+    void reset_stats() {
+        std::lock_guard<std::mutex> lock(stats_mu);
+        done_seqs.clear();
+        failed_batches = 0;
+        max_busy = busy_now;
+    }
 
     void notify_done() {
         if (waiters.load(std::memory_order_acquire) == 0) return;
@@ -261,6 +270,7 @@ struct tdes_server {
                 if (sl.busy) continue;
                 take.clear();
                 uint64_t cost = 0;
+                if (queued.load(std::memory_order_acquire) == 0) break;  // nothing to take
                 {
                     std::lock_guard<std::mutex> lock(mu);
                     while (!queue.empty() && take.size() < cfg.max_batch &&
@@ -272,6 +282,7 @@ struct tdes_server {
                         queue.pop_front();
                         if (alone) break;
                     }
+                    queued.store(queue.size(), std::memory_order_release);
                 }
                 if (take.empty()) break;
                 descs.resize(take.size());
@@ -330,8 +341,12 @@ struct tdes_server {
                 std::lock_guard<std::mutex> lock(stats_mu);
                 max_busy = std::max(max_busy, ++busy_now);
             }
-            std::unique_lock<std::mutex> lock(mu);
-            if (stop.load(std::memory_order_acquire) && !any_busy && queue.empty()) break;
+            // The queue's lock is taken only to take requests (above) and to
+            // sleep (below): a dispatcher spinning on the lock slowed the
+            // submitting threads that share it.
+            if (stop.load(std::memory_order_acquire) && !any_busy &&
+                queued.load(std::memory_order_acquire) == 0)
+                break;
             const int64_t now = now_ns();
             if (worked) {
                 last_progress = now;
@@ -343,10 +358,11 @@ struct tdes_server {
             // seldom further away, and waking a sleeping thread would add
             // tens of microseconds to its latency.
             if (now - last_progress < kSpinNs) {
-                lock.unlock();
                 std::this_thread::yield();
                 continue;
             }
+            std::unique_lock<std::mutex> lock(mu);
+            if (stop.load(std::memory_order_acquire) && !any_busy && queue.empty()) break;
             if (!any_busy) {
                 // idle: the queue is empty (anything queued fits the empty
                 // budget), so sleep until a submission or the stop
@@ -360,9 +376,9 @@ struct tdes_server {
             // long batches in flight: poll their events in naps of 5 us
             // doubling up to 100 us; a submission ends a nap at once
             nap_ns = nap_ns ? std::min<int64_t>(2 * nap_ns, 100000) : 5000;
-            const size_t queued = queue.size();
+            const size_t waiting = queue.size();
             cv_work.wait_for(lock, std::chrono::nanoseconds(nap_ns), [&] {
-                return queue.size() != queued || stop.load(std::memory_order_acquire);
+                return queue.size() != waiting || stop.load(std::memory_order_acquire);
             });
         }
     }
@@ -490,6 +506,7 @@ int tdes_server_submit(tdes_server_t* s, const tdes_desc_t* req, uint64_t* ticke
             s->complete(t, TDES_OK, now_ns());
         } else {
             s->queue.push_back({*req, t, cost, s->wants_stage(*req), lone_request(*req)});
+            s->queued.store(s->queue.size(), std::memory_order_release);
             s->cv_work.notify_one();
             return TDES_OK;
         }
@@ -541,6 +558,7 @@ int tdes_server_submit_group(tdes_server_t* s, const tdes_desc_t* reqs, uint32_t
                 s->queue.push_back({reqs[i], t0 + i, cost_of(reqs[i]), s->wants_stage(reqs[i]),
                                     lone_request(reqs[i])});
         }
+        s->queued.store(s->queue.size(), std::memory_order_release);
         s->cv_work.notify_one();
     }
     s->notify_done();
@@ -591,11 +609,23 @@ int tdes_server_stats(tdes_server_t* s, int reset, tdes_server_stats_t* out) {
         out->untimed_batches += seqs.size() - kTimeRing;
         seqs.erase(seqs.begin(), seqs.end() - kTimeRing);
     }
+    // read back only the ring entries that hold these batches
     std::vector<unsigned long long> ring;
     if (!seqs.empty()) {
-        ring.resize(2 * kTimeRing);
-        const cudaError_t e = cudaMemcpy(ring.data(), s->times_ring, ring.size() * 8,
-                                         cudaMemcpyDeviceToHost);
+        ring.assign(2 * kTimeRing, 0ull);
+        const auto mm = std::minmax_element(seqs.begin(), seqs.end());
+        const uint64_t lo = *mm.first, hi = *mm.second;
+        auto fetch = [&](uint64_t a, uint64_t b) {  // ring entries [a, b]
+            return cudaMemcpy(ring.data() + 2 * a, s->times_ring + 2 * a, (b - a + 1) * 16,
+                              cudaMemcpyDeviceToHost);
+        };
+        cudaError_t e;
+        if (hi - lo + 1 >= kTimeRing) e = fetch(0, kTimeRing - 1);
+        else if (lo % kTimeRing <= hi % kTimeRing) e = fetch(lo % kTimeRing, hi % kTimeRing);
+        else {
+            e = fetch(lo % kTimeRing, kTimeRing - 1);
+            if (e == cudaSuccess) e = fetch(0, hi % kTimeRing);
+        }
         if (e != cudaSuccess) return scuda(e, "reading batch times");
     }
     std::vector<Interval> iv;
@@ -707,10 +737,9 @@ int tdes_serve_loadtest(tdes_server_t* s, const tdes_loadtest_config_t* c,
     std::deque<Held> held;
     uint64_t head = 0;
     std::vector<uint64_t> tickets(n);
+    s->reset_stats();  // overlap statistics of this run only (before the schedule starts)
     const int64_t t0 = now_ns() + 1000000;
     const uint64_t batches0 = s->batches.load();
-    tdes_server_stats_t st0;
-    tdes_server_stats(s, 1, &st0);  // overlap statistics of this run only
     for (uint64_t i = 0; i < n; ++i) {
         tdes_desc_t& d = reqs[i];
         if (head + d.nbytes > c->out_pool_bytes) head = 0;
