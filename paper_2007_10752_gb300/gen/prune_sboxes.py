@@ -91,9 +91,12 @@ def main(paths):
             c = best if p is None else json.load(open(p.format(g=g)))
             if not M.verify(g, c):
                 continue
+            prov = dict(c.get("provenance", {"recorded": False}))
             c = prune(g, c)
             if len(c["gates"]) < len(best["gates"]):
                 print(f"S{g + 1}: {len(best['gates'])} -> {len(c['gates'])}")
+                prov["pruned"] = True
+                c["provenance"] = prov
                 best = c
                 changed = True
         store["sboxes"][g] = best
