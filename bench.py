@@ -804,6 +804,11 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
             "peak_max_slots_busy": peak["max_slots_busy"],
             "peak_device_overlap_frac": round(peak["device_overlap_frac"], 4),
             "autotune": {"class": tune["key"], "tuned": tuned, "default": default,
+                         "objective": "p99 at a common offered load, closed-loop GB/s >= 97% "
+                                      "of the default's",
+                         "load_gbs": round(tune["load_gbps"], 2),
+                         "tuned_p99_ms": round(tune["best_p99_ms"], 4),
+                         "default_p99_ms": round(tune["baseline_p99_ms"], 4),
                          "tuned_gbs": round(tune["best_gbps"], 2),
                          "default_gbs": round(tune["baseline_gbps"], 2),
                          "candidates": tune["candidates"]},

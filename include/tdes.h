@@ -579,25 +579,28 @@ typedef struct {
 int tdes_server_stats(tdes_server_t *s, int reset, tdes_server_stats_t *out);
 
 /* Autotuner of the server's shape (warps per CTA, CTAs per SM each batch
- * leaves free for the next, slots, round form): a coordinate search over
- * warps 2, 4, 8, reserved CTAs 1, 2 (at least one CTA per SM stays free so
- * that a new batch can start while others run), slots 2, 4, 8 and the two
- * round forms, each candidate the median
- * closed-loop GB/s of three tdes_serve_loadtest runs of `load` (its
- * offered_gbps is ignored: every request arrives at once) on a fresh server,
- * then the best against the built-in default (4 warps, 1 reserved CTA, 4
- * slots), alternating, kept only if faster.  Unless TDES_TUNE_NO_STORE, the
- * choice is appended to the autotune cache, from which
- * tdes_server_config_default takes it on this kind of GPU.  If the cache
- * already has it and TDES_TUNE_FORCE is not set, nothing is timed.  The
- * load test writes into load->out_pool. */
+ * leaves free for the next, slots, round form) for the request mix of `load`
+ * (its offered_gbps is ignored).  A shape's score is its p99 latency at one
+ * offered load for all candidates, 90% of the built-in default's closed-loop
+ * throughput, among the shapes that keep at least 97% of that throughput
+ * closed-loop; each figure is the median of three tdes_serve_loadtest runs
+ * on a fresh server.  Coordinate search over warps 2, 4, 8, reserved CTAs 1,
+ * 2 (at least one CTA per SM stays free so that a new batch can start while
+ * others run), slots 2, 4, 8 and the two round forms, then the best against
+ * the built-in default (4 warps, 1 reserved CTA, 4 slots, per-pass rounds),
+ * alternating, kept only if better.  Unless TDES_TUNE_NO_STORE, the choice is
+ * appended to the autotune cache, from which tdes_server_config_default takes
+ * it on this kind of GPU.  If the cache already has it and TDES_TUNE_FORCE is
+ * not set, nothing is timed.  The load tests write into load->out_pool. */
 typedef struct {
     char key[64];
     tdes_server_config_t best;     /* the default configuration with the tuned fields */
     tdes_server_config_t baseline; /* the built-in default */
-    double best_gbps, baseline_gbps;
+    double best_gbps, baseline_gbps; /* closed-loop throughput */
     uint32_t candidates;
     int from_cache;
+    double best_p99_ms, baseline_p99_ms; /* p99 at load_gbps (0 when from the cache) */
+    double load_gbps;
 } tdes_server_autotune_result_t;
 
 int tdes_server_autotune(const tdes_keytable_t *kt, const tdes_loadtest_config_t *load,

@@ -819,10 +819,16 @@ int tdes_serve_loadtest(tdes_server_t* s, const tdes_loadtest_config_t* c,
 
 namespace {
 
-// Median closed-loop GB/s of `runs` load tests of a fresh server in cfg
-// (after a warm-up of a tenth of the requests).
-int serve_gbps(const tdes_keytable_t* kt, const tdes_server_config_t& cfg,
-               const tdes_loadtest_config_t& load, int runs, double* gbps) {
+// One candidate's figures: the median closed-loop GB/s of `runs` load tests
+// of a fresh server in cfg (after a warm-up of a tenth of the requests) and,
+// when load_gbps > 0, the median p99 latency of `runs` open-loop tests at
+// that offered load.
+struct ServeScore {
+    double gbps = 0.0, p99_ms = 0.0;
+};
+
+int serve_score(const tdes_keytable_t* kt, const tdes_server_config_t& cfg,
+                const tdes_loadtest_config_t& load, int runs, double load_gbps, ServeScore* out) {
     tdes_server_t* s = nullptr;
     int rc = tdes_server_create(kt, &cfg, &s);
     if (rc != TDES_OK) return rc;
@@ -831,18 +837,33 @@ int serve_gbps(const tdes_keytable_t* kt, const tdes_server_config_t& cfg,
     c.offered_gbps = 0.0;
     c.n_requests = std::max<uint64_t>(1, load.n_requests / 10);
     rc = tdes_serve_loadtest(s, &c, &r);
-    std::vector<double> v;
+    std::vector<double> g, l;
     c.n_requests = load.n_requests;
     for (int i = 0; i < runs && rc == TDES_OK; ++i) {
         c.seed = load.seed + 1 + (uint64_t)i;
+        c.offered_gbps = 0.0;
         rc = tdes_serve_loadtest(s, &c, &r);
-        v.push_back(r.gbps);
+        g.push_back(r.gbps);
+        if (rc == TDES_OK && load_gbps > 0) {
+            c.offered_gbps = load_gbps;
+            rc = tdes_serve_loadtest(s, &c, &r);
+            l.push_back(r.p99_ms);
+        }
     }
     tdes_server_destroy(s);
     if (rc != TDES_OK) return rc;
-    std::sort(v.begin(), v.end());
-    *gbps = v[v.size() / 2];
+    std::sort(g.begin(), g.end());
+    out->gbps = g[g.size() / 2];
+    if (!l.empty()) {
+        std::sort(l.begin(), l.end());
+        out->p99_ms = l[l.size() / 2];
+    }
     return TDES_OK;
+}
+
+bool same_shape(const tdes_server_config_t& a, const tdes_server_config_t& b) {
+    return a.warps_per_cta == b.warps_per_cta && a.reserve_ctas_per_sm == b.reserve_ctas_per_sm &&
+           a.slots == b.slots && a.round_form == b.round_form;
 }
 
 }  // namespace
@@ -875,23 +896,36 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
         res->from_cache = 1;
         return TDES_OK;
     }
+    // The score of a shape is its p99 latency at 90% of the default shape's
+    // closed-loop throughput (the same offered load for every candidate),
+    // among the shapes that keep at least 97% of that throughput closed-loop;
+    // a serving system is judged by its tail latency under load, and the
+    // shape with the highest closed-loop throughput is not the one with the
+    // lowest tail (2 warps per CTA won on throughput and showed p99 1.78 ms
+    // at 95% of its own peak).
     const int runs = 3;
-    tdes_server_config_t best = base;
-    double best_gbps = 0.0;
-    int rc = serve_gbps(kt, best, *load, runs, &best_gbps);
+    ServeScore sb;
+    int rc = serve_score(kt, base, *load, runs, 0.0, &sb);
     if (rc != TDES_OK) return rc;
+    const double load_gbps = 0.9 * sb.gbps, floor_gbps = 0.97 * sb.gbps;
+    rc = serve_score(kt, base, *load, runs, load_gbps, &sb);
+    if (rc != TDES_OK) return rc;
+    tdes_server_config_t best = base;
+    ServeScore bs = sb;
     uint32_t timed = 1;
+    auto better = [&](const ServeScore& x, const ServeScore& y) {  // x better than y
+        if ((x.gbps >= floor_gbps) != (y.gbps >= floor_gbps)) return x.gbps >= floor_gbps;
+        return x.p99_ms < y.p99_ms;
+    };
     auto consider = [&](tdes_server_config_t t) -> int {
-        if (t.warps_per_cta == best.warps_per_cta && t.reserve_ctas_per_sm == best.reserve_ctas_per_sm &&
-            t.slots == best.slots && t.round_form == best.round_form)
-            return TDES_OK;
-        double g = 0.0;
-        const int r = serve_gbps(kt, t, *load, runs, &g);
+        if (same_shape(t, best)) return TDES_OK;
+        ServeScore x;
+        const int r = serve_score(kt, t, *load, runs, load_gbps, &x);
         if (r != TDES_OK) return r;
         ++timed;
-        if (g > best_gbps) {
+        if (better(x, bs)) {
             best = t;
-            best_gbps = g;
+            bs = x;
         }
         return TDES_OK;
     };
@@ -919,32 +953,43 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
         t.round_form = 1 - best.round_form;
         if ((rc = consider(t)) != TDES_OK) return rc;
     }
-    // the winner against the default, alternating
-    double base_gbps = best_gbps;
-    const bool differs = best.warps_per_cta != base.warps_per_cta ||
-                         best.reserve_ctas_per_sm != base.reserve_ctas_per_sm ||
-                         best.slots != base.slots || best.round_form != base.round_form;
-    if (differs) {
-        std::vector<double> gb, gt;
+    // the winner against the default once more, alternating, so that drift
+    // over the search does not decide
+    if (!same_shape(best, base)) {
+        std::vector<ServeScore> vb, vt;
         for (int i = 0; i < 3; ++i) {
-            double x = 0.0;
-            if ((rc = serve_gbps(kt, base, *load, 1, &x)) != TDES_OK) return rc;
-            gb.push_back(x);
-            if ((rc = serve_gbps(kt, best, *load, 1, &x)) != TDES_OK) return rc;
-            gt.push_back(x);
+            ServeScore x;
+            if ((rc = serve_score(kt, base, *load, 1, load_gbps, &x)) != TDES_OK) return rc;
+            vb.push_back(x);
+            if ((rc = serve_score(kt, best, *load, 1, load_gbps, &x)) != TDES_OK) return rc;
+            vt.push_back(x);
         }
-        std::sort(gb.begin(), gb.end());
-        std::sort(gt.begin(), gt.end());
-        base_gbps = gb[1];
-        best_gbps = gt[1];
-        if (!(best_gbps > base_gbps)) {
+        auto med = [](std::vector<ServeScore> v) {
+            ServeScore m;
+            std::vector<double> g, l;
+            for (const ServeScore& x : v) {
+                g.push_back(x.gbps);
+                l.push_back(x.p99_ms);
+            }
+            std::sort(g.begin(), g.end());
+            std::sort(l.begin(), l.end());
+            m.gbps = g[1];
+            m.p99_ms = l[1];
+            return m;
+        };
+        sb = med(vb);
+        bs = med(vt);
+        if (!better(bs, sb)) {
             best = base;
-            best_gbps = base_gbps;
+            bs = sb;
         }
     }
     res->best = best;
-    res->best_gbps = best_gbps;
-    res->baseline_gbps = base_gbps;
+    res->best_gbps = bs.gbps;
+    res->baseline_gbps = sb.gbps;
+    res->best_p99_ms = bs.p99_ms;
+    res->baseline_p99_ms = sb.p99_ms;
+    res->load_gbps = load_gbps;
     res->candidates = timed;
     if (!(flags & TDES_TUNE_NO_STORE)) {
         tdes::TunedShape t;
@@ -952,8 +997,8 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
         t.shape.ctas_per_sm = best.reserve_ctas_per_sm;
         t.shape.round_form = best.round_form;
         t.slots = (int)best.slots;
-        t.gbps = best_gbps;
-        t.baseline_gbps = base_gbps;
+        t.gbps = bs.gbps;
+        t.baseline_gbps = sb.gbps;
         rc = tdes::tune_store(key, t);
         if (rc != TDES_OK) return rc;
     }

@@ -102,7 +102,9 @@ class ServerAutotuneResult(ctypes.Structure):
     """tdes_server_autotune_result_t"""
     _fields_ = [("key", ctypes.c_char * 64), ("best", ServerConfig), ("baseline", ServerConfig),
                 ("best_gbps", ctypes.c_double), ("baseline_gbps", ctypes.c_double),
-                ("candidates", ctypes.c_uint32), ("from_cache", ctypes.c_int)]
+                ("candidates", ctypes.c_uint32), ("from_cache", ctypes.c_int),
+                ("best_p99_ms", ctypes.c_double), ("baseline_p99_ms", ctypes.c_double),
+                ("load_gbps", ctypes.c_double)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -634,7 +636,9 @@ def tdes_server_autotune(kt, in_pool, out_pool, n_requests, flags=0, **mix) -> d
     cfg = lambda x: {f: getattr(x, f) for f, _ in ServerConfig._fields_}  # noqa: E731
     return {"key": r.key.decode(), "best": cfg(r.best), "baseline": cfg(r.baseline),
             "best_gbps": r.best_gbps, "baseline_gbps": r.baseline_gbps,
-            "candidates": r.candidates, "from_cache": bool(r.from_cache)}
+            "best_p99_ms": r.best_p99_ms, "baseline_p99_ms": r.baseline_p99_ms,
+            "load_gbps": r.load_gbps, "candidates": r.candidates,
+            "from_cache": bool(r.from_cache)}
 
 
 class Server:
