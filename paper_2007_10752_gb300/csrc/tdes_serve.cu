@@ -983,6 +983,10 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
             best = base;
             bs = sb;
         }
+    } else {
+        // the default won, possibly on a later measurement of its own shape
+        // (a coordinate step can come back to it): report one figure for it
+        sb = bs;
     }
     res->best = best;
     res->best_gbps = bs.gbps;
