@@ -206,3 +206,55 @@ def test_many_submissions_with_host_heap_churn(cuda_lib):
             o, nb = int(offs[i]), int(lens[i])
             assert (got[o:o + nb] == want[o:o + nb]).all(), f"ticket {t} message {i}"
     ctx.close()
+
+
+def test_in_place_halo_and_direct_messages(cuda_lib):
+    """A context batch with in-place CBC decryption over several tiles (the
+    per-tile snapshot runs first), a 64 MiB ECB message and a 64 MiB CTR
+    message (run by the single-key kernels inside the batch) and small
+    messages, in place and out of place: every byte against the oracle (the
+    large ones on 2^16 sampled blocks and their first and last tiles)."""
+    T = cuda_lib
+    keys = synth.key_triples(59, 5)
+    kt = T.KeyTable(keys)
+    ctx = T.Ctx(kt)
+    big = 64 << 20
+    plan = [(3, 0, 6000 * 8, True), (3, 1, 1025 * 8, True), (0, 2, big, False), (2, 3, big, True),
+            (1, 4, 4096, True), (4, 0, 700 * 8, False), (0, 1, 24, True)]
+    bufs, ents, datas = [], [], []
+    for j, (mode, key, nbytes, in_place) in enumerate(plan):
+        data = synth.random_bytes(5900 + j, nbytes)
+        iv = int(synth.words(59, j, 1, synth.STREAM_IV)[0])
+        if mode == 2:
+            iv &= 0xFFFFFFFF00000000
+        x = torch.from_numpy(data).cuda()
+        y = x if in_place else torch.zeros_like(x)
+        bufs.append((x, y))
+        datas.append((mode, key, iv, data))
+        ents.append((mode, key, iv, x, y, nbytes))
+    torch.cuda.synchronize()
+    t = ctx.submit(ents)
+    assert ctx.wait(t, 60.0) == 0
+    rng = np.random.default_rng(59)
+    for (x, y), (mode, key, iv, data) in zip(bufs, datas):
+        k = keys[key].tobytes()
+        got = y.cpu().numpy()
+        if data.size <= (1 << 20):
+            want = {0: lambda: oracle.tdes_ecb(k, data),
+                    1: lambda: oracle.tdes_ecb(k, data, decrypt=True),
+                    2: lambda: oracle.tdes_ctr(k, iv >> 32, iv & 0xFFFFFFFF, data),
+                    3: lambda: oracle.tdes_cbc_decrypt(k, iv, data),
+                    4: lambda: oracle.tdes_cbc_encrypt(k, iv, data)}[mode]()
+            assert (got == want).all(), f"mode {mode}, {data.size} bytes"
+            continue
+        nb = data.size // 8
+        blocks = np.concatenate([np.arange(1024), np.arange(nb - 1024, nb),
+                                 rng.integers(0, nb, 1 << 16)])
+        for b in np.unique(blocks)[::7]:
+            blk = data[8 * b:8 * b + 8]
+            if mode == 0:
+                w = oracle.tdes_ecb(k, blk)
+            else:
+                w = oracle.tdes_ctr(k, iv >> 32, (iv & 0xFFFFFFFF) + int(b), blk)
+            assert (got[8 * b:8 * b + 8] == w).all(), f"mode {mode} block {b}"
+    ctx.close()
