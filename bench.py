@@ -790,11 +790,19 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
     # host payloads: request buffers in pinned host memory, read and written by
     # the kernels over the host link (the server's default; its optional device
     # staging measured lower closed-loop throughput)
+    # The tuner's shape is chosen on device payloads; over the host link the
+    # built-in shape (4 slots) is measured beside it.
     host_in = in_pool[: 1 << 30].cpu().pin_memory()
     host_out = torch.empty(2 << 30, dtype=torch.uint8).pin_memory()
     hpeak = srv.loadtest(host_in, host_out, n_peak, 0.0, seed=7)
     hhalf = srv.loadtest(host_in, host_out, n_points // 2, 0.5 * hpeak["gbps"], seed=8)
     srv.close()
+    builtin = {k: tune["baseline"][k] for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots",
+                                                 "round_form")}
+    srv_b = tdes.Server(kt, budget_bytes=8 << 30, **builtin)
+    bpeak = srv_b.loadtest(host_in, host_out, n_peak, 0.0, seed=7)
+    bhalf = srv_b.loadtest(host_in, host_out, n_points // 2, 0.5 * bpeak["gbps"], seed=8)
+    srv_b.close()
     del out_pool, host_in, host_out
     keys = ("warps_per_cta", "reserve_ctas_per_sm", "slots", "round_form")
     tuned = {k: tune["best"][k] for k in keys}
@@ -814,12 +822,19 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
                          "candidates": tune["candidates"]},
             "points": points,
             "host_payloads": {"note": "same request mix, payloads in pinned host memory "
-                                      "(kernels access it over NVLink-C2C)",
+                                      "(kernels access it over NVLink-C2C); tuned server, "
+                                      "then the built-in shape",
                               "peak_closed_loop_gbs": round(hpeak["gbps"], 2),
                               "load_0.5": {"offered_gbs": round(hhalf["offered_gbps"], 2),
                                            "achieved_gbs": round(hhalf["gbps"], 2),
                                            "p50_ms": round(hhalf["p50_ms"], 4),
-                                           "p99_ms": round(hhalf["p99_ms"], 4)}},
+                                           "p99_ms": round(hhalf["p99_ms"], 4)},
+                              "builtin_shape": builtin,
+                              "builtin_peak_closed_loop_gbs": round(bpeak["gbps"], 2),
+                              "builtin_load_0.5": {"offered_gbs": round(bhalf["offered_gbps"], 2),
+                                                   "achieved_gbs": round(bhalf["gbps"], 2),
+                                                   "p50_ms": round(bhalf["p50_ms"], 4),
+                                                   "p99_ms": round(bhalf["p99_ms"], 4)}},
             "server": srv.config}
 
 
