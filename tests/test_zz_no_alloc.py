@@ -1,14 +1,15 @@
 """The allocation-free CBC decryption entry point, checked against the CPU
-oracle.
+oracle and the allocating entry point.
 
 tdes_cbc_decrypt_noalloc exists for callers that cannot let the library
 allocate device memory (a server whose pool owns the GPU, a plugin handed
 fixed buffers).  Its in-place calls keep the per-tile halo in a fixed scratch
 array inside the library instead of a temporary allocation.  Every result
 here is compared byte for byte with the oracle's CBC decryption of the same
-seeded input: several tiles with a ragged one (the scratch path), a single
-tile in place (no scratch), 8-byte-aligned buffers, and out of place, each
-twice in a row so that the second call runs on the scratch the first left.
+seeded input and with tdes_cbc_decrypt's: several tiles with a ragged one
+(the scratch path), a single tile in place (no scratch), 8-byte-aligned
+buffers, and out of place, each twice in a row so that the second call runs
+on the scratch the first left.
 This file is collected last so that a failure here stops a -x run only after
 every other test has run.
 """
@@ -52,9 +53,12 @@ def test_noalloc_matches_oracle_twice(cuda_lib, name, nblocks, offset):
         T.tdes_cbc_decrypt_noalloc(ks, iv, x, x)             # in place
         src = _dev(data, offset)
         y = T.tdes_cbc_decrypt_noalloc(ks, iv, src)           # out of place
+        z = _dev(data, offset)
+        T.tdes_cbc_decrypt(ks, iv, z, z)                      # the allocating entry point
         torch.cuda.synchronize()
         assert np.array_equal(x.cpu().numpy(), want), f"{name}: in-place call {call} differs"
         assert np.array_equal(y.cpu().numpy(), want), f"{name}: out-of-place call {call} differs"
+        assert np.array_equal(z.cpu().numpy(), want), f"{name}: regular entry point differs"
         assert np.array_equal(src.cpu().numpy(), data), f"{name}: input changed"
         ks.free()
 
