@@ -1059,7 +1059,7 @@ int tdes_batch_plan(const tdes_keytable_t* kt, const tdes_desc_t* descs, uint32_
     tdes::LaunchShape shape;  // the default shape
     if (b->tuned) shape = tuned.shape;
     int rc = tdes::set_batch_shape(b, shape);
-    if (rc != TDES_OK && b->tuned) {  // a cache entry this build cannot use
+    if (rc != TDES_OK && b->tuned) {  // a cache entry this library version cannot use
         b->tuned = false;
         rc = tdes::set_batch_shape(b, tdes::LaunchShape());
     }
