@@ -258,7 +258,10 @@ int tdes_batch_get_shape(const tdes_batch_t *b, tdes_launch_shape_t *shape);
 
 /* Runs the whole batch on `stream`: one persistent launch whose warps claim
  * work items from an atomic counter (preceded by a small snapshot launch
- * when a large message is CBC-decrypted in place).  Asynchronous. */
+ * when a large message is CBC-decrypted in place).  Asynchronous.  Two
+ * launches of one plan must not run at the same time (they share its claim
+ * counter and snapshot buffer): queue them on one stream or order them with
+ * events.  tdes_batch_submit_plan does this itself within a context. */
 int tdes_batch_launch(tdes_batch_t *b, tdes_stream_t stream);
 
 /* The same work as one CUDA graph: captured on first use (and after
@@ -360,6 +363,8 @@ int tdes_batch_submit(tdes_ctx_t *ctx, const tdes_desc_t *descs, uint32_t count,
 
 /* The same for a batch planned by tdes_batch_plan (it must use the
  * context's key table): its CUDA graph is replayed on a context stream.
+ * A plan submitted again while its previous ticket is pending is queued on
+ * that ticket's stream, behind it, so the two runs never overlap.
  * The plan must not be freed or reconfigured before the ticket completes. */
 int tdes_batch_submit_plan(tdes_ctx_t *ctx, tdes_batch_t *b, uint64_t *ticket);
 

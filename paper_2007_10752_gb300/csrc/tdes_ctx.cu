@@ -78,6 +78,10 @@ struct tdes_ctx {
     std::mutex mu;
     uint64_t next_ticket = 1;
     std::unordered_map<uint64_t, Record> records;
+    // Last ticket of each plan submitted with tdes_batch_submit_plan: two
+    // launches of one plan share its claim counter and halo, so a plan whose
+    // previous ticket is still pending is queued behind it on its stream.
+    std::unordered_map<const tdes_batch*, uint64_t> plan_last;
     int fit[9] = {0};                    // CTAs per SM of the batch kernel, by warps per CTA
     size_t dyn[9] = {0};
 
@@ -283,7 +287,16 @@ int tdes_batch_submit_plan(tdes_ctx_t* c, tdes_batch_t* b, uint64_t* ticket) {
         }
     std::lock_guard<std::mutex> lock(c->mu);
     if (b->total_items || !b->direct.empty()) {
-        const int k = c->pick_stream();
+        int k = -1;
+        const auto pl = c->plan_last.find(b);
+        if (pl != c->plan_last.end()) {
+            const auto prev = c->records.find(pl->second);  // pending tickets are never released
+            if (prev != c->records.end()) {
+                c->settle(prev->second);
+                if (!prev->second.complete) k = prev->second.stream;
+            }
+        }
+        if (k < 0) k = c->pick_stream();
         cudaStream_t s = c->streams[k];
         rc = tdes_batch_launch_graph(b, s);
         if (rc != TDES_OK) return rc;
@@ -300,6 +313,7 @@ int tdes_batch_submit_plan(tdes_ctx_t* c, tdes_batch_t* b, uint64_t* ticket) {
     }
     const uint64_t t = c->next_ticket++;
     c->records.emplace(t, std::move(r));
+    c->plan_last[b] = t;
     *ticket = t;
     return TDES_OK;
 }

@@ -173,8 +173,8 @@ struct tdes_server {
     uint64_t next_seq = 0;  // dispatcher thread only
     std::mutex stats_mu;
     uint32_t busy_now = 0, max_busy = 0;
-    std::vector<uint64_t> done_seqs;
-    uint64_t failed_batches = 0;
+    std::vector<uint64_t> done_seqs;  // at most 2 kTimeRing: older times are overwritten
+    uint64_t failed_batches = 0;      // and batches whose times the ring no longer holds
 
     // Clears the overlap statistics (cheap: no device read).
     void reset_stats() {
@@ -262,8 +262,15 @@ struct tdes_server {
                 completed_any = true;
                 std::lock_guard<std::mutex> lock(stats_mu);
                 --busy_now;
-                if (st == TDES_OK) done_seqs.push_back(sl.seq);
-                else ++failed_batches;
+                if (st == TDES_OK) {
+                    if (done_seqs.size() >= 2 * kTimeRing) {  // bounded on a server never reset
+                        done_seqs.erase(done_seqs.begin(), done_seqs.begin() + kTimeRing);
+                        failed_batches += kTimeRing;
+                    }
+                    done_seqs.push_back(sl.seq);
+                } else {
+                    ++failed_batches;
+                }
             }
             if (completed_any) notify_done();
             for (Slot& sl : slots) {
@@ -325,6 +332,10 @@ struct tdes_server {
                 if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
                 if (e != cudaSuccess) {
                     sticky_error.store(TDES_ECUDA);
+                    // copies already queued read the slot's pinned image and
+                    // staging, which the slot's next batch rewrites
+                    cudaStreamSynchronize(sl.stream);
+                    cudaGetLastError();
                     const int64_t t = now_ns();
                     for (const Pending& pd : take) complete(pd.ticket, TDES_ECUDA, t);
                     notify_done();
