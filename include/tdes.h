@@ -403,8 +403,8 @@ int tdes_batch_release(tdes_ctx_t *ctx, uint64_t ticket);
 
 /* Device scratch the call needs for n_msgs messages of msg_bytes under the
  * key table kt: 4 to 8 bytes per message (more for longer messages, whose
- * slices hold fewer messages) plus about 100 bytes per key triple (1.3 GB for
- * 2^28 messages of 64 bytes under 65536 triples).
+ * slices hold fewer messages), about 100 bytes per key triple and 25 MB
+ * (1.42 GB for 2^28 messages of 64 bytes under 65536 triples).
  * TDES_EINVAL for a msg_bytes that is not a multiple of 8 in [8, 256] or
  * n_msgs > TDES_UNIFORM_MAX_MSGS. */
 int tdes_uniform_scratch_bytes(const tdes_keytable_t *kt, uint64_t n_msgs, uint64_t msg_bytes,

@@ -47,11 +47,18 @@ constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per 
 // one held block per chain (25 KB; one CTA per SM of 8 warps for mixed-key
 // chains, 9 for single-key tiles)
 constexpr int kChainWarpBytes = kUniTableBytes + 32 * 32 * 4 + 32 * 32 * 8;
+// Mixed-key CBC-encryption slices: 12 warps per CTA, one CTA per SM, each
+// warp with its table and its chains' message indices in shared memory
+// (17 KB) and its held blocks in a slab of global scratch (8 KB per warp).
+constexpr int kMixedChainWarps = 12;
+constexpr int kMixedChainWarpBytes = kUniTableBytes + 32 * 32 * 4;
+constexpr int kMaxChainCtas = 256;  // the kernel's grid: min(SMs, this)
 // sm_103a shared memory: 228 KB per SM, 1 KB of it reserved per resident CTA,
 // so a CTA may take at most 227 KB
 constexpr int kSmemPerSm = 228 * 1024, kSmemReservedPerCta = 1024;
 static_assert(kKeyChainWarps * kChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm, "single-key chain CTA");
-static_assert(kUniWarps * kChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm, "mixed-key chain CTA");
+static_assert(kMixedChainWarps * kMixedChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm,
+              "mixed-key chain CTA");
 static_assert(2 * (kUniWarps * kUniTableBytes + kSmemReservedPerCta) <= kSmemPerSm, "two tile CTAs per SM");
 constexpr int kScanThreads = 1024;
 constexpr uint32_t kChainsPerTile = kTileBlocks;       // CBC encryption: one chain per tile slot
@@ -93,6 +100,7 @@ struct UniParams {
     uint32_t* order;            // message indices in group order
     uint32_t* tile_group;       // [tile] group
     uint32_t* slice_group;      // [slice] group
+    uint2* held;                // mixed-key chain slices: 1024 held blocks per warp
     UniHeader* hdr;
 };
 
@@ -660,15 +668,17 @@ __global__ void __launch_bounds__(KIND == kKindCbcEnc ? 32 * kKeyChainWarps : 32
 // table (bit s of every word: slice s's key and direction).  Slices differ
 // in mode, but each slice's mode is the same in every lane.
 template <bool CHAIN>
-__global__ void __launch_bounds__(32 * kUniWarps, CHAIN ? 1 : 2) uni_mixed_kernel(UniParams p) {
+__global__ void __launch_bounds__(CHAIN ? 32 * kMixedChainWarps : 32 * kUniWarps, CHAIN ? 1 : 2)
+    uni_mixed_kernel(UniParams p) {
+    constexpr uint32_t kWarps = CHAIN ? kMixedChainWarps : kUniWarps;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t* wtab = reinterpret_cast<uint32_t*>(
-        uni_smem + (size_t)warp * (CHAIN ? kChainWarpBytes : kUniTableBytes));
+        uni_smem + (size_t)warp * (CHAIN ? kMixedChainWarpBytes : kUniTableBytes));
     const uint32_t first = CHAIN ? p.hdr->slice2_base : 0u;
     const uint32_t ns = CHAIN ? p.hdr->slices[1] : p.hdr->slices[0];
     const uint32_t ntiles = (ns + 31u) / 32u;
-    const uint32_t W = gridDim.x * kUniWarps;
-    for (uint32_t t = blockIdx.x * kUniWarps + warp; t < ntiles; t += W) {
+    const uint32_t W = gridDim.x * kWarps;
+    for (uint32_t t = blockIdx.x * kWarps + warp; t < ntiles; t += W) {
         uint32_t pos = 0, cm = 0, kd = 0;  // cm: message count | mode << 8
         if (32u * t + lane < ns) {
             const uint32_t s = first + 32u * t + lane;
@@ -707,8 +717,9 @@ __global__ void __launch_bounds__(32 * kUniWarps, CHAIN ? 1 : 2) uni_mixed_kerne
                 A0[s] = c.x;
                 A1[s] = c.y;
             }
-            uni_chain_passes<true>(p, A0, A1, wtab, widx, reinterpret_cast<uint2*>(widx + 32 * 32),
-                                   lane, false);
+            uni_chain_passes<true>(p, A0, A1, wtab, widx,
+                                   p.held + (size_t)(blockIdx.x * kWarps + warp) * (32 * 32), lane,
+                                   false);
         } else {
             // lane l holds block l % m of the slice's message l / m
             const uint32_t slot = (lane * p.magic) >> 16, blk = lane - slot * p.m;
@@ -772,7 +783,8 @@ size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 // Scratch layout: header, five per-group arrays, order, tile and slice maps.
 struct UniLayout {
     size_t groups, max_tiles, max_slices;
-    size_t o_counts, o_cursor, o_msg, o_tile, o_slice, o_order, o_tg, o_sg, o_part, o_base, total;
+    size_t o_counts, o_cursor, o_msg, o_tile, o_slice, o_order, o_tg, o_sg, o_part, o_base, o_held;
+    size_t total;
 };
 
 UniLayout layout_for(uint64_t n_msgs, uint32_t m, uint32_t n_keys) {
@@ -792,7 +804,8 @@ UniLayout layout_for(uint64_t n_msgs, uint32_t m, uint32_t n_keys) {
     L.o_sg = L.o_tg + al256(L.max_tiles * 4);
     L.o_part = L.o_sg + al256(L.max_slices * 4);
     L.o_base = L.o_part + al256((size_t)scan_blocks(n_keys) * sizeof(Sums));
-    L.total = L.o_base + al256((size_t)scan_blocks(n_keys) * sizeof(Sums));
+    L.o_held = L.o_base + al256((size_t)scan_blocks(n_keys) * sizeof(Sums));
+    L.total = L.o_held + (size_t)kMaxChainCtas * kMixedChainWarps * 32 * 32 * sizeof(uint2);
     return L;
 }
 
@@ -836,7 +849,7 @@ cudaError_t prepare(int device, UniLaunch* out) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kKeyChainWarps * kChainWarpBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(uni_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kUniWarps * kChainWarpBytes);
+                                 kMixedChainWarps * kMixedChainWarpBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(uni_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     int fit = 0;
@@ -933,6 +946,7 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
     p.order = reinterpret_cast<uint32_t*>(base + L.o_order);
     p.tile_group = reinterpret_cast<uint32_t*>(base + L.o_tg);
     p.slice_group = reinterpret_cast<uint32_t*>(base + L.o_sg);
+    p.held = reinterpret_cast<uint2*>(base + L.o_held);
 
     const int grid = geo.sms * 8;
     const int work_grid = geo.sms * geo.work_ctas;
@@ -966,14 +980,20 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
         }
         uni_mixed_kernel<false><<<g, b, dyn, s>>>(p);
         // CBC-encryption chains: one CTA per SM, each warp with room for its
-        // chains' message indices and held blocks (2^28 messages of 64 B:
-        // 75.2 -> 73.1 ms with the indices, alternating A/B runs).  Nine
-        // warps fit; they took 2^22 single-key chains of 64 B from 1.60 to
-        // 1.52 ms, and left the mixed-key chains unchanged.
+        // chains' message indices (2^28 messages of 64 B: 75.2 -> 73.1 ms
+        // with the indices, alternating A/B runs) and its held blocks.  The
+        // single-key tiles keep both in shared memory, 9 warps per CTA (2^22
+        // single-key chains of 64 B: 1.60 -> 1.52 ms against 8).  The
+        // mixed-key slices keep the held blocks in their warp's slab of
+        // global scratch instead, which lets 12 warps fit (65.10 -> 64.65
+        // ms for 2^28 messages, against 8 warps with everything in shared
+        // memory); with the indices there too, 16 warps at 128 registers
+        // spilled 308 bytes and took 66.3 ms.
         const dim3 g1(geo.sms);
         uni_tile_kernel<kKindCbcEnc, false><<<g1, dim3(32 * kKeyChainWarps),
                                               (size_t)kKeyChainWarps * kChainWarpBytes, s>>>(p);
-        uni_mixed_kernel<true><<<g1, b, (size_t)kUniWarps * kChainWarpBytes, s>>>(p);
+        uni_mixed_kernel<true><<<dim3(std::min(geo.sms, kMaxChainCtas)), dim3(32 * kMixedChainWarps),
+                                 (size_t)kMixedChainWarps * kMixedChainWarpBytes, s>>>(p);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && skipped != nullptr) {
