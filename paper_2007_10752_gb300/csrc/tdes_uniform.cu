@@ -547,12 +547,39 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
 // C_i, C_{i+1}.  A sector is then read and written half as often (64-byte
 // messages: 2^28 of them under 65536 keys, 69.1 -> 66.2 ms per call; 2^22
 // CBC encryptions under two keys, 2.15 -> 1.59 ms).
+// The mixed-key chains' held blocks live in global scratch (a slab per
+// warp, 25 MB in all, rewritten every pass): their accesses ask L2 to keep
+// the lines over the chains' random message reads (evict-last).  The
+// single-key chains hold them in shared memory.
+template <bool GLOBAL>
+__device__ __forceinline__ uint2 ld_held(const uint2* q, uint64_t pol) {
+    if (!GLOBAL) return *q;
+    uint2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(q), "l"(pol)
+                 : "memory");
+    return v;
+}
+template <bool GLOBAL>
+__device__ __forceinline__ void st_held(uint2* q, uint2 v, uint64_t pol) {
+    if (!GLOBAL) {
+        *q = v;
+        return;
+    }
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(q), "r"(v.x),
+                 "r"(v.y), "l"(pol)
+                 : "memory");
+}
+
 template <bool MIXED>
 __device__ __forceinline__ void uni_chain_passes(const UniParams& p, uint32_t (&A0)[32],
                                                  uint32_t (&A1)[32], const uint32_t* __restrict__ tab,
                                                  const uint32_t* widx, uint2* held, uint32_t lane,
                                                  bool one_pass) {
     const bool pair = p.m % 2u == 0u && (((uintptr_t)p.in | (uintptr_t)p.out) & 15u) == 0u;
+    uint64_t pol = 0;
+    if (MIXED) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     for (uint32_t i = 0; i < p.m; ++i) {
         const bool odd = (i & 1u) != 0u;
         if (!pair) {
@@ -573,7 +600,7 @@ __device__ __forceinline__ void uni_chain_passes(const UniParams& p, uint32_t (&
                 if (mi != ~0u) x = ld_chain(reinterpret_cast<const uint4*>(msg_in(p, mi) + i));
                 A0[s] ^= x.x;
                 A1[s] ^= x.y;
-                held[32 * s + lane] = make_uint2(x.z, x.w);
+                st_held<MIXED>(held + 32 * s + lane, make_uint2(x.z, x.w), pol);
             }
         }
         tdes_process32_compact<MIXED>(A0, A1, tab, one_pass);
@@ -586,8 +613,8 @@ __device__ __forceinline__ void uni_chain_passes(const UniParams& p, uint32_t (&
         } else if (!odd) {  // hold C_i, start pass i + 1 from C_i ^ P_{i+1}
 #pragma unroll
             for (int s = 0; s < 32; ++s) {
-                const uint2 x = held[32 * s + lane];
-                held[32 * s + lane] = make_uint2(A0[s], A1[s]);
+                const uint2 x = ld_held<MIXED>(held + 32 * s + lane, pol);
+                st_held<MIXED>(held + 32 * s + lane, make_uint2(A0[s], A1[s]), pol);
                 A0[s] ^= x.x;
                 A1[s] ^= x.y;
             }
@@ -595,7 +622,7 @@ __device__ __forceinline__ void uni_chain_passes(const UniParams& p, uint32_t (&
 #pragma unroll
             for (int s = 0; s < 32; ++s) {
                 const uint32_t mi = widx[32 * s + lane];
-                const uint2 c = held[32 * s + lane];
+                const uint2 c = ld_held<MIXED>(held + 32 * s + lane, pol);
                 if (mi != ~0u)
                     *reinterpret_cast<uint4*>(msg_out(p, mi) + i - 1) = make_uint4(c.x, c.y, A0[s], A1[s]);
             }
@@ -987,7 +1014,8 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
         // mixed-key slices keep the held blocks in their warp's slab of
         // global scratch instead, which lets 12 warps fit (65.10 -> 64.65
         // ms for 2^28 messages, against 8 warps with everything in shared
-        // memory); with the indices there too, 16 warps at 128 registers
+        // memory; with the slab's accesses asking L2 to keep its lines,
+        // 64.20 ms); with the indices there too, 16 warps at 128 registers
         // spilled 308 bytes and took 66.3 ms.
         const dim3 g1(geo.sms);
         uni_tile_kernel<kKindCbcEnc, false><<<g1, dim3(32 * kKeyChainWarps),
