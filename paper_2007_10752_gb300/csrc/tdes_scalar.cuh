@@ -137,7 +137,13 @@ __device__ __forceinline__ uint64_t tdes_block_warp(uint64_t v, const LaneConsts
     // R is known (m0, m1), and the in-word index is a rotate amount (only
     // its low 5 bits count): R -> {bit test, select} || {rotate, XOR} ->
     // rotate -> ballot.
+    // Lane j's F bit is bit j of the new R once XORed with bit j of L, so
+    // each lane XORs its own bit of L (Lb, taken from R a round ahead, off
+    // the dependent path) into its vote and the ballot is the new R.
     const uint32_t b5 = 1u << ((c.rot + 5u) & 31u);
+    uint32_t lane;
+    asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+    uint32_t Lb = (L >> lane) & 1u;
 #pragma unroll
     for (int r = 0; r < rounds; ++r) {
         const uint32_t kn = keys[8 * (r + 1 < rounds ? r + 1 : r) + c.keypos];
@@ -145,14 +151,16 @@ __device__ __forceinline__ uint64_t tdes_block_warp(uint64_t v, const LaneConsts
         const uint32_t m1 = (k & 32u) ? c.mlo : c.mhi;
         const uint32_t w = (R & b5) ? m1 : m0;
         const uint32_t sh = __funnelshift_r(R, R, c.rot) ^ k;
-        const uint32_t f = __ballot_sync(0xFFFFFFFFu, __funnelshift_r(w, w, sh) & 1u);
-        const uint32_t t = L ^ f;
+        const uint32_t Rb = (R >> lane) & 1u;
+        const uint32_t t = __ballot_sync(0xFFFFFFFFu, (__funnelshift_r(w, w, sh) ^ Lb) & 1u);
         L = R;
+        Lb = Rb;
         R = t;
         if ((r & 15) == 15) {  // end of a DES pass: R16 || L16 continues as L0 || R0
             const uint32_t u = L;
             L = R;
             R = u;
+            Lb = (L >> lane) & 1u;
         }
         k = kn;
     }
