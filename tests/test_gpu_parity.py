@@ -199,19 +199,31 @@ def test_argument_errors(cuda_lib):
     torch.cuda.synchronize()
 
 
-def test_host_buffer_pipeline(cuda_lib):
+@pytest.mark.parametrize("kind", ["pinned", "pageable", "pinned_4_bytes_off"])
+def test_host_buffer_pipeline(cuda_lib, kind):
+    """Host buffers in and out: pinned ones are read and written by the kernel
+    directly; pageable ones, and pinned ones off an 8-byte boundary, stream
+    through the device buffer in several chunks."""
     nblocks = (1 << 20) + 333  # 8 MiB + ragged, several chunks of a 1 MiB device buffer
     keys = synth.key_triple(6000)
     data = synth.random_bytes(6000, 8 * nblocks)
     ks = cuda_lib.KeySchedule.from_triple(keys)
-    hin = torch.from_numpy(data).pin_memory()
-    hout = torch.empty_like(hin).pin_memory()
+    if kind == "pageable":
+        hin, hout = data.copy(), np.empty_like(data)
+    else:
+        off = 4 if kind == "pinned_4_bytes_off" else 0
+        a = torch.empty(data.size + 8, dtype=torch.uint8).pin_memory()
+        b = torch.empty(data.size + 8, dtype=torch.uint8).pin_memory()
+        hin, hout = a[off:off + data.size], b[off:off + data.size]
+        hin.copy_(torch.from_numpy(data))
     dev_buf = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     cuda_lib.tdes_ecb_crypt_host(ks, False, hin, hout, dev_buf)
     want = oracle.tdes_parallel(keys, data, "ecb_enc", threads=NCPU)
-    assert (hout.numpy() == want).all()
+    got = hout if kind == "pageable" else hout.numpy()
+    assert (got == want).all()
     cuda_lib.tdes_ecb_crypt_host(ks, True, hout, hout, dev_buf)  # in place, host side
-    assert (hout.numpy() == data).all()
+    got = hout if kind == "pageable" else hout.numpy()
+    assert (got == data).all()
 
 
 def test_full_size_1gib(cuda_lib):
