@@ -767,11 +767,17 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
     out_pool = torch.empty(8 << 30, dtype=torch.uint8, device=in_pool.device)
     # the library's server autotuner on this request mix (closed loop); the
     # server below then starts in the tuned configuration by default
-    tune = tdes.tdes_server_autotune(kt, in_pool, out_pool, n_peak, flags=tdes.TUNE_FORCE,
+    # 50000 requests a run: with 20000 (about 200 samples above the 99th
+    # percentile) the tuner's choice changed between calls
+    tune = tdes.tdes_server_autotune(kt, in_pool, out_pool, 50000, flags=tdes.TUNE_FORCE,
                                      seed=11)
     srv = tdes.Server(kt, budget_bytes=8 << 30)
     srv.loadtest(in_pool, out_pool, 2000, 0.0, seed=99)  # warm-up
-    peak = srv.loadtest(in_pool, out_pool, n_peak, 0.0, seed=5)
+    # the closed-loop peak, which sets every load point: the median of three
+    # runs of 50000 requests (one run of 20000 varied by about 5% between calls)
+    peaks = sorted((srv.loadtest(in_pool, out_pool, 50000, 0.0, seed=sd) for sd in (5, 6, 7)),
+                   key=lambda r: r["gbps"])
+    peak = peaks[1]
     points = []
     for frac in (0.25, 0.5, 0.75, 0.95):
         r = srv.loadtest(in_pool, out_pool, n_points, frac * peak["gbps"], seed=int(frac * 100))
@@ -809,6 +815,7 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
     tuned = {k: tune["best"][k] for k in keys}
     default = {k: tune["baseline"][k] for k in keys}
     return {"workload": SERVE_WORKLOAD, "peak_closed_loop_gbs": round(peak["gbps"], 2),
+            "peak_runs_gbs": [round(r["gbps"], 2) for r in peaks],
             "peak_p50_ms": round(peak["p50_ms"], 3),
             "peak_max_slots_busy": peak["max_slots_busy"],
             "peak_device_overlap_frac": round(peak["device_overlap_frac"], 4),
