@@ -517,7 +517,12 @@ def tdes_autotune_cache_path() -> str:
 class Ctx:
     """Owns a tdes_ctx_t: batches submitted with a ticket, polled per
     descriptor and waited on with a time limit (tdes_batch_submit / poll /
-    wait / release)."""
+    wait / release).
+
+    The device reads a ticket's buffers and plan after submit returns, so
+    the context keeps the tensors given as entries' in/out and the Batch of
+    submit_plan referenced until the ticket is released or the context is
+    closed.  Raw integer addresses are the caller's to keep valid."""
 
     def __init__(self, kt: KeyTable, streams: int = 2):
         lib = load()
@@ -529,25 +534,32 @@ class Ctx:
         self.handle = h.value
         self.kt = kt
         self._counts = {}
+        self._keep = {}  # ticket -> objects the device may still read
 
     def submit(self, entries) -> int:
         """entries: (mode, key_index, iv_or_ctr, in, out, nbytes) each, or a
         DESC_DTYPE array; returns the ticket."""
+        keep = []
         if isinstance(entries, np.ndarray):
             descs = np.ascontiguousarray(entries, dtype=DESC_DTYPE)
             n, addr = descs.shape[0], descs.ctypes.data
         else:
+            entries = list(entries)
+            keep = [b for e in entries for b in (e[3], e[4]) if not isinstance(b, int)]
             descs, n = make_descs(entries)
             addr = ctypes.addressof(descs)
         t = ctypes.c_uint64()
         _check(load().tdes_batch_submit(self.handle, addr, n, ctypes.byref(t)))
         self._counts[t.value] = n
+        if keep:
+            self._keep[t.value] = keep
         return t.value
 
     def submit_plan(self, batch: "Batch") -> int:
         t = ctypes.c_uint64()
         _check(load().tdes_batch_submit_plan(self.handle, batch.handle, ctypes.byref(t)))
         self._counts[t.value] = len(batch.status)
+        self._keep[t.value] = [batch]
         return t.value
 
     def poll(self, ticket: int, count: int | None = None) -> tuple:
@@ -564,12 +576,14 @@ class Ctx:
         r = int(load().tdes_batch_release(self.handle, ticket))
         if r == TDES_OK:
             self._counts.pop(ticket, None)
+            self._keep.pop(ticket, None)
         return r
 
     def close(self):
         if self.handle:
-            load().tdes_ctx_destroy(self.handle)
+            load().tdes_ctx_destroy(self.handle)  # waits for the context's streams
             self.handle = None
+        self._keep.clear()
 
     def __del__(self):
         try:

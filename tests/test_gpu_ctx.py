@@ -9,6 +9,7 @@ long CBC-encryption chain, run out with TDES_ETIMEDOUT and leave the
 context usable); several tickets are in flight at once; a planned batch gets
 a ticket too."""
 import ctypes
+import gc
 import os
 
 import numpy as np
@@ -266,7 +267,9 @@ def test_resubmitted_plan_runs_in_order(cuda_lib):
     waited on.  Each run reads what the run before it wrote, so the bytes
     must equal the oracle applied three times in a row: two runs of one plan
     overlapping on two streams would share its claim counter and halo
-    snapshot and skip or repeat tiles."""
+    snapshot and skip or repeat tiles.  The caller drops its Batch right
+    after submitting: the context holds the plan until the tickets are
+    released."""
     T = cuda_lib
     seed, n, n_keys = 61, 48, 11
     keys = synth.key_triples(seed, n_keys)
@@ -285,8 +288,12 @@ def test_resubmitted_plan_runs_in_order(cuda_lib):
     b = T.Batch(kt, ents)
     torch.cuda.synchronize()
     tickets = [ctx.submit_plan(b) for _ in range(3)]
+    del b  # the context keeps the plan until its tickets are released
+    gc.collect()
     for t in tickets:
         assert ctx.wait(t, 60.0) == 0
+    for t in tickets:
+        assert ctx.release(t) == 0
     want = data
     for _ in range(3):
         want = expected(keys, lens, modes, kidx, ivs, offs, want)
