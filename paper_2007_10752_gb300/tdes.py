@@ -656,7 +656,11 @@ def tdes_server_autotune(kt, in_pool, out_pool, n_requests, flags=0, **mix) -> d
 
 
 class Server:
-    """Owns a tdes_server_t (continuous-batching request server)."""
+    """Owns a tdes_server_t (continuous-batching request server).
+
+    Tensors given as a request's in/out stay referenced until a poll or wait
+    reports the request finished (or the server is closed), so the torch
+    allocator does not hand them out while the device still uses them."""
 
     def __init__(self, kt: KeyTable, **config):
         lib = load()
@@ -669,27 +673,48 @@ class Server:
         self.handle = h.value
         self.kt = kt
         self.config = {f: getattr(cfg, f) for f, _ in ServerConfig._fields_}
+        self._keep = {}  # first ticket -> (request count, tensors the device may still use)
+        self._submits = 0
+
+    def _hold(self, ticket: int, count: int, objs):
+        objs = [o for o in objs if not isinstance(o, int)]
+        if objs:
+            self._keep[ticket] = (count, objs)
+        self._submits += 1
+        if self._submits % 1024 == 0:  # callers that never poll: drop finished requests
+            for t, (c, _) in list(self._keep.items()):
+                if int(load().tdes_server_poll_group(self.handle, t, c, None)) != 1:
+                    del self._keep[t]
 
     def submit(self, mode, key_index, iv_or_ctr, inp, out, nbytes=None) -> int:
         n = _nbytes(inp) if nbytes is None else nbytes
         d = Desc(mode, key_index, iv_or_ctr & (2**64 - 1), _ptr(inp), _ptr(out), n)
         t = ctypes.c_uint64()
         _check(load().tdes_server_submit(self.handle, ctypes.byref(d), ctypes.byref(t)))
+        self._hold(t.value, 1, (inp, out))
         return t.value
 
     def poll(self, ticket: int) -> int:
-        return int(load().tdes_server_poll(self.handle, ticket))
+        r = int(load().tdes_server_poll(self.handle, ticket))
+        if r != 1:
+            self._keep.pop(ticket, None)
+        return r
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
-        return int(load().tdes_server_wait(self.handle, ticket, int(timeout_s * 1e9)))
+        r = int(load().tdes_server_wait(self.handle, ticket, int(timeout_s * 1e9)))
+        if r not in (1, TDES_ETIMEDOUT):
+            self._keep.pop(ticket, None)
+        return r
 
     def submit_group(self, entries) -> tuple:
         """entries: (mode, key_index, iv_or_ctr, in, out, nbytes) each; returns
         (ticket, count) of the group."""
+        entries = list(entries)
         arr, n = make_descs(entries)
         t = ctypes.c_uint64()
         _check(load().tdes_server_submit_group(self.handle, ctypes.addressof(arr), n,
                                                ctypes.byref(t)))
+        self._hold(t.value, n, [b for e in entries for b in (e[3], e[4])])
         return t.value, n
 
     def poll_group(self, group) -> tuple:
@@ -697,11 +722,16 @@ class Server:
         ticket, n = group
         st = np.zeros(n, dtype=np.int32)
         r = int(load().tdes_server_poll_group(self.handle, ticket, n, st.ctypes.data))
+        if r != 1:
+            self._keep.pop(ticket, None)
         return r, st
 
     def wait_group(self, group, timeout_s: float = 60.0) -> int:
         ticket, n = group
-        return int(load().tdes_server_wait_group(self.handle, ticket, n, int(timeout_s * 1e9)))
+        r = int(load().tdes_server_wait_group(self.handle, ticket, n, int(timeout_s * 1e9)))
+        if r not in (1, TDES_ETIMEDOUT):
+            self._keep.pop(ticket, None)
+        return r
 
     def loadtest(self, in_pool, out_pool, n_requests, offered_gbps, seed=1, small_frac=0.8,
                  small=(64, 4096), large=(64 << 10, 16 << 20), mode_probs=(1, 1, 1),
@@ -719,8 +749,9 @@ class Server:
 
     def close(self):
         if self.handle:
-            load().tdes_server_destroy(self.handle)
+            load().tdes_server_destroy(self.handle)  # drains the queue and the device work
             self.handle = None
+        self._keep.clear()
 
     def __del__(self):
         try:
