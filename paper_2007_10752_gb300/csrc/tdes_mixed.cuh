@@ -16,7 +16,11 @@
 #ifdef __CUDACC__
 // Lane i holds row i of a 32x32 bit matrix (bit j = M[i][j]); returns column
 // `lane` (bit i = M[i][lane]).  Each step swaps the off-diagonal blocks of
-// width w between lanes i and i ^ w.
+// width w between lanes i and i ^ w: the partner's word rotated left by w
+// (by 32 - w in the lane of the pair whose bit w is set) has the block this
+// lane takes in place, and one select under a per-lane mask merges it with
+// the block this lane keeps.  Three operations a step (shuffle, rotate,
+// select) where the two-branch form took about eight.
 __device__ __forceinline__ uint32_t transpose_lanes32(uint32_t x, uint32_t lane) {
 #pragma unroll
     for (int w = 16; w >= 1; w >>= 1) {
@@ -25,8 +29,11 @@ __device__ __forceinline__ uint32_t transpose_lanes32(uint32_t x, uint32_t lane)
                           : w == 4  ? 0xF0F0F0F0u
                           : w == 2  ? 0xCCCCCCCCu
                                     : 0xAAAAAAAAu;
+        const bool upper = (lane & w) != 0;
+        const uint32_t keep = upper ? hi : ~hi;  // this lane's own block
         const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, w);
-        x = (lane & w) ? ((x & hi) | ((y & hi) >> w)) : ((x & ~hi) | ((y & ~hi) << w));
+        const uint32_t r = __funnelshift_l(y, y, upper ? 32 - w : w);
+        x = (x & keep) | (r & ~keep);
     }
     return x;
 }
