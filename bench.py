@@ -801,14 +801,22 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
     # built-in shape (4 slots) is measured beside it.
     host_in = in_pool[: 1 << 30].cpu().pin_memory()
     host_out = torch.empty(2 << 30, dtype=torch.uint8).pin_memory()
-    hpeak = srv.loadtest(host_in, host_out, n_peak, 0.0, seed=7)
-    hhalf = srv.loadtest(host_in, host_out, n_points // 2, 0.5 * hpeak["gbps"], seed=8)
+    # Over the host link single runs now and then met a stall of a few ms (a
+    # peak 25% low, or a p99 of 9.6 ms at half load, in 1 of 3 bench runs), so
+    # the peak and the half-load point are each the median of three runs.
+    def host_point(server):
+        pk = sorted((server.loadtest(host_in, host_out, n_peak, 0.0, seed=sd) for sd in (7, 17, 27)),
+                    key=lambda r: r["gbps"])[1]
+        half = sorted((server.loadtest(host_in, host_out, n_points // 4, 0.5 * pk["gbps"], seed=sd)
+                       for sd in (8, 18, 28)), key=lambda r: r["p99_ms"])[1]
+        return pk, half
+
+    hpeak, hhalf = host_point(srv)
     srv.close()
     builtin = {k: tune["baseline"][k] for k in ("warps_per_cta", "reserve_ctas_per_sm", "slots",
                                                  "round_form")}
     srv_b = tdes.Server(kt, budget_bytes=8 << 30, **builtin)
-    bpeak = srv_b.loadtest(host_in, host_out, n_peak, 0.0, seed=7)
-    bhalf = srv_b.loadtest(host_in, host_out, n_points // 2, 0.5 * bpeak["gbps"], seed=8)
+    bpeak, bhalf = host_point(srv_b)
     srv_b.close()
     del out_pool, host_in, host_out
     keys = ("warps_per_cta", "reserve_ctas_per_sm", "slots", "round_form")
@@ -831,7 +839,8 @@ def run_serving(torch, tdes, synth, in_pool, n_points=100000, n_peak=20000):
             "points": points,
             "host_payloads": {"note": "same request mix, payloads in pinned host memory "
                                       "(kernels access it over NVLink-C2C); tuned server, "
-                                      "then the built-in shape",
+                                      "then the built-in shape; each figure the median of "
+                                      "three runs",
                               "peak_closed_loop_gbs": round(hpeak["gbps"], 2),
                               "load_0.5": {"offered_gbs": round(hhalf["offered_gbps"], 2),
                                            "achieved_gbs": round(hhalf["gbps"], 2),

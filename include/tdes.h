@@ -596,7 +596,9 @@ int tdes_server_stats(tdes_server_t *s, int reset, tdes_server_stats_t *out);
  * 2 (at least one CTA per SM stays free so that a new batch can start while
  * others run), slots 2, 4, 8 and the two round forms, then the best against
  * the built-in default (4 warps, 1 reserved CTA, 4 slots, per-pass rounds),
- * alternating, kept only if better.  Unless TDES_TUNE_NO_STORE, the choice is
+ * alternating, kept only if better.  "Better" on p99 means lower by more than
+ * 3%, so that shapes within run-to-run spread of each other do not replace
+ * one another.  Unless TDES_TUNE_NO_STORE, the choice is
  * appended to the autotune cache, from which tdes_server_config_default takes
  * it on this kind of GPU.  If the cache already has it and TDES_TUNE_FORCE is
  * not set, nothing is timed.  The load tests write into load->out_pool. */

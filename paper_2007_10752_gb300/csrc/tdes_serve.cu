@@ -838,6 +838,8 @@ struct ServeScore {
     double gbps = 0.0, p99_ms = 0.0;
 };
 
+constexpr double kServeTuneMargin = 0.03;
+
 int serve_score(const tdes_keytable_t* kt, const tdes_server_config_t& cfg,
                 const tdes_loadtest_config_t& load, int runs, double load_gbps, ServeScore* out) {
     tdes_server_t* s = nullptr;
@@ -924,9 +926,13 @@ int tdes_server_autotune(const tdes_keytable_t* kt, const tdes_loadtest_config_t
     tdes_server_config_t best = base;
     ServeScore bs = sb;
     uint32_t timed = 1;
+    // x replaces y only if its p99 is lower by more than kServeTuneMargin:
+    // shapes within run-to-run spread of each other (a few percent of p99)
+    // would otherwise decide by noise, and two calls could pick different
+    // shapes of the same quality.
     auto better = [&](const ServeScore& x, const ServeScore& y) {  // x better than y
         if ((x.gbps >= floor_gbps) != (y.gbps >= floor_gbps)) return x.gbps >= floor_gbps;
-        return x.p99_ms < y.p99_ms;
+        return x.p99_ms < (1.0 - kServeTuneMargin) * y.p99_ms;
     };
     auto consider = [&](tdes_server_config_t t) -> int {
         if (same_shape(t, best)) return TDES_OK;
