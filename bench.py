@@ -390,13 +390,19 @@ def run_ours(args):
         hbuf = torch.from_numpy(host.copy()).pin_memory()
         dev_buf = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
         tdes.tdes_ecb_crypt_host(ks, False, hbuf, hbuf, dev_buf)  # warm-up
-        n_e2e = max(3, min(10, args.steps // 50))
+        # Each call timed on its own and the median kept: the host link and
+        # host memory are shared with the GPU's neighbour on the same host,
+        # and one call in a few met a slowdown (a mean of 3 calls once read
+        # 142 against 157-159 GB/s).  Every call's rate is reported.
+        n_e2e = max(5, min(10, args.steps // 50))
         if world > 1:
             dist.barrier()
-        t = time.perf_counter()
+        calls = []
         for _ in range(n_e2e):
+            t = time.perf_counter()
             tdes.tdes_ecb_crypt_host(ks, False, hbuf, hbuf, dev_buf)
-        el = (time.perf_counter() - t) / n_e2e
+            calls.append(time.perf_counter() - t)
+        el = float(np.median(calls))
         if world > 1:
             el = reduce_max(el, f"cuda:{dev}")
         # the copies alone, for context: the host link bounds the end-to-end number
@@ -415,6 +421,8 @@ def run_ours(args):
                "h2d_bytes_per_step": NBYTES, "d2h_bytes_per_step": NBYTES,
                "api": "tdes_ecb_crypt_host (pinned host buffer in place: the kernel reads and "
                       "writes it over the host link)",
+               "statistic": f"median of {n_e2e} calls, each timed on its own",
+               "calls_gbs": [round(NBYTES / c / 1e9, 1) for c in calls],
                "copy_only_h2d_gbs": round(h2d, 1), "copy_only_d2h_gbs": round(d2h, 1)}
         del hbuf, dev_buf
 
