@@ -1016,7 +1016,11 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
         // ms for 2^28 messages, against 8 warps with everything in shared
         // memory; with the slab's accesses asking L2 to keep its lines,
         // 64.20 ms); with the indices there too, 16 warps at 128 registers
-        // spilled 308 bytes and took 66.3 ms.
+        // spilled 308 bytes and took 66.3 ms.  The single-key tiles with
+        // their held blocks in the slab at 12 warps were slower (2^22 chains
+        // under two keys: 1.71 -> 1.91 ms): with few keys a tile's chains lie
+        // close together, their data is mostly in L2 already, and the
+        // shared-memory held blocks' shorter latency counts for more.
         const dim3 g1(geo.sms);
         uni_tile_kernel<kKindCbcEnc, false><<<g1, dim3(32 * kKeyChainWarps),
                                               (size_t)kKeyChainWarps * kChainWarpBytes, s>>>(p);
