@@ -43,6 +43,11 @@ namespace {
 constexpr int kUniWarps = 8;                            // warps per CTA of the work kernels
 constexpr int kKeyChainWarps = 9;                       // single-key CBC-encryption tiles: 9 x 25 KB
 constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per warp
+// Mixed-key block tiles: beside the table, each slice's message indices (up to
+// kSliceSlots messages a slice, so messages of 32 bytes or more) and modes,
+// read again after the rounds
+constexpr int kSliceSlots = 8;
+constexpr int kMixedWarpBytes = kUniTableBytes + 32 * kSliceSlots * 4 + 32;
 // CBC-encryption chains: a warp's table, its 1024 chains' message indices and
 // one held block per chain (25 KB; one CTA per SM of 8 warps for mixed-key
 // chains, 9 for single-key tiles)
@@ -60,6 +65,8 @@ static_assert(kKeyChainWarps * kChainWarpBytes + kSmemReservedPerCta <= kSmemPer
 static_assert(kMixedChainWarps * kMixedChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm,
               "mixed-key chain CTA");
 static_assert(2 * (kUniWarps * kUniTableBytes + kSmemReservedPerCta) <= kSmemPerSm, "two tile CTAs per SM");
+static_assert(2 * (kUniWarps * kMixedWarpBytes + kSmemReservedPerCta) <= kSmemPerSm,
+              "two mixed-key CTAs per SM");
 constexpr int kScanThreads = 1024;
 constexpr uint32_t kChainsPerTile = kTileBlocks;       // CBC encryption: one chain per tile slot
 constexpr uint32_t kModes = 5;                         // groups per key: one per TDES_MODE_*
@@ -700,7 +707,7 @@ __global__ void __launch_bounds__(CHAIN ? 32 * kMixedChainWarps : 32 * kUniWarps
     constexpr uint32_t kWarps = CHAIN ? kMixedChainWarps : kUniWarps;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t* wtab = reinterpret_cast<uint32_t*>(
-        uni_smem + (size_t)warp * (CHAIN ? kMixedChainWarpBytes : kUniTableBytes));
+        uni_smem + (size_t)warp * (CHAIN ? kMixedChainWarpBytes : kMixedWarpBytes));
     const uint32_t first = CHAIN ? p.hdr->slice2_base : 0u;
     const uint32_t ns = CHAIN ? p.hdr->slices[1] : p.hdr->slices[0];
     const uint32_t ntiles = (ns + 31u) / 32u;
@@ -748,42 +755,72 @@ __global__ void __launch_bounds__(CHAIN ? 32 * kMixedChainWarps : 32 * kUniWarps
                                    p.held + (size_t)(blockIdx.x * kWarps + warp) * (32 * 32), lane,
                                    false);
         } else {
-            // lane l holds block l % m of the slice's message l / m
+            // lane l holds block l % m of the slice's message l / m.  With at
+            // most kSliceSlots messages a slice, each message's index (written
+            // by the lane holding its first block) and each slice's mode stay
+            // in shared memory for the loops after the rounds.
             const uint32_t slot = (lane * p.magic) >> 16, blk = lane - slot * p.m;
+            const bool keep = p.per_slice <= (uint32_t)kSliceSlots;
+            uint32_t* sidx = wtab + TDES_TABLE_WORDS;                              // [slice][slot]
+            uint8_t* smode = reinterpret_cast<uint8_t*>(sidx + 32 * kSliceSlots);  // [slice]
+            if (keep) smode[lane] = (uint8_t)(cm >> 8);
             uint32_t A0[32], A1[32];
 #pragma unroll
             for (int s = 0; s < 32; ++s) {
                 const uint32_t ps = __shfl_sync(0xFFFFFFFFu, pos, s);
                 const uint32_t c = __shfl_sync(0xFFFFFFFFu, cm, s);
                 uint2 v = make_uint2(0u, 0u);
+                uint32_t mi = ~0u;
                 if (slot < (c & 0xFFu)) {
-                    const uint32_t mi = p.order[ps + slot];
+                    mi = p.order[ps + slot];
                     v = (c >> 8) == TDES_MODE_CTR ? ctr_words(ld_iv(p, mi), blk) : ld_msg(msg_in(p, mi) + blk);
                 }
+                if (keep && blk == 0) sidx[kSliceSlots * s + slot] = mi;
                 A0[s] = v.x;
                 A1[s] = v.y;
             }
+            __syncwarp();
             tdes_process32_compact<true>(A0, A1, wtab, false);
+            if (keep) {
 #pragma unroll
-            for (int s = 0; s < 32; ++s) {
-                const uint32_t ps = __shfl_sync(0xFFFFFFFFu, pos, s);
-                const uint32_t c = __shfl_sync(0xFFFFFFFFu, cm, s);
-                const uint32_t md = c >> 8;
-                if (slot < (c & 0xFFu) && (md == TDES_MODE_CTR || md == TDES_MODE_CBC_DECRYPT)) {
-                    const uint32_t mi = p.order[ps + slot];
-                    const uint2 v = md == TDES_MODE_CTR ? ld_msg(msg_in(p, mi) + blk) : cbc_prev(p, mi, blk);
-                    A0[s] ^= v.x;
-                    A1[s] ^= v.y;
+                for (int s = 0; s < 32; ++s) {
+                    const uint32_t md = smode[s];
+                    const uint32_t mi = sidx[kSliceSlots * s + slot];
+                    if (mi != ~0u && (md == TDES_MODE_CTR || md == TDES_MODE_CBC_DECRYPT)) {
+                        const uint2 v = md == TDES_MODE_CTR ? ld_msg(msg_in(p, mi) + blk) : cbc_prev(p, mi, blk);
+                        A0[s] ^= v.x;
+                        A1[s] ^= v.y;
+                    }
+                }
+                __syncwarp();  // in place: every read precedes the writes
+#pragma unroll
+                for (int s = 0; s < 32; ++s) {
+                    const uint32_t mi = sidx[kSliceSlots * s + slot];
+                    if (mi != ~0u) __stcs(msg_out(p, mi) + blk, make_uint2(A0[s], A1[s]));
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < 32; ++s) {
+                    const uint32_t ps = __shfl_sync(0xFFFFFFFFu, pos, s);
+                    const uint32_t c = __shfl_sync(0xFFFFFFFFu, cm, s);
+                    const uint32_t md = c >> 8;
+                    if (slot < (c & 0xFFu) && (md == TDES_MODE_CTR || md == TDES_MODE_CBC_DECRYPT)) {
+                        const uint32_t mi = p.order[ps + slot];
+                        const uint2 v = md == TDES_MODE_CTR ? ld_msg(msg_in(p, mi) + blk) : cbc_prev(p, mi, blk);
+                        A0[s] ^= v.x;
+                        A1[s] ^= v.y;
+                    }
+                }
+                __syncwarp();  // in place: every read precedes the writes
+#pragma unroll
+                for (int s = 0; s < 32; ++s) {
+                    const uint32_t ps = __shfl_sync(0xFFFFFFFFu, pos, s);
+                    const uint32_t cs = __shfl_sync(0xFFFFFFFFu, cm, s) & 0xFFu;
+                    if (slot < cs)
+                        __stcs(msg_out(p, p.order[ps + slot]) + blk, make_uint2(A0[s], A1[s]));
                 }
             }
-            __syncwarp();  // in place: every read precedes the writes
-#pragma unroll
-            for (int s = 0; s < 32; ++s) {
-                const uint32_t ps = __shfl_sync(0xFFFFFFFFu, pos, s);
-                const uint32_t cs = __shfl_sync(0xFFFFFFFFu, cm, s) & 0xFFu;
-                if (slot < cs)
-                    __stcs(msg_out(p, p.order[ps + slot]) + blk, make_uint2(A0[s], A1[s]));
-            }
+            __syncwarp();  // sidx and smode are rewritten by the next tile
         }
     }
 }
@@ -878,7 +915,8 @@ cudaError_t prepare(int device, UniLaunch* out) {
         e = cudaFuncSetAttribute(uni_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kMixedChainWarps * kMixedChainWarpBytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(uni_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        e = cudaFuncSetAttribute(uni_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kUniWarps * kMixedWarpBytes);
     int fit = 0;
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, uni_tile_kernel<kKindEcb, true>,
@@ -1005,7 +1043,7 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
             uni_tile_kernel<kKindCtr, false><<<g, b, dyn, s>>>(p);
             uni_tile_kernel<kKindCbcDec, false><<<g, b, dyn, s>>>(p);
         }
-        uni_mixed_kernel<false><<<g, b, dyn, s>>>(p);
+        uni_mixed_kernel<false><<<g, b, (size_t)kUniWarps * kMixedWarpBytes, s>>>(p);
         // CBC-encryption chains: one CTA per SM, each warp with room for its
         // chains' message indices (2^28 messages of 64 B: 75.2 -> 73.1 ms
         // with the indices, alternating A/B runs) and its held blocks.  The
