@@ -48,6 +48,11 @@ constexpr int kUniTableBytes = TDES_TABLE_WORDS * 4;    // one staged table per 
 // read again after the rounds
 constexpr int kSliceSlots = 8;
 constexpr int kMixedWarpBytes = kUniTableBytes + 32 * kSliceSlots * 4 + 32;
+// Single-key block tiles: beside the table, the tile's message indices (up to
+// kTileSlots messages a tile, so 16-byte-path messages of 64 bytes or more),
+// read again after the rounds
+constexpr int kTileSlots = 128;
+constexpr int kTileWarpBytes = kUniTableBytes + kTileSlots * 4;
 // CBC-encryption chains: a warp's table, its 1024 chains' message indices and
 // one held block per chain (25 KB; one CTA per SM of 8 warps for mixed-key
 // chains, 9 for single-key tiles)
@@ -64,7 +69,7 @@ constexpr int kSmemPerSm = 228 * 1024, kSmemReservedPerCta = 1024;
 static_assert(kKeyChainWarps * kChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm, "single-key chain CTA");
 static_assert(kMixedChainWarps * kMixedChainWarpBytes + kSmemReservedPerCta <= kSmemPerSm,
               "mixed-key chain CTA");
-static_assert(2 * (kUniWarps * kUniTableBytes + kSmemReservedPerCta) <= kSmemPerSm, "two tile CTAs per SM");
+static_assert(2 * (kUniWarps * kTileWarpBytes + kSmemReservedPerCta) <= kSmemPerSm, "two tile CTAs per SM");
 static_assert(2 * (kUniWarps * kMixedWarpBytes + kSmemReservedPerCta) <= kSmemPerSm,
               "two mixed-key CTAs per SM");
 constexpr int kScanThreads = 1024;
@@ -354,7 +359,7 @@ __global__ void uni_scatter_kernel(UniParams p) {
     }
 }
 
-extern __shared__ __align__(16) uint8_t uni_smem[];  // kUniTableBytes per warp
+extern __shared__ __align__(16) uint8_t uni_smem[];  // a slice per warp (kTileWarpBytes, ...)
 
 __device__ __forceinline__ const uint2* msg_in(const UniParams& p, uint32_t mi) {
     return reinterpret_cast<const uint2*>(p.in + (uint64_t)mi * p.msg_bytes);
@@ -449,8 +454,13 @@ __device__ __forceinline__ uint2 cbc_prev(const UniParams& p, uint32_t mi, uint3
 // for 2^28 messages).
 template <int KIND, bool VEC16>
 __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
-                                               const uint32_t* __restrict__ tab, uint32_t lane,
-                                               bool one_pass) {
+                                               const uint32_t* __restrict__ tab, uint32_t* tidx,
+                                               uint32_t lane, bool one_pass) {
+    // 16-byte path with at most kTileSlots messages a tile: the lane holding
+    // a message's first pair keeps its index in tidx for the loops after the
+    // rounds, which read it there instead of from order (2^28 messages of
+    // 64 B: 64.03 -> 63.42 ms, alternating A/B runs)
+    const bool keep = VEC16 && p.per_tile <= (uint32_t)kTileSlots;
     uint32_t A0[32], A1[32];
     uint32_t pos0 = tile_pos0(p, t);
 #pragma unroll
@@ -460,6 +470,7 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
         if (VEC16) {
             const bool ok = q.slot0 < p.per_tile;
             const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
+            if (keep && ok && q.blk0 == 0u) tidx[q.slot0] = mi0;
             if (KIND == kKindCtr) {
                 const uint64_t c0 = ld_iv(p, mi0);
                 v0 = ctr_words(c0, q.blk0);
@@ -478,8 +489,11 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
         A0[2 * j + 1] = v1.x;
         A1[2 * j + 1] = v1.y;
     }
+    __syncwarp();
     tdes_process32_compact<false>(A0, A1, tab, one_pass);
     pos0 = tile_pos0(p, t);  // reloaded: nothing but the planes stays live across the rounds
+    // the message of slot x (x < per_tile) after the rounds
+    auto msg_of = [&](uint32_t x) { return keep ? tidx[x] : p.order[pos0 + x]; };
     if (KIND == kKindCtr || KIND == kKindCbcDec) {
         uint2 carry = make_uint2(0u, 0u);  // CBC decryption: lane 31's second block of pair j - 1
 #pragma unroll
@@ -492,7 +506,7 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
                 // down (lane 0: lane 31 of pair j - 1), in the same message
                 // unless b0 = 0, where the IV stands in.
                 const bool ok = q.slot0 < p.per_tile;
-                const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
+                const uint32_t mi0 = msg_of(min(q.slot0, p.per_tile - 1u));
                 const uint4 w = ld_msg(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
                 uint2 up = make_uint2(__shfl_up_sync(0xFFFFFFFFu, w.z, 1),
                                       __shfl_up_sync(0xFFFFFFFFu, w.w, 1));
@@ -503,7 +517,7 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
                 if (!ok) v0 = v1 = make_uint2(0u, 0u);
             } else if (VEC16 && KIND == kKindCtr) {
                 const bool ok = q.slot0 < p.per_tile;
-                const uint32_t mi0 = p.order[pos0 + min(q.slot0, p.per_tile - 1u)];
+                const uint32_t mi0 = msg_of(min(q.slot0, p.per_tile - 1u));
                 const uint4 w = ld_msg(reinterpret_cast<const uint4*>(msg_in(p, mi0) + q.blk0));
                 v0 = make_uint2(w.x, w.y);
                 v1 = make_uint2(w.z, w.w);
@@ -529,7 +543,7 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
     for (int j = 0; j < 16; ++j) {
         const PairSlots q = pair_slots(p, 64u * j + 2u * lane);
         if (q.slot0 < p.per_tile) {
-            const uint32_t mi0 = p.order[pos0 + q.slot0];
+            const uint32_t mi0 = msg_of(q.slot0);
             if (VEC16) {
                 __stcs(reinterpret_cast<uint4*>(msg_out(p, mi0) + q.blk0),
                        make_uint4(A0[2 * j], A1[2 * j], A0[2 * j + 1], A1[2 * j + 1]));
@@ -543,6 +557,7 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
             }
         }
     }
+    __syncwarp();  // tidx is rewritten by the next tile
 }
 
 // The block passes of 1024 CBC-encryption chains: widx[32 s + lane] is the
@@ -668,7 +683,7 @@ __global__ void __launch_bounds__(KIND == kKindCbcEnc ? 32 * kKeyChainWarps : 32
                                   KIND == kKindCbcEnc ? 1 : 2) uni_tile_kernel(UniParams p) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t* wtab = reinterpret_cast<uint32_t*>(
-        uni_smem + (size_t)warp * (KIND == kKindCbcEnc ? kChainWarpBytes : kUniTableBytes));
+        uni_smem + (size_t)warp * (KIND == kKindCbcEnc ? kChainWarpBytes : kTileWarpBytes));
     const uint32_t first = p.hdr->kind_tiles[KIND];
     const uint32_t n = p.hdr->kind_tiles[KIND + 1] - first;
     const uint32_t nw = blockDim.x >> 5;
@@ -692,7 +707,7 @@ __global__ void __launch_bounds__(KIND == kKindCbcEnc ? 32 * kKeyChainWarps : 32
         if (KIND == kKindCbcEnc)
             uni_chain_tile(p, t, wtab, lane, one_pass);
         else
-            uni_block_tile<KIND, VEC16>(p, t, wtab, lane, one_pass);
+            uni_block_tile<KIND, VEC16>(p, t, wtab, wtab + TDES_TABLE_WORDS, lane, one_pass);
     }
 }
 
@@ -900,7 +915,7 @@ cudaError_t prepare(int device, UniLaunch* out) {
     UniLaunch u;
     u.device = device;
     cudaError_t e = cudaDeviceGetAttribute(&u.sms, cudaDevAttrMultiProcessorCount, device);
-    const int dyn = kUniWarps * kUniTableBytes;
+    const int dyn = kUniWarps * kTileWarpBytes;
     const void* fns[] = {
         (const void*)uni_tile_kernel<kKindEcb, false>, (const void*)uni_tile_kernel<kKindEcb, true>,
         (const void*)uni_tile_kernel<kKindCtr, false>, (const void*)uni_tile_kernel<kKindCtr, true>,
@@ -1015,7 +1030,7 @@ int tdes_uniform_crypt(const tdes_keytable_t* kt, const uint32_t* key_index, con
 
     const int grid = geo.sms * 8;
     const int work_grid = geo.sms * geo.work_ctas;
-    const size_t dyn = (size_t)kUniWarps * kUniTableBytes;
+    const size_t dyn = (size_t)kUniWarps * kTileWarpBytes;
     const char* what = "clearing the plan counters";
     e = cudaMemsetAsync(base, 0, L.o_cursor, s);  // header and counts
     if (e == cudaSuccess) {
