@@ -459,8 +459,10 @@ __device__ __forceinline__ void uni_block_tile(const UniParams& p, uint32_t t,
     // 16-byte path with at most kTileSlots messages a tile: the lane holding
     // a message's first pair keeps its index in tidx for the loops after the
     // rounds, which read it there instead of from order (2^28 messages of
-    // 64 B: 64.03 -> 63.42 ms, alternating A/B runs)
-    const bool keep = VEC16 && p.per_tile <= (uint32_t)kTileSlots;
+    // 64 B: 64.03 -> 63.42 ms, alternating A/B runs).  CBC-decryption tiles
+    // ran slower with it (10.33 -> 10.59 ms in a launch list) and keep the
+    // order reads: 63.41 -> 63.14 ms.
+    const bool keep = VEC16 && KIND != kKindCbcDec && p.per_tile <= (uint32_t)kTileSlots;
     uint32_t A0[32], A1[32];
     uint32_t pos0 = tile_pos0(p, t);
 #pragma unroll
