@@ -392,9 +392,10 @@ def run_ours(args):
         tdes.tdes_ecb_crypt_host(ks, False, hbuf, hbuf, dev_buf)  # warm-up
         # Each call timed on its own and the median kept: the host link and
         # host memory are shared with the GPU's neighbour on the same host,
-        # and one call in a few met a slowdown (a mean of 3 calls once read
-        # 142 against 157-159 GB/s).  Every call's rate is reported.
-        n_e2e = max(5, min(10, args.steps // 50))
+        # and calls sometimes met a slowdown (a mean of 3 calls once read 142
+        # against 157-159 GB/s; in another run plain host-to-device copies ran
+        # at 22 GB/s for a while).  Every call's rate is reported.
+        n_e2e = 9
         if world > 1:
             dist.barrier()
         calls = []
@@ -408,14 +409,18 @@ def run_ours(args):
         # the copies alone, for context: the host link bounds the end-to-end number
         dbuf = torch.empty(NBYTES, dtype=torch.uint8, device=f"cuda:{dev}")
         torch.cuda.synchronize()
-        t = time.perf_counter()
-        dbuf.copy_(hbuf, non_blocking=True)
-        torch.cuda.synchronize()
-        h2d = NBYTES / (time.perf_counter() - t) / 1e9
-        t = time.perf_counter()
-        hbuf.copy_(dbuf, non_blocking=True)
-        torch.cuda.synchronize()
-        d2h = NBYTES / (time.perf_counter() - t) / 1e9
+
+        def copy_gbs(dst, src):  # median of three timed copies
+            r = []
+            for _ in range(3):
+                t = time.perf_counter()
+                dst.copy_(src, non_blocking=True)
+                torch.cuda.synchronize()
+                r.append(NBYTES / (time.perf_counter() - t) / 1e9)
+            return float(np.median(r))
+
+        h2d = copy_gbs(dbuf, hbuf)
+        d2h = copy_gbs(hbuf, dbuf)
         del dbuf
         e2e = {"value": world * NBYTES / el / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": NBYTES, "d2h_bytes_per_step": NBYTES,
