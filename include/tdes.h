@@ -150,15 +150,13 @@ int tdes_cbc_decrypt_noalloc(const tdes_ks_t *ks, uint64_t iv, const void *in, v
                              size_t nbytes, tdes_stream_t stream);
 
 /* Host-buffer ECB: encrypts (decrypt == 0) or decrypts host memory
- * host_in[0, nbytes) into host_out.  When both buffers are pinned host
- * memory (cudaHostAlloc / cudaHostRegister), 8-byte aligned and the same or
- * disjoint, the kernel reads and writes them directly over the host link in
- * one launch and dev_buf is not used.  Otherwise the data streams through the
- * caller's device buffer dev_buf of dev_bytes bytes (16-byte aligned, at
- * least 4 x 32 KiB, used as 4 to 16 rotating parts of about 32 MiB):
- * host-to-device copies, the kernel and device-to-host copies of successive
- * chunks overlap on internal streams.  dev_buf is checked either way.
- * Synchronous: returns when host_out is complete.  in == out is allowed. */
+ * host_in[0, nbytes) into host_out, streaming it through the caller's device
+ * buffer dev_buf of dev_bytes bytes (16-byte aligned, at least 4 x 32 KiB,
+ * used as 4 to 16 rotating parts of about 32 MiB): host-to-device copies,
+ * the kernel and device-to-host copies of successive chunks overlap on
+ * internal streams.  Host buffers should be pinned (cudaHostAlloc /
+ * page-locked) for full copy speed.  Synchronous: returns when host_out is
+ * complete.  in == out is allowed. */
 int tdes_ecb_crypt_host(const tdes_ks_t *ks, int decrypt, const void *host_in, void *host_out,
                         size_t nbytes, void *dev_buf, size_t dev_bytes);
 

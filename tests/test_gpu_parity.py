@@ -201,9 +201,8 @@ def test_argument_errors(cuda_lib):
 
 @pytest.mark.parametrize("kind", ["pinned", "pageable", "pinned_4_bytes_off"])
 def test_host_buffer_pipeline(cuda_lib, kind):
-    """Host buffers in and out: pinned ones are read and written by the kernel
-    directly; pageable ones, and pinned ones off an 8-byte boundary, stream
-    through the device buffer in several chunks."""
+    """Host buffers in and out, pinned, pageable, and pinned but off an 8-byte
+    boundary: each streams through the device buffer in several chunks."""
     nblocks = (1 << 20) + 333  # 8 MiB + ragged, several chunks of a 1 MiB device buffer
     keys = synth.key_triple(6000)
     data = synth.random_bytes(6000, 8 * nblocks)
