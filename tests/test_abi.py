@@ -87,3 +87,50 @@ def test_oversized_calls_refused_without_device(lib):
     rc = lib.tdes_cbc_decrypt_noalloc(ks, 0, p, p, tdes.TDES_NOALLOC_MAX_BYTES + 8192, None)
     assert rc == tdes.TDES_EINVAL
     assert "scratch limit" in lib.tdes_last_error().decode()
+
+
+def test_batch_server_and_tuner_calls_refuse_null_arguments(lib):
+    """The batch-context, shape, autotuner, server and uniform calls refuse
+    NULL handles and pointers with TDES_EINVAL before any device query (this
+    suite has no GPU), and the no-result calls accept NULL quietly."""
+    vp = ctypes.c_void_p
+    t = ctypes.c_uint64()
+    h = vp()
+    EINVAL = tdes.TDES_EINVAL
+    refused = {
+        "tdes_ctx_create": lambda: lib.tdes_ctx_create(None, None, ctypes.byref(h)),
+        "tdes_batch_submit": lambda: lib.tdes_batch_submit(None, None, 0, ctypes.byref(t)),
+        "tdes_batch_submit_plan": lambda: lib.tdes_batch_submit_plan(None, None, ctypes.byref(t)),
+        "tdes_batch_poll": lambda: lib.tdes_batch_poll(None, 1, None),
+        "tdes_batch_wait": lambda: lib.tdes_batch_wait(None, 1, 1000),
+        "tdes_batch_release": lambda: lib.tdes_batch_release(None, 1),
+        "tdes_batch_plan": lambda: lib.tdes_batch_plan(None, None, 0, None, ctypes.byref(h)),
+        "tdes_batch_set_shape": lambda: lib.tdes_batch_set_shape(None, None),
+        "tdes_batch_get_shape": lambda: lib.tdes_batch_get_shape(None, None),
+        "tdes_batch_configure": lambda: lib.tdes_batch_configure(None, 8, 0),
+        "tdes_batch_info": lambda: lib.tdes_batch_info(None, None),
+        "tdes_batch_launch": lambda: lib.tdes_batch_launch(None, None),
+        "tdes_batch_autotune": lambda: lib.tdes_batch_autotune(None, 0, 5, None, None),
+        "tdes_keytable_create": lambda: lib.tdes_keytable_create(None, 1, ctypes.byref(h)),
+        "tdes_server_create": lambda: lib.tdes_server_create(None, None, ctypes.byref(h)),
+        "tdes_server_submit": lambda: lib.tdes_server_submit(None, None, ctypes.byref(t)),
+        "tdes_server_poll": lambda: lib.tdes_server_poll(None, 1),
+        "tdes_server_stats": lambda: lib.tdes_server_stats(None, 0, None),
+        "tdes_server_autotune": lambda: lib.tdes_server_autotune(None, None, 0, None),
+        "tdes_serve_loadtest": lambda: lib.tdes_serve_loadtest(None, None, None),
+        "tdes_uniform_scratch_bytes": lambda: lib.tdes_uniform_scratch_bytes(None, 1, 64, None),
+        "tdes_uniform_info": lambda: lib.tdes_uniform_info(None, None),
+    }
+    for name, call in refused.items():
+        assert call() == EINVAL, name
+    # calls without a result accept NULL
+    lib.tdes_ctx_destroy(None)
+    lib.tdes_ctx_config_default(None)
+    lib.tdes_batch_free(None)
+    lib.tdes_keytable_free(None)
+    lib.tdes_server_destroy(None)
+    cfg = tdes.CtxConfig()
+    lib.tdes_ctx_config_default(ctypes.byref(cfg))
+    assert cfg.streams == 2
+    # the autotune cache follows TDES_AUTOTUNE_CACHE (set for the test session)
+    assert lib.tdes_autotune_cache_path().decode() == os.environ["TDES_AUTOTUNE_CACHE"]
