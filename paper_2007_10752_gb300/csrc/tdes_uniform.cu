@@ -742,15 +742,17 @@ __global__ void __launch_bounds__(CHAIN ? 32 * kMixedChainWarps : 32 * kUniWarps
             pos = p.msg_off[g] + at;
             kd = key * 2u + dir_of_mode(md);
         }
-        {
+        // the tile's table: lane s's slice row, transposed across the lanes
+        auto stage_table = [&]() {
             const uint32_t* row = p.keypacked + (uint64_t)kd * kPackedWords;
             __syncwarp();
 #pragma unroll 1
             for (int q = 0; q < kPackedWords; ++q)
                 wtab[32 * q + lane] = transpose_lanes32(__ldg(row + q), lane);
             __syncwarp();
-        }
+        };
         if (CHAIN) {
+            stage_table();
             // lane l walks chain l of every slice
             uint32_t* widx = wtab + TDES_TABLE_WORDS;
             uint32_t A0[32], A1[32];
@@ -796,7 +798,9 @@ __global__ void __launch_bounds__(CHAIN ? 32 * kMixedChainWarps : 32 * kUniWarps
                 A0[s] = v.x;
                 A1[s] = v.y;
             }
-            __syncwarp();
+            // staged after the loads are issued, so that their latency
+            // overlaps the table build
+            stage_table();
             tdes_process32_compact<true>(A0, A1, wtab, false);
             if (keep) {
 #pragma unroll
