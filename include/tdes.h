@@ -587,7 +587,7 @@ int tdes_server_stats(tdes_server_t *s, int reset, tdes_server_stats_t *out);
 /* Autotuner of the server's shape (warps per CTA, CTAs per SM each batch
  * leaves free for the next, slots, round form) for the request mix of `load`
  * (its offered_gbps is ignored).  A shape's score is its p99 latency at one
- * offered load for all candidates, 90% of the built-in default's closed-loop
+ * offered load for all candidates, 95% of the built-in default's closed-loop
  * throughput, among the shapes that keep at least 97% of that throughput
  * closed-loop; each figure is the median of three tdes_serve_loadtest runs
  * on a fresh server.  Coordinate search over warps 2, 4, 8, reserved CTAs 1,
